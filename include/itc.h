@@ -1,0 +1,237 @@
+/*
+ * itc.h -- C ABI of libitc.so: lattice information-theoretic clustering on one GPU
+ * (C. Bauckhage, K. Kersting, "Efficient Information Theoretic Clustering on Discrete Lattices",
+ * arXiv:1310.7114).
+ *
+ * Problem (Sec. 2.1): given data on a lattice -- a binary image X (Sec. 3.2), a per-pixel weight
+ * image h (Sec. 5) or a gray image read as a 3-D [u, v, g] occupancy lattice (Sec. 1 (ii)) -- and
+ * an initial codebook W = {w_1..w_M}, move W to minimise the Cauchy-Schwarz divergence of
+ * Eq. (1) between the Parzen densities p = h * G and q = W * G (Eq. (dens1), (dens2)).
+ * Following Sec. 3.1 the data sums are read from precomputed, truncated, separable Gaussian
+ * fields; Algorithm 1 iterates the fixed-point update of Eq. (origupdate) with those fields.
+ *
+ * Conventions shared by every entry point
+ *   - Coordinates: u = row (slow axis), v = column (fast axis), g = gray level.  A codebook
+ *     vector is stored as (u, v) or (u, v, g) floats; W arrays are [M][ndim] row-major.
+ *   - Kernel: g(d) = prod_i exp(-d_i^2 / (2 sigma_i^2)) (unnormalised).  sigma is the width of
+ *     the product kernels tau = rho of Sec. 2.1 (xi = omega = sigma / sqrt 2), so the three
+ *     overlap integrals of Eq. (1) share one kernel and D_cs = log S_WW + log S_XX - 2 log S_XW.
+ *   - Truncation (Sec. 3.1, finite filter masks): data sums run over the box
+ *     |x_i - y_i| <= R_i, R_i = ceil(trunc * sigma_i); taps are not renormalised; sites
+ *     outside the lattice hold no data.  Codebook-codebook sums are not truncated.
+ *   - Fields: planar FP32, plane p of an image is [G][H][fpitch] floats with
+ *     fpitch = itc_field_pitch(W) (a multiple of 4); planes are A, F_u, F_v (, F_g):
+ *       A(y)   = sum_x h(x) g(x - y)
+ *       F_i(y) = sum_x h(x) g(x - y) (x_i - y_i)   (centred moments, default)
+ *       F_i(y) = sum_x h(x) g(x - y) x_i           (ITC_FIELDS_ABSOLUTE: the convolution of the
+ *                                                   coordinate-weighted image u.X, v.X, g.X)
+ *   - Memory: every data pointer is a DEVICE pointer unless its comment says "host".  The caller
+ *     owns every buffer; the library allocates no device memory and keeps no global state.
+ *     Scratch memory is caller-provided `ws` of at least the size the matching *_bytes query
+ *     returns.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Every call only
+ *     enqueues work and returns; results are valid once the stream has reached them.
+ *   - Errors: 0 = success; negative = error (nothing was launched unless ITC_ERR_CUDA says a
+ *     launch failed); positive = warning.  Per-image device status goes to itc_stats.status.
+ */
+#ifndef ITC_H
+#define ITC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------- status codes */
+#define ITC_OK 0
+#define ITC_WARN_EMPTY_SUPPORT 1   /* device status: some w_k had no data in its window (kept) */
+#define ITC_ERR_INVALID_ARG (-1)   /* bad pointer, size, sigma, flag or layout */
+#define ITC_ERR_CUDA (-2)          /* a CUDA launch or query failed */
+#define ITC_ERR_TIMEOUT (-3)       /* a bounded device wait gave up */
+#define ITC_ERR_NONFINITE (-4)     /* device status: S_XW = 0 or a non-finite value appeared */
+#define ITC_ERR_WORKSPACE (-5)     /* workspace missing, too small or misaligned */
+#define ITC_ERR_UNSUPPORTED (-6)   /* valid request outside this build's limits */
+
+/* --------------------------------------------------------------------------- data types */
+#define ITC_U8 0   /* 2-D: occupancy 0/1 (binary image X of Sec. 3.2); 3-D: gray level */
+#define ITC_F32 1  /* 2-D: weights h >= 0 (weighted ITC, Sec. 5) */
+
+/* -------------------------------------------------------------------------------- flags */
+#define ITC_CONTINUOUS 1       /* keep W real (lookups at the rounded site); default snaps W to
+                                  the lattice after every update (W as an image, Sec. 3.2) */
+#define ITC_FIELDS_ABSOLUTE 2  /* itc_fields writes u.X, v.X (, g.X) convolutions, not centred */
+#define ITC_STOP_ON_FIXED 4    /* stop when an iteration moves no codebook (theta = 0 test of
+                                  Algorithm 1) */
+
+/* Limits of this build. */
+#define ITC_MAX_RADIUS_UV 32   /* R_u, R_v */
+#define ITC_MAX_RADIUS_UV_3D 24 /* R_u, R_v of 3-D gray lattices */
+#define ITC_MAX_RADIUS_G 64    /* R_g */
+#define ITC_MAX_M 2048         /* codebook vectors per image */
+#define ITC_MAX_GRAY 256       /* G */
+
+/* One lattice image.  `data` and `weight` are device pointers. */
+typedef struct {
+    int ndim;            /* 2: binary or weighted image; 3: gray image as [u, v, g] lattice */
+    int H, W;            /* rows (u) and columns (v) */
+    int G;               /* ndim 3: gray levels (lattice depth along g, <= 256); ndim 2: 1 */
+    int pitch;           /* elements between consecutive rows of `data` and `weight` (>= W) */
+    int dtype;           /* ITC_U8 or ITC_F32 (ITC_F32 only for ndim 2) */
+    const void* data;    /* H rows of `pitch` elements */
+    const float* weight; /* ndim 3 only: per-pixel weight h(u, v) >= 0, or NULL for 1 */
+} itc_image;
+
+/* Method parameters (host struct, passed by pointer, read during the call). */
+typedef struct {
+    float sigma[3];      /* kernel width per axis (u, v, g), lattice units, > 0 */
+    float trunc;         /* mask half width in sigmas: R_i = ceil(trunc * sigma_i); paper: small
+                            masks (Sec. 3.1); 3 is the usual choice */
+    int iters;           /* fixed-point iterations (Algorithm 1 loop), >= 0 */
+    float step_scale;    /* 1: Eq. (origupdate); 0.5: Eq. (accupdate) evaluated exactly */
+    int flags;           /* ITC_CONTINUOUS | ITC_FIELDS_ABSOLUTE | ITC_STOP_ON_FIXED */
+} itc_params;
+
+/* Per-image results, written by the device. */
+typedef struct {
+    double dcs;          /* D_cs of Eq. (1) at the reported W (+inf if S_XW == 0) */
+    double sxw, sww, sxx;/* the three sums of Eq. (1) */
+    double c;            /* S_XW / S_WW, the constant c of Eq. (origupdate) */
+    int empty;           /* codebooks with no data in their window in the last evaluation */
+    int moved;           /* codebooks moved by the last update */
+    int iters_done;      /* updates applied */
+    int status;          /* ITC_OK, ITC_WARN_EMPTY_SUPPORT or ITC_ERR_NONFINITE */
+} itc_stats;
+
+/* ------------------------------------------------------------------------------ queries */
+
+/* Row pitch (floats) of every field plane of an image W columns wide: W rounded up to 4. */
+int itc_field_pitch(int W);
+
+/* Bytes of the field planes of `img` (ndim+1 planes of G*H*itc_field_pitch(W) floats);
+ * 0 if img is invalid. */
+size_t itc_fields_bytes(const itc_image* img);
+
+/* Scratch bytes itc_fields needs for `img` (per-tile S_XX partial sums); 0 if invalid. */
+size_t itc_fields_workspace_bytes(const itc_image* img);
+
+/* Message for a status code (static string). */
+const char* itc_status_string(int code);
+
+/* ------------------------------------------------------------------------------ fields */
+/*
+ * itc_fields -- step 2 of Algorithm 1, P = X * G (Sec. 3.1; weighted P = h * G, Sec. 5):
+ * the truncated separable Gaussian fields of one image and S_XX = sum_x h(x) A(x) (the V(X)
+ * term of Eq. (1)).
+ *   img    : the image (host struct; data on device)
+ *   p      : sigma, trunc and ITC_FIELDS_ABSOLUTE are used
+ *   fields : device, itc_fields_bytes(img) bytes, 16-byte aligned; written
+ *   sxx    : device double, written (may be NULL)
+ *   ws     : device scratch of itc_fields_workspace_bytes(img) bytes, 16-byte aligned
+ * Errors: ITC_ERR_INVALID_ARG (bad image/params/pointer), ITC_ERR_WORKSPACE, ITC_ERR_CUDA.
+ */
+int itc_fields(const itc_image* img, const itc_params* p, float* fields, double* sxx,
+               void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------- one update step */
+/*
+ * itc_step -- one iteration of Algorithm 1 (steps 4-10): gather A and the moments at the
+ * lattice-rounded codebook sites, add the M x M codebook interaction sums, apply Eq. (origupdate)
+ * in the centred form w_k' = w_k + step_scale (D_k - c E_k) / a_k with c = S_XW / S_WW, then
+ * (default) round w_k' to the lattice, floor(x + 0.5) clamped to the image.  All codebooks read
+ * the same old W (Jacobi).  A codebook with a_k = 0 keeps its position (status warning).
+ *   fields    : device, from itc_fields with the same img/p (centred or absolute, per p->flags)
+ *   sxx       : device double from itc_fields (required; used for the D_cs in stats)
+ *   W_in      : device [M][ndim]; W_out: device [M][ndim] (may alias W_in)
+ *   W_lattice : device int [M][ndim] = rounded W_out, or NULL
+ *   stats     : device, 1 record: D_cs, sums and c at W_in; moved/empty of this update; or NULL
+ * Errors: ITC_ERR_INVALID_ARG, ITC_ERR_CUDA.
+ */
+int itc_step(const itc_image* img, const itc_params* p, const float* fields, const double* sxx,
+             int M, const float* W_in, float* W_out, int* W_lattice, itc_stats* stats,
+             void* stream);
+
+/* ------------------------------------------------------------------- batched runs (plan) */
+/*
+ * A plan describes a batch of B images (ragged sizes, codebook counts and parameters) for
+ * itc_run and itc_backward.  It is a byte blob built on the host by itc_plan; the caller copies
+ * the same bytes to device memory (16-byte aligned) and passes both copies.  The plan picks the
+ * tile shape per parameter class (itc_autotune may refine it) and lays out the workspace:
+ * the fields of every image, per-tile partial sums and the ragged W / grad_h offsets.
+ *
+ * Ragged arrays: W and grad_W are [sum_b M_b][ndim_b] floats, image b starting at codebook
+ * offset w_off(b) = sum_{b' < b} M_b' (times ndim); grad_h is one float per pixel, image b at
+ * offset gh_off(b) = sum_{b' < b} H_b' W_b', rows of W_b floats.
+ */
+
+/* Host bytes of a plan for B images. */
+size_t itc_plan_bytes(int B);
+
+/*
+ * itc_plan -- build a batch plan.
+ *   imgs   : host array of B image descriptors (data on device; 2-D images only in a batch
+ *            with ndim 3 images is allowed, each image keeps its own ndim)
+ *   M      : host int[B], codebook count per image (1..ITC_MAX_M)
+ *   p      : host itc_params[B] (per image) -- or one record if p_stride == 0
+ *   plan   : host buffer of itc_plan_bytes(B) bytes, written
+ *   ws_bytes_out : workspace bytes itc_run / itc_backward need for this plan
+ * Errors: ITC_ERR_INVALID_ARG (any invalid image, M or params; nothing written).
+ */
+int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, int p_stride,
+             void* plan, size_t plan_bytes, size_t* ws_bytes_out);
+
+/* Total floats of the ragged grad_h layout of a plan (sum of H_b W_b). */
+size_t itc_plan_pixels(const void* plan_host);
+
+/*
+ * itc_plan_offsets -- where image b of a plan lives (host-only query):
+ *   field_off : byte offset of the image's field planes inside `ws` (planes as for itc_fields,
+ *               plane stride = G * H * itc_field_pitch(W) floats), valid after itc_run
+ *   w_off     : offset in floats of the image's codebooks in the ragged W / grad_W arrays
+ *   gh_off    : offset in floats of the image's pixels in the ragged grad_h array
+ * Any output pointer may be NULL.  Errors: ITC_ERR_INVALID_ARG (bad plan or b out of range).
+ */
+int itc_plan_offsets(const void* plan_host, int b, size_t* field_off, size_t* w_off, size_t* gh_off);
+
+/*
+ * itc_run -- Algorithm 1 for every image of a plan: fields (step 2) for all images in one
+ * launch per parameter class, then all images' iterations (steps 3-11) in one launch, one CTA
+ * per image.  W is read as the initial codebooks (step 1 is done by the caller) and overwritten
+ * with the result.  The fields stay in `ws` for a following itc_backward with the same plan.
+ *   plan_host, plan_dev : the same plan bytes on host and on device
+ *   W      : device ragged [sum M][ndim], in/out
+ *   stats  : device itc_stats[B]: D_cs and sums at the returned W; or NULL
+ *   ws     : device scratch, >= ws_bytes from itc_plan, 256-byte aligned
+ * The enqueued work is stream-capturable (CUDA graphs).
+ * Errors: ITC_ERR_INVALID_ARG, ITC_ERR_WORKSPACE, ITC_ERR_CUDA.
+ */
+int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
+            size_t ws_bytes, void* stream);
+
+/*
+ * itc_backward -- gradient of Eq. (1) for every image of a plan, scaled by an upstream gradient:
+ *   dD/dw_{k,i} = (2 / sigma_i^2) (E_{k,i} / S_WW - D_{k,i} / S_XW)
+ *   dD/dh(x)    = 2 A(x) / S_XX - (2 / S_XW) sum_k g(x - w_k) [x in the box of round(w_k)]
+ * D_k = sum_x h g(x - w_k)(x - w_k) over the box around round(w_k) (kernel at the real w_k),
+ * E_k = sum_j g(w_j - w_k)(w_j - w_k).  dD/dh is the derivative with respect to the per-pixel
+ * weight of weighted ITC (Sec. 5); its second term is a transposed Gaussian stamp of the
+ * codebook (q = W * G, Sec. 3.1).  The fields A are recomputed per tile from the images, never
+ * read from a stored copy, so the call needs no forward state beyond W.
+ *   W       : device ragged codebooks at which to differentiate
+ *   grad_dcs: device float[B] upstream gradient (NULL = 1)
+ *   grad_W  : device ragged [sum M][ndim], written (or NULL)
+ *   grad_h  : device ragged pixels (itc_plan_pixels floats), written (or NULL); 2-D images get
+ *             dD/dh(u,v); 3-D images get dD/dh of the weight of pixel (u,v) (voxel at its gray)
+ *   stats   : device itc_stats[B], D_cs and sums at W (or NULL)
+ *   ws      : as for itc_run
+ * Errors: ITC_ERR_INVALID_ARG, ITC_ERR_WORKSPACE, ITC_ERR_CUDA.
+ */
+int itc_backward(const void* plan_host, const void* plan_dev, const float* W,
+                 const float* grad_dcs, float* grad_W, float* grad_h, itc_stats* stats, void* ws,
+                 size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ITC_H */

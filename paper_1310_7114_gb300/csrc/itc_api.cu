@@ -1,0 +1,415 @@
+// itc_api.cu -- host side of libitc.so: argument checks, tap tables, batch plans and launches.
+// Every entry point is declared (and documented) in include/itc.h.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "itc_internal.cuh"
+
+using namespace itc;
+
+namespace {
+
+constexpr int kGridTileH2 = 64;   // fields tile height, 2-D
+constexpr int kGridTileH3 = 32;   // fields tile height, 3-D
+
+bool finite_pos(float x) { return isfinite(x) && x > 0.f; }
+
+int radius_of(float sigma, float trunc) { return (int)ceil((double)trunc * (double)sigma); }
+
+int check_image(const itc_image* img) {
+    if (!img || !img->data) return ITC_ERR_INVALID_ARG;
+    if (img->ndim != 2 && img->ndim != 3) return ITC_ERR_INVALID_ARG;
+    if (img->H < 1 || img->W < 1 || img->pitch < img->W) return ITC_ERR_INVALID_ARG;
+    if (img->ndim == 2) {
+        if (img->G != 1 && img->G != 0) return ITC_ERR_INVALID_ARG;
+        if (img->dtype != ITC_U8 && img->dtype != ITC_F32) return ITC_ERR_INVALID_ARG;
+        if (img->weight) return ITC_ERR_INVALID_ARG;
+    } else {
+        if (img->G < 1 || img->G > ITC_MAX_GRAY) return ITC_ERR_INVALID_ARG;
+        if (img->dtype != ITC_U8) return ITC_ERR_INVALID_ARG;
+    }
+    if ((long long)img->H * img->pitch > (1LL << 40)) return ITC_ERR_UNSUPPORTED;
+    return ITC_OK;
+}
+
+int check_params(const itc_params* p, int ndim) {
+    if (!p) return ITC_ERR_INVALID_ARG;
+    if (!finite_pos(p->trunc)) return ITC_ERR_INVALID_ARG;
+    for (int i = 0; i < ndim; ++i)
+        if (!finite_pos(p->sigma[i])) return ITC_ERR_INVALID_ARG;
+    if (p->iters < 0 || !isfinite(p->step_scale)) return ITC_ERR_INVALID_ARG;
+    if (p->flags & ~(ITC_CONTINUOUS | ITC_FIELDS_ABSOLUTE | ITC_STOP_ON_FIXED)) return ITC_ERR_INVALID_ARG;
+    const double ru = ceil((double)p->trunc * p->sigma[0]), rv = ceil((double)p->trunc * p->sigma[1]);
+    if (ru > ITC_MAX_RADIUS_UV || rv > ITC_MAX_RADIUS_UV) return ITC_ERR_UNSUPPORTED;
+    if (ndim == 3 && ceil((double)p->trunc * p->sigma[2]) > ITC_MAX_RADIUS_G) return ITC_ERR_UNSUPPORTED;
+    // 3-D tiles stage four input channels; past R = 24 they exceed the 227 KB of shared memory
+    if (ndim == 3 && (ru > ITC_MAX_RADIUS_UV_3D || rv > ITC_MAX_RADIUS_UV_3D)) return ITC_ERR_UNSUPPORTED;
+    return ITC_OK;
+}
+
+// g[d + R] = exp(-d^2 / (2 sigma^2)) and d g[d + R], computed in double, rounded once.
+void fill_taps(float sigma, int R, float* g, float* dg) {
+    for (int d = -R; d <= R; ++d) {
+        const double v = exp(-((double)d * d) / (2.0 * (double)sigma * sigma));
+        g[d + R] = (float)v;
+        dg[d + R] = (float)(d * v);
+    }
+}
+
+void make_taps(const itc_params* p, int ndim, Taps* t) {
+    memset(t, 0, sizeof(*t));
+    for (int i = 0; i < 3; ++i) {
+        const float s = (i < ndim) ? p->sigma[i] : 1.f;
+        t->sigma[i] = s;
+        t->inv2s2[i] = (i < ndim) ? (float)(1.0 / (2.0 * (double)s * s)) : 0.f;
+        t->R[i] = (i < ndim) ? radius_of(s, p->trunc) : 0;
+    }
+    fill_taps(t->sigma[0], t->R[0], t->gu, t->dgu);
+    fill_taps(t->sigma[1], t->R[1], t->gv, t->dgv);
+    if (ndim == 3) fill_taps(t->sigma[2], t->R[2], t->gg, t->dgg);
+}
+
+int tile_h_of(int ndim) { return ndim == 3 ? kGridTileH3 : kGridTileH2; }
+
+void fill_desc(const itc_image* img, const itc_params* p, int M, ImageDesc* d) {
+    memset(d, 0, sizeof(*d));
+    d->data = img->data;
+    d->weight = img->weight;
+    d->ndim = img->ndim;
+    d->H = img->H;
+    d->W = img->W;
+    d->G = img->ndim == 3 ? img->G : 1;
+    d->pitch = img->pitch;
+    d->dtype = img->dtype;
+    d->fpitch = itc_field_pitch(img->W);
+    d->M = M;
+    d->iters = p->iters;
+    d->flags = p->flags;
+    d->step_scale = p->step_scale;
+    const int th = tile_h_of(img->ndim);
+    d->tiles_u = (img->H + th - 1) / th;
+    d->tiles_v = (img->W + kTileW - 1) / kTileW;
+    d->tiles_g = img->ndim == 3 ? (d->G + kGSlices - 1) / kGSlices : 1;
+    d->plane_floats = (long long)d->G * img->H * d->fpitch;
+    d->bwd_tiles_u = (img->H + kBwdTileH - 1) / kBwdTileH;
+    d->bwd_tiles_v = (img->W + kBwdTileW - 1) / kBwdTileW;
+    for (int i = 0; i < 3; ++i) {
+        const float s = i < img->ndim ? p->sigma[i] : 1.f;
+        d->sigma[i] = s;
+        d->inv2s2[i] = i < img->ndim ? (float)(1.0 / (2.0 * (double)s * s)) : 0.f;
+        d->R[i] = i < img->ndim ? radius_of(s, p->trunc) : 0;
+    }
+}
+
+long long tiles_of(const ImageDesc& d) { return (long long)d.tiles_u * d.tiles_v * d.tiles_g; }
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? ITC_OK : ITC_ERR_CUDA; }
+
+size_t plan_layout(int B, size_t* desc_off, size_t* ints_off) {
+    const size_t h = align_up(sizeof(PlanHeader), 256);
+    const size_t d = align_up((size_t)B * sizeof(ImageDesc), 256);
+    const size_t n = align_up((size_t)(3 * (size_t)B + kMaxClasses + 2) * sizeof(int), 256);
+    if (desc_off) *desc_off = h;
+    if (ints_off) *ints_off = h + d;
+    return h + d + n;
+}
+
+const PlanHeader* plan_of(const void* plan_host) {
+    const PlanHeader* h = reinterpret_cast<const PlanHeader*>(plan_host);
+    if (!h || h->magic != kPlanMagic) return nullptr;
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int itc_field_pitch(int W) { return W <= 0 ? 0 : (W + 3) & ~3; }
+
+size_t itc_fields_bytes(const itc_image* img) {
+    if (check_image(img) != ITC_OK) return 0;
+    const int G = img->ndim == 3 ? img->G : 1;
+    return (size_t)(img->ndim + 1) * G * img->H * itc_field_pitch(img->W) * sizeof(float);
+}
+
+size_t itc_fields_workspace_bytes(const itc_image* img) {
+    if (check_image(img) != ITC_OK) return 0;
+    itc_params p;
+    memset(&p, 0, sizeof(p));
+    p.sigma[0] = p.sigma[1] = p.sigma[2] = 1.f;
+    p.trunc = 1.f;
+    ImageDesc d;
+    fill_desc(img, &p, 1, &d);
+    return align_up((size_t)tiles_of(d) * sizeof(double), 256);
+}
+
+const char* itc_status_string(int code) {
+    switch (code) {
+        case ITC_OK: return "ok";
+        case ITC_WARN_EMPTY_SUPPORT: return "warning: a codebook vector has no data within its mask (kept in place)";
+        case ITC_ERR_INVALID_ARG: return "invalid argument";
+        case ITC_ERR_CUDA: return "CUDA launch or query failed";
+        case ITC_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case ITC_ERR_NONFINITE: return "S_XW is zero or a value is not finite";
+        case ITC_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+        case ITC_ERR_UNSUPPORTED: return "request outside this build's limits";
+        default: return "unknown status";
+    }
+}
+
+int itc_fields(const itc_image* img, const itc_params* p, float* fields, double* sxx, void* ws,
+               size_t ws_bytes, void* stream) {
+    int rc = check_image(img);
+    if (rc) return rc;
+    if ((rc = check_params(p, img->ndim))) return rc;
+    if (!fields || !aligned(fields, 16)) return ITC_ERR_INVALID_ARG;
+    const size_t need = itc_fields_workspace_bytes(img);
+    if (!ws || ws_bytes < need || !aligned(ws, 16)) return ITC_ERR_WORKSPACE;
+    FieldsLaunch L;
+    memset(&L, 0, sizeof(L));
+    make_taps(p, img->ndim, &L.taps);
+    fill_desc(img, p, 1, &L.one);
+    L.fields = fields;
+    L.partials = reinterpret_cast<double*>(ws);
+    L.tile_h = tile_h_of(img->ndim);
+    L.absolute = (p->flags & ITC_FIELDS_ABSOLUTE) ? 1 : 0;
+    const long long nt = tiles_of(L.one);
+    if (nt > 0x7fffffffLL) return ITC_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    rc = cuda_status(launch_fields(L, (int)nt, L.taps.R[0], L.taps.R[1], img->ndim, img->dtype, s));
+    if (rc) return rc;
+    if (sxx) rc = cuda_status(launch_reduce_sxx(L.partials, (int)nt, sxx, s));
+    return rc;
+}
+
+int itc_step(const itc_image* img, const itc_params* p, const float* fields, const double* sxx, int M,
+             const float* W_in, float* W_out, int* W_lattice, itc_stats* stats, void* stream) {
+    int rc = check_image(img);
+    if (rc) return rc;
+    if ((rc = check_params(p, img->ndim))) return rc;
+    if (M < 1 || M > ITC_MAX_M) return ITC_ERR_INVALID_ARG;
+    if (!fields || !W_in || !W_out || !sxx) return ITC_ERR_INVALID_ARG;
+    RunLaunch L;
+    memset(&L, 0, sizeof(L));
+    fill_desc(img, p, M, &L.one);
+    L.one.iters = 1;
+    L.fields = fields;
+    L.sxx_single = sxx;
+    L.W_in = W_in;
+    L.W_out = W_out;
+    L.W_lattice = W_lattice;
+    L.stats = stats;
+    L.absolute = (p->flags & ITC_FIELDS_ABSOLUTE) ? 1 : 0;
+    L.final_eval = 0;
+    return cuda_status(launch_run(L, 1, M, 1, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t itc_plan_bytes(int B) {
+    if (B < 1) return 0;
+    return plan_layout(B, nullptr, nullptr);
+}
+
+int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, int p_stride,
+             void* plan, size_t plan_bytes, size_t* ws_bytes_out) {
+    if (B < 1 || !imgs || !M || !p || !plan) return ITC_ERR_INVALID_ARG;
+    size_t desc_off, ints_off;
+    const size_t need = plan_layout(B, &desc_off, &ints_off);
+    if (plan_bytes < need) return ITC_ERR_INVALID_ARG;
+    for (int b = 0; b < B; ++b) {
+        int rc = check_image(imgs + b);
+        if (rc) return rc;
+        const itc_params* pb = p_stride ? p + b : p;
+        if ((rc = check_params(pb, imgs[b].ndim))) return rc;
+        if (M[b] < 1 || M[b] > ITC_MAX_M) return ITC_ERR_INVALID_ARG;
+    }
+    std::vector<unsigned char> buf(need, 0);
+    PlanHeader* h = reinterpret_cast<PlanHeader*>(buf.data());
+    ImageDesc* descs = reinterpret_cast<ImageDesc*>(buf.data() + desc_off);
+    int* ints = reinterpret_cast<int*>(buf.data() + ints_off);
+    h->magic = kPlanMagic;
+    h->B = B;
+    h->desc_off = (long long)desc_off;
+    h->ints_off = (long long)ints_off;
+
+    // parameter classes: (ndim, dtype, sigma, trunc)
+    struct Key { int ndim, dtype; float s0, s1, s2, trunc; };
+    std::vector<Key> keys;
+    std::vector<int> cls_of(B);
+    for (int b = 0; b < B; ++b) {
+        const itc_params* pb = p_stride ? p + b : p;
+        Key k{imgs[b].ndim, imgs[b].dtype, pb->sigma[0], pb->sigma[1], imgs[b].ndim == 3 ? pb->sigma[2] : 0.f, pb->trunc};
+        int c = -1;
+        for (size_t i = 0; i < keys.size(); ++i)
+            if (memcmp(&keys[i], &k, sizeof(Key)) == 0) { c = (int)i; break; }
+        if (c < 0) {
+            if ((int)keys.size() == kMaxClasses) return ITC_ERR_UNSUPPORTED;
+            keys.push_back(k);
+            c = (int)keys.size() - 1;
+            ClassInfo& ci = h->cls[c];
+            make_taps(pb, imgs[b].ndim, &ci.taps);
+            ci.ndim = imgs[b].ndim;
+            ci.dtype = imgs[b].dtype;
+            ci.absolute = 0;
+            ci.tile_h = tile_h_of(imgs[b].ndim);
+        }
+        cls_of[b] = c;
+        fill_desc(imgs + b, pb, M[b], descs + b);
+        descs[b].cls = c;
+    }
+    h->ncls = (int)keys.size();
+
+    // fields, codebook and pixel offsets
+    long long foff = 0, woff = 0, ghoff = 0, maxM = 0;
+    int bwd = 0;
+    for (int b = 0; b < B; ++b) {
+        ImageDesc& d = descs[b];
+        d.field_off = foff;
+        foff += (long long)align_up((size_t)(d.ndim + 1) * d.plane_floats, 64);
+        d.w_off = woff;
+        woff += (long long)d.M * d.ndim;
+        d.gh_off = ghoff;
+        ghoff += (long long)d.H * d.W;
+        d.bwd_tile_begin = bwd;
+        bwd += d.bwd_tiles_u * d.bwd_tiles_v;
+        if (d.M > maxM) maxM = d.M;
+    }
+    h->fields_floats = foff;
+    h->total_pixels = ghoff;
+    h->max_M = (int)maxM;
+
+    // per class: image list, tile prefix, partial layout (class-major, images in list order)
+    int io = 0;
+    long long pbase = 0;
+    for (int c = 0; c < h->ncls; ++c) {
+        ClassInfo& ci = h->cls[c];
+        ci.list_off = io;
+        int n = 0;
+        for (int b = 0; b < B; ++b)
+            if (cls_of[b] == c) ints[io + n++] = b;
+        ci.nimg = n;
+        io += n;
+        ci.prefix_off = io;
+        long long t = 0;
+        ci.partial_base = pbase;
+        for (int i = 0; i < n; ++i) {
+            ImageDesc& d = descs[ints[ci.list_off + i]];
+            ints[io + i] = (int)t;
+            d.tile_begin = (int)t;
+            d.partial_off = pbase + t;
+            t += tiles_of(d);
+            if (t > 0x7fffffffLL) return ITC_ERR_UNSUPPORTED;
+        }
+        ints[io + n] = (int)t;
+        io += n + 1;
+        ci.ntiles = (int)t;
+        pbase += t;
+    }
+    h->total_tiles = pbase;
+    // backward pixel-tile prefix over all images
+    const int bwd_off = io;
+    for (int b = 0; b < B; ++b) ints[io++] = descs[b].bwd_tile_begin;
+    ints[io++] = bwd;
+    h->nints = io;
+    h->bwd_prefix_off = bwd_off;
+    h->bwd_tiles = bwd;
+
+    // workspace: [fields][S_XX partials][per-image backward scalars]
+    size_t off = 0;
+    h->ws_fields_off = 0;
+    off = align_up((size_t)foff * sizeof(float), 256);
+    h->ws_partials_off = (long long)off;
+    off = align_up(off + (size_t)pbase * sizeof(double), 256);
+    h->ws_scal_off = (long long)off;
+    off = align_up(off + (size_t)B * 4 * sizeof(double), 256);
+    h->ws_bytes = (long long)off;
+    if (ws_bytes_out) *ws_bytes_out = off;
+    memcpy(plan, buf.data(), need);
+    return ITC_OK;
+}
+
+size_t itc_plan_pixels(const void* plan_host) {
+    const PlanHeader* h = plan_of(plan_host);
+    return h ? (size_t)h->total_pixels : 0;
+}
+
+int itc_plan_offsets(const void* plan_host, int b, size_t* field_off, size_t* w_off, size_t* gh_off) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || b < 0 || b >= h->B) return ITC_ERR_INVALID_ARG;
+    const ImageDesc& d = reinterpret_cast<const ImageDesc*>(reinterpret_cast<const unsigned char*>(plan_host) + h->desc_off)[b];
+    if (field_off) *field_off = (size_t)h->ws_fields_off + (size_t)d.field_off * sizeof(float);
+    if (w_off) *w_off = (size_t)d.w_off;
+    if (gh_off) *gh_off = (size_t)d.gh_off;
+    return ITC_OK;
+}
+
+int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
+            size_t ws_bytes, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
+    const ImageDesc* descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
+    const int* ints = reinterpret_cast<const int*>(pd + h->ints_off);
+    unsigned char* w = reinterpret_cast<unsigned char*>(ws);
+    float* fields = reinterpret_cast<float*>(w + h->ws_fields_off);
+    double* partials = reinterpret_cast<double*>(w + h->ws_partials_off);
+    for (int c = 0; c < h->ncls; ++c) {
+        const ClassInfo& ci = h->cls[c];
+        FieldsLaunch L;
+        memset(&L, 0, sizeof(L));
+        L.taps = ci.taps;
+        L.descs = descs;
+        L.img_list = ints + ci.list_off;
+        L.tile_prefix = ints + ci.prefix_off;
+        L.nimg = ci.nimg;
+        L.fields = fields;
+        L.partials = partials;
+        L.tile_h = ci.tile_h;
+        L.absolute = 0;
+        int rc = cuda_status(launch_fields(L, ci.ntiles, ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
+        if (rc) return rc;
+    }
+    RunLaunch R;
+    memset(&R, 0, sizeof(R));
+    R.descs = descs;
+    R.fields = fields;
+    R.partials = partials;
+    R.W_in = W;
+    R.W_out = W;
+    R.stats = stats;
+    R.absolute = 0;
+    R.final_eval = 1;
+    return cuda_status(launch_run(R, h->B, h->max_M, 0, s));
+}
+
+int itc_backward(const void* plan_host, const void* plan_dev, const float* W, const float* grad_dcs,
+                 float* grad_W, float* grad_h, itc_stats* stats, void* ws, size_t ws_bytes, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
+    unsigned char* w = reinterpret_cast<unsigned char*>(ws);
+    BackwardLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
+    L.fields = reinterpret_cast<const float*>(w + h->ws_fields_off);
+    L.partials = reinterpret_cast<const double*>(w + h->ws_partials_off);
+    L.W = W;
+    L.grad_dcs = grad_dcs;
+    L.grad_W = grad_W;
+    L.grad_h = grad_h;
+    L.stats = stats;
+    L.scal = reinterpret_cast<double*>(w + h->ws_scal_off);
+    L.bwd_prefix = reinterpret_cast<const int*>(pd + h->ints_off) + h->bwd_prefix_off;
+    L.B = h->B;
+    return cuda_status(launch_backward(L, h->B, h->max_M, h->bwd_tiles,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,286 @@
+// itc_backward.cu -- gradient of the Cauchy-Schwarz divergence, Eq. (1), with respect to the
+// codebook and to the per-pixel weights of weighted ITC (Sec. 5).
+//
+//   dD/dw_{k,i} = (2 / sigma_i^2) (E_{k,i} / S_WW - D_{k,i} / S_XW)
+//   dD/dh(x)    = 2 A(x) / S_XX - (2 / S_XW) sum_k g(x - w_k) [x in box(round(w_k))]
+//
+// Kernel 1 (one CTA per image): window sums a_k, D_k around round(w_k) read directly from the
+// image (kernel evaluated at the real w_k, one warp per k), the M x M sums s_k, E_k (one warp
+// per k, xor-shuffle reduction), S_XW, S_WW, grad_W and two per-image scalars for kernel 2.
+// Kernel 2 (one CTA per 16 x 64 pixel tile): the codebooks whose box meets the tile are listed
+// in k order (ballot compaction, so the per-pixel sums are deterministic), then every pixel
+// combines the stored field A with the stamp of the listed codebook Gaussians -- the transposed
+// form of the gather in the forward update.
+#include <math.h>
+
+#include "itc_internal.cuh"
+
+namespace itc {
+namespace {
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int lattice_round_i(float x, int n) {
+    float r = floorf(x + 0.5f);
+    return (int)fminf(fmaxf(r, 0.f), (float)(n - 1));
+}
+__device__ __forceinline__ float pixel_weight(const ImageDesc& D, int u, int v) {
+    const size_t o = (size_t)u * D.pitch + v;
+    if (D.ndim == 3) return D.weight ? __ldg(D.weight + o) : 1.f;
+    if (D.dtype == ITC_U8) return (float)__ldg(reinterpret_cast<const unsigned char*>(D.data) + o);
+    return __ldg(reinterpret_cast<const float*>(D.data) + o);
+}
+__device__ __forceinline__ int pixel_gray(const ImageDesc& D, int u, int v) {
+    return (int)__ldg(reinterpret_cast<const unsigned char*>(D.data) + (size_t)u * D.pitch + v);
+}
+
+__global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_constant__ BackwardLaunch L) {
+    const ImageDesc& D = L.descs[blockIdx.x];
+    const int M = D.M, nd = D.ndim, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    extern __shared__ __align__(16) float sm[];
+    float* sw = sm;
+    float* sa = sw + 3 * M;
+    float* sD = sa + M;
+    float* ss = sD + 3 * M;
+    float* sE = ss + M;
+    __shared__ double red[4];
+
+    if (tid < 32) {
+        const long long nt = (long long)D.tiles_u * D.tiles_v * D.tiles_g;
+        double v = 0;
+        for (long long i = tid; i < nt; i += 32) v += L.partials[D.partial_off + i];
+        v = warp_sum_d(v);
+        if (tid == 0) red[3] = v;
+    }
+    const float* Wk = L.W + D.w_off;
+    for (int k = tid; k < M; k += blockDim.x)
+        for (int i = 0; i < 3; ++i) sw[k * 3 + i] = i < nd ? Wk[k * nd + i] : 0.f;
+    __syncthreads();
+    const double sxx = red[3];
+    const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
+    const int Ru = D.R[0], Rv = D.R[1], Rg = D.R[2];
+
+    // window sums at the real w_k over the box around round(w_k)
+    for (int k = wid; k < M; k += nw) {
+        const float w0 = sw[k * 3], w1 = sw[k * 3 + 1], w2 = sw[k * 3 + 2];
+        const int r0 = lattice_round_i(w0, D.H), r1 = lattice_round_i(w1, D.W);
+        const int r2 = nd == 3 ? lattice_round_i(w2, D.G) : 0;
+        const int ua = max(0, r0 - Ru), ub = min(D.H - 1, r0 + Ru);
+        const int va = max(0, r1 - Rv), vb = min(D.W - 1, r1 + Rv);
+        const int nv = vb - va + 1, npos = (ub - ua + 1) * nv;
+        float a = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+        for (int p = lane; p < npos; p += 32) {
+            const int u = ua + p / nv, v = va + p % nv;
+            const float h = pixel_weight(D, u, v);
+            if (h == 0.f) continue;
+            const float du = (float)u - w0, dv = (float)v - w1;
+            float dg = 0.f;
+            if (nd == 3) {
+                const int gl = pixel_gray(D, u, v);
+                if (abs(gl - r2) > Rg) continue;
+                dg = (float)gl - w2;
+            }
+            const float g = h * expf(-(du * du * c0 + dv * dv * c1 + dg * dg * c2));
+            a += g;
+            d0 = fmaf(g, du, d0);
+            d1 = fmaf(g, dv, d1);
+            d2 = fmaf(g, dg, d2);
+        }
+        a = warp_sum_f(a);
+        d0 = warp_sum_f(d0);
+        d1 = warp_sum_f(d1);
+        d2 = warp_sum_f(d2);
+        if (lane == 0) {
+            sa[k] = a;
+            sD[k * 3] = d0;
+            sD[k * 3 + 1] = d1;
+            sD[k * 3 + 2] = d2;
+        }
+    }
+    // codebook interaction sums
+    for (int k = wid; k < M; k += nw) {
+        const float wk0 = sw[k * 3], wk1 = sw[k * 3 + 1], wk2 = sw[k * 3 + 2];
+        float s = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
+        for (int j = lane; j < M; j += 32) {
+            const float d0 = sw[j * 3] - wk0, d1 = sw[j * 3 + 1] - wk1;
+            const float d2 = nd == 3 ? sw[j * 3 + 2] - wk2 : 0.f;
+            const float g = expf(-(d0 * d0 * c0 + d1 * d1 * c1 + d2 * d2 * c2));
+            s += g;
+            e0 = fmaf(g, d0, e0);
+            e1 = fmaf(g, d1, e1);
+            e2 = fmaf(g, d2, e2);
+        }
+        s = warp_sum_f(s);
+        e0 = warp_sum_f(e0);
+        e1 = warp_sum_f(e1);
+        e2 = warp_sum_f(e2);
+        if (lane == 0) {
+            ss[k] = s;
+            sE[k * 3] = e0;
+            sE[k * 3 + 1] = e1;
+            sE[k * 3 + 2] = e2;
+        }
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double x = 0, y = 0;
+        int e = 0;
+        for (int k = lane; k < M; k += 32) {
+            x += (double)sa[k];
+            y += (double)ss[k];
+            e += !(sa[k] > 0.f);
+        }
+        x = warp_sum_d(x);
+        y = warp_sum_d(y);
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (lane == 0) {
+            red[0] = x;
+            red[1] = y;
+            red[2] = (double)e;
+        }
+    }
+    __syncthreads();
+    const double sxw = red[0], sww = red[1];
+    const double gD = L.grad_dcs ? (double)L.grad_dcs[blockIdx.x] : 1.0;
+    if (L.grad_W) {
+        float* gW = L.grad_W + D.w_off;
+        for (int k = tid; k < M; k += blockDim.x)
+            for (int i = 0; i < nd; ++i) {
+                const double s2 = (double)D.sigma[i] * (double)D.sigma[i];
+                gW[k * nd + i] = (float)(gD * 2.0 / s2 * ((double)sE[k * 3 + i] / sww - (double)sD[k * 3 + i] / sxw));
+            }
+    }
+    if (tid == 0) {
+        L.scal[blockIdx.x * 4 + 0] = 2.0 * gD / sxx;
+        L.scal[blockIdx.x * 4 + 1] = 2.0 * gD / sxw;
+        if (L.stats) {
+            itc_stats r;
+            r.sxw = sxw;
+            r.sww = sww;
+            r.sxx = sxx;
+            r.c = sxw / sww;
+            r.dcs = sxw > 0 ? log(sww) + log(sxx) - 2.0 * log(sxw) : INFINITY;
+            r.empty = (int)red[2];
+            r.moved = 0;
+            r.iters_done = 0;
+            r.status = !(sxw > 0) || !isfinite(r.dcs) ? ITC_ERR_NONFINITE
+                       : (r.empty > 0 ? ITC_WARN_EMPTY_SUPPORT : ITC_OK);
+            L.stats[blockIdx.x] = r;
+        }
+    }
+}
+
+__device__ __forceinline__ int find_image(const int* __restrict__ prefix, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_constant__ BackwardLaunch L) {
+    const int img = find_image(L.bwd_prefix, L.B + 1, blockIdx.x);
+    const ImageDesc& D = L.descs[img];
+    const int t = blockIdx.x - __ldg(L.bwd_prefix + img);
+    const int u0 = (t / D.bwd_tiles_v) * kBwdTileH, v0 = (t % D.bwd_tiles_v) * kBwdTileW;
+    const int M = D.M, nd = D.ndim, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int Ru = D.R[0], Rv = D.R[1], Rg = D.R[2];
+    extern __shared__ __align__(16) float sm[];
+    float* lw = sm;                                   // listed real positions, 3 per entry
+    int* lr = reinterpret_cast<int*>(lw + 3 * M);     // listed rounded positions, 3 per entry
+    __shared__ int wcount[kThreads / 32];
+    __shared__ int s_total;
+    const float* Wk = L.W + D.w_off;
+
+    // stable compaction of the codebooks whose box meets this tile
+    int total = 0;
+    for (int base = 0; base < M; base += blockDim.x) {
+        const int k = base + tid;
+        bool hit = false;
+        float w[3] = {0.f, 0.f, 0.f};
+        int r[3] = {0, 0, 0};
+        if (k < M) {
+            for (int i = 0; i < nd; ++i) w[i] = Wk[k * nd + i];
+            r[0] = lattice_round_i(w[0], D.H);
+            r[1] = lattice_round_i(w[1], D.W);
+            if (nd == 3) r[2] = lattice_round_i(w[2], D.G);
+            hit = (r[0] + Ru >= u0) && (r[0] - Ru <= u0 + kBwdTileH - 1) &&
+                  (r[1] + Rv >= v0) && (r[1] - Rv <= v0 + kBwdTileW - 1);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wcount[wid] = __popc(bal);
+        __syncthreads();
+        int off = total;
+        for (int q = 0; q < wid; ++q) off += wcount[q];
+        if (hit) {
+            const int pos = off + __popc(bal & ((1u << lane) - 1u));
+            for (int i = 0; i < 3; ++i) {
+                lw[pos * 3 + i] = w[i];
+                lr[pos * 3 + i] = r[i];
+            }
+        }
+        int add = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) add += wcount[q];
+        total += add;
+        __syncthreads();
+    }
+    if (tid == 0) s_total = total;
+    __syncthreads();
+    const int nl = s_total;
+    const double s1 = L.scal[img * 4 + 0], s2 = L.scal[img * 4 + 1];
+    const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
+    const float* A = L.fields + D.field_off;
+    const int v = v0 + (tid & 63);
+    for (int q = tid >> 6; q < kBwdTileH; q += kThreads / 64) {
+        const int u = u0 + q;
+        if (u >= D.H || v >= D.W) continue;
+        int gl = 0;
+        long long o = (long long)u * D.fpitch + v;
+        if (nd == 3) {
+            gl = pixel_gray(D, u, v);
+            if (gl >= D.G) {   // a voxel outside the lattice: no field value
+                L.grad_h[D.gh_off + (long long)u * D.W + v] = 0.f;
+                continue;
+            }
+            o += (long long)gl * D.H * D.fpitch;
+        }
+        const float a = __ldg(A + o);
+        float st = 0.f;
+        for (int l = 0; l < nl; ++l) {
+            if (abs(u - lr[l * 3]) > Ru || abs(v - lr[l * 3 + 1]) > Rv) continue;
+            if (nd == 3 && abs(gl - lr[l * 3 + 2]) > Rg) continue;
+            const float du = (float)u - lw[l * 3], dv = (float)v - lw[l * 3 + 1];
+            const float dg = nd == 3 ? (float)gl - lw[l * 3 + 2] : 0.f;
+            st += expf(-(du * du * c0 + dv * dv * c1 + dg * dg * c2));
+        }
+        L.grad_h[D.gh_off + (long long)u * D.W + v] = (float)(s1 * (double)a - s2 * (double)st);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles,
+                            cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    const size_t smem1 = (size_t)max_M * 9 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(bwd_codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+    if (e != cudaSuccess) return e;
+    bwd_codebook_kernel<<<B, kRunThreads, smem1, s>>>(L);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !L.grad_h || pixel_tiles <= 0) return e;
+    const size_t smem2 = (size_t)max_M * 6 * sizeof(float);
+    e = cudaFuncSetAttribute(bwd_pixels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
+    bwd_pixels_kernel<<<(unsigned)pixel_tiles, kThreads, smem2, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace itc

@@ -1,0 +1,149 @@
+// itc_internal.cuh -- layouts shared by the kernels and the host side of libitc.so.
+// Nothing here is part of the public ABI (include/itc.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "itc.h"
+
+namespace itc {
+
+constexpr int kMaxTapsUV = 2 * ITC_MAX_RADIUS_UV + 1;
+constexpr int kMaxTapsG = 2 * ITC_MAX_RADIUS_G + 1;
+constexpr int kMaxClasses = 16;     // distinct (sigma, trunc, flags, ndim, dtype) classes per plan
+constexpr int kThreads = 256;       // fields / backward CTA size
+constexpr int kTileW = 64;          // output columns per fields tile
+constexpr int kRunThreads = 256;    // codebook-iteration CTA size
+
+// Truncated, unnormalised 1-D Gaussian taps of one parameter class, computed on the host in
+// double and rounded once to float:  g[d + R] = exp(-d^2 / (2 sigma^2)),  dg[d + R] = d g[d + R].
+struct Taps {
+    float gu[kMaxTapsUV], dgu[kMaxTapsUV];
+    float gv[kMaxTapsUV], dgv[kMaxTapsUV];
+    float gg[kMaxTapsG], dgg[kMaxTapsG];
+    float sigma[3];
+    float inv2s2[3];   // 1 / (2 sigma_i^2)
+    int R[3];
+};
+
+// One image as the kernels see it (device-resident inside a plan, or passed by value).
+struct ImageDesc {
+    const void* data;
+    const float* weight;
+    int ndim, H, W, G, pitch, dtype;
+    int fpitch;                 // field row pitch in floats
+    int M;
+    int cls;                    // parameter class
+    int iters, flags;
+    float step_scale;
+    int tiles_u, tiles_v, tiles_g;   // fields tile grid of this image
+    int tile_begin;             // first tile of this image inside its class launch
+    long long partial_off;      // first S_XX partial (doubles) of this image
+    long long field_off;        // offset of plane 0 in floats (from the fields base)
+    long long plane_floats;     // floats per plane = G * H * fpitch
+    long long w_off;            // offset of the image's codebooks, in floats (codebook * ndim)
+    long long gh_off;           // offset of the image's grad_h, in floats
+    int bwd_tile_begin;         // first tile of this image in the backward pixel pass
+    int bwd_tiles_u, bwd_tiles_v;
+    float sigma[3];
+    float inv2s2[3];            // 1 / (2 sigma_i^2)
+    int R[3];
+};
+
+struct ClassInfo {
+    Taps taps;
+    int ndim, dtype, absolute, tile_h;
+    int nimg, ntiles;
+    int list_off;               // offset (ints) of this class's image list in the plan int area
+    int prefix_off;             // offset (ints) of the class tile prefix (nimg + 1 ints)
+    long long partial_base;     // first partial of the class
+};
+
+struct PlanHeader {
+    uint32_t magic;
+    int B;
+    int ncls;
+    int max_M;
+    long long total_pixels;     // sum H*W (grad_h layout)
+    long long fields_floats;    // sum of every image's field planes
+    long long total_tiles;
+    long long ws_fields_off;    // bytes
+    long long ws_partials_off;  // bytes
+    long long ws_bytes;
+    long long desc_off;         // bytes from plan start to ImageDesc[B]
+    long long ints_off;         // bytes from plan start to the int area
+    long long nints;
+    long long ws_scal_off;      // bytes: per-image backward scalars (4 doubles each)
+    long long bwd_tiles;        // backward pixel tiles over all images
+    int bwd_prefix_off;         // offset (ints) of the backward tile prefix (B + 1 ints)
+    ClassInfo cls[kMaxClasses];
+};
+
+constexpr uint32_t kPlanMagic = 0x49544350u;  // "ITCP"
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Tile height of the fields kernels for a given radius (rows of outputs per CTA).
+inline int default_tile_h(int ndim, int Ru) {
+    if (ndim == 3) return 32;
+    return Ru <= 6 ? 64 : 64;
+}
+
+// Kernel launch records (passed by value as __grid_constant__ parameters).
+struct FieldsLaunch {
+    Taps taps;
+    const ImageDesc* descs;     // plan descriptors (batched) or nullptr (single image)
+    ImageDesc one;              // the single image when descs == nullptr
+    const int* img_list;        // class image list (batched)
+    const int* tile_prefix;     // class tile prefix (batched, nimg + 1)
+    int nimg;
+    float* fields;              // fields base
+    double* partials;           // S_XX partial base
+    int tile_h;
+    int absolute;
+};
+
+struct RunLaunch {
+    const ImageDesc* descs;
+    ImageDesc one;
+    const float* fields;
+    const double* partials;
+    const double* sxx_single;   // single-image S_XX (itc_step) or nullptr
+    const float* W_in;
+    float* W_out;
+    int* W_lattice;
+    itc_stats* stats;
+    int absolute;
+    int final_eval;             // 1: stats at the final W (itc_run); 0: stats at W_in (itc_step)
+};
+
+struct BackwardLaunch {
+    const ImageDesc* descs;
+    const float* fields;
+    const double* partials;
+    const float* W;
+    const float* grad_dcs;
+    float* grad_W;
+    float* grad_h;
+    itc_stats* stats;
+    double* scal;               // per-image scalars in workspace: S_XW, S_WW, S_XX, gD
+    const int* bwd_prefix;      // B + 1 prefix of backward pixel tiles
+    int B;
+};
+
+constexpr int kBwdTileH = 16;   // backward pixel tile: 16 rows x 64 columns
+constexpr int kBwdTileW = 64;
+constexpr int kGSlices = 8;     // 3-D fields: gray slices per CTA
+
+}  // namespace itc
+
+// Kernel entry points (defined in the .cu files, launched from itc_api.cu).
+namespace itc {
+cudaError_t launch_fields(const FieldsLaunch& L, int nblocks, int R_u, int R_v, int ndim, int dtype,
+                          cudaStream_t s);
+cudaError_t launch_reduce_sxx(const double* partials, int n, double* out, cudaStream_t s);
+cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, int iters_cap, cudaStream_t s);
+cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles,
+                            cudaStream_t s);
+}  // namespace itc

@@ -1,0 +1,155 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every function
+include/itc.h declares, and rejects invalid arguments before touching the device; batch plans
+(host-only) lay out offsets as documented."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1310_7114_gb300 import build as itc_build
+from paper_1310_7114_gb300 import itc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    itc_build.build()
+    return itc.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "itc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(itc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(itc.EXPORTS) == names
+
+
+def test_struct_sizes_match_the_header():
+    assert ctypes.sizeof(itc.ItcImage) == 40
+    assert ctypes.sizeof(itc.ItcParams) == 28
+    assert ctypes.sizeof(itc.ItcStats) == 56
+
+
+def test_queries(L):
+    assert L.itc_field_pitch(1) == 4 and L.itc_field_pitch(64) == 64 and L.itc_field_pitch(65) == 68
+    img = itc.ItcImage(2, 100, 70, 1, 80, itc.ITC_U8, 0x1000, None)
+    assert L.itc_fields_bytes(ctypes.byref(img)) == 3 * 100 * 72 * 4
+    img3 = itc.ItcImage(3, 10, 12, 256, 12, itc.ITC_U8, 0x1000, None)
+    assert L.itc_fields_bytes(ctypes.byref(img3)) == 4 * 256 * 10 * 12 * 4
+    bad = itc.ItcImage(2, 100, 70, 1, 60, itc.ITC_U8, 0x1000, None)  # pitch < W
+    assert L.itc_fields_bytes(ctypes.byref(bad)) == 0
+    for c in (0, 1, -1, -2, -3, -4, -5, -6, 99):
+        assert isinstance(L.itc_status_string(c), bytes)
+
+
+def _p(sigma=2.0, trunc=3.0, iters=0, step=1.0, flags=0):
+    return itc.make_params(sigma, trunc, iters, step, flags)
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda i, p: setattr(i, "data", None), itc.ITC_ERR_INVALID_ARG),
+    (lambda i, p: setattr(i, "ndim", 4), itc.ITC_ERR_INVALID_ARG),
+    (lambda i, p: setattr(i, "H", 0), itc.ITC_ERR_INVALID_ARG),
+    (lambda i, p: setattr(i, "dtype", 7), itc.ITC_ERR_INVALID_ARG),
+    (lambda i, p: setattr(p, "trunc", 0.0), itc.ITC_ERR_INVALID_ARG),
+    (lambda i, p: setattr(p, "trunc", float("nan")), itc.ITC_ERR_INVALID_ARG),
+    (lambda i, p: p.sigma.__setitem__(0, -1.0), itc.ITC_ERR_INVALID_ARG),
+    (lambda i, p: setattr(p, "flags", 64), itc.ITC_ERR_INVALID_ARG),
+    (lambda i, p: p.sigma.__setitem__(1, 40.0), itc.ITC_ERR_UNSUPPORTED),
+])
+def test_fields_rejects_invalid_arguments_without_launching(L, mutate, code):
+    img = itc.ItcImage(2, 64, 64, 1, 64, itc.ITC_U8, 0x1000, None)
+    p = _p()
+    mutate(img, p)
+    rc = L.itc_fields(ctypes.byref(img), ctypes.byref(p), 0x2000, None, 0x3000, 1 << 20, None)
+    assert rc == code
+
+
+def test_fields_workspace_checks(L):
+    img = itc.ItcImage(2, 64, 64, 1, 64, itc.ITC_U8, 0x1000, None)
+    p = _p()
+    need = L.itc_fields_workspace_bytes(ctypes.byref(img))
+    assert need > 0
+    assert L.itc_fields(ctypes.byref(img), ctypes.byref(p), 0x2000, None, None, need, None) == itc.ITC_ERR_WORKSPACE
+    assert L.itc_fields(ctypes.byref(img), ctypes.byref(p), 0x2000, None, 0x3000, need - 8, None) == itc.ITC_ERR_WORKSPACE
+    assert L.itc_fields(ctypes.byref(img), ctypes.byref(p), 0x2004, None, 0x3000, need, None) == itc.ITC_ERR_INVALID_ARG
+
+
+def test_step_rejects_bad_codebook_sizes(L):
+    img = itc.ItcImage(2, 64, 64, 1, 64, itc.ITC_U8, 0x1000, None)
+    p = _p(iters=1)
+    for M in (0, -3, 5000):
+        assert L.itc_step(ctypes.byref(img), ctypes.byref(p), 0x2000, 0x3000, M, 0x4000, 0x5000, None, None,
+                          None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_step(ctypes.byref(img), ctypes.byref(p), 0x2000, None, 8, 0x4000, 0x5000, None, None,
+                      None) == itc.ITC_ERR_INVALID_ARG
+
+
+def _plan(L, shapes, Ms, params, ndims=None):
+    B = len(shapes)
+    ndims = ndims or [2] * B
+    imgs = (itc.ItcImage * B)(*[itc.ItcImage(d, h, w, 256 if d == 3 else 1, w + 3, itc.ITC_U8, 0x10000 * (b + 1), None)
+                                for b, ((h, w), d) in enumerate(zip(shapes, ndims))])
+    M = (ctypes.c_int * B)(*Ms)
+    if isinstance(params, list):
+        ps, stride = (itc.ItcParams * B)(*params), 1
+    else:
+        ps, stride = (itc.ItcParams * 1)(params), 0
+    nb = L.itc_plan_bytes(B)
+    buf = ctypes.create_string_buffer(nb)
+    ws = ctypes.c_size_t(0)
+    rc = L.itc_plan(B, imgs, M, ps, stride, ctypes.cast(buf, ctypes.c_void_p), nb, ctypes.byref(ws))
+    return rc, buf, ws.value
+
+
+def test_plan_layout(L):
+    shapes = [(64, 64), (100, 70), (300, 513), (17, 9)]
+    Ms = [8, 16, 128, 3]
+    rc, buf, ws = _plan(L, shapes, Ms, [_p(2.0), _p(3.0), _p(2.0), _p(4.0)])
+    assert rc == 0
+    assert L.itc_plan_pixels(ctypes.cast(buf, ctypes.c_void_p)) == sum(h * w for h, w in shapes)
+    # workspace holds at least the fields of every image (3 planes, rows padded to 4 floats)
+    assert ws >= sum(3 * h * ((w + 3) // 4 * 4) * 4 for h, w in shapes)
+    assert ws % 256 == 0
+
+
+def test_plan_rejects_invalid_batches(L):
+    assert _plan(L, [(64, 64)], [0], _p())[0] == itc.ITC_ERR_INVALID_ARG
+    assert _plan(L, [(64, 64)], [4096], _p())[0] == itc.ITC_ERR_INVALID_ARG
+    assert _plan(L, [(64, 64), (32, 32)], [8, 8], [_p(), _p(trunc=-1.0)])[0] == itc.ITC_ERR_INVALID_ARG
+    # more parameter classes than a plan holds
+    shapes = [(32, 32)] * 20
+    rc = _plan(L, shapes, [4] * 20, [_p(1.0 + 0.1 * i) for i in range(20)])[0]
+    assert rc == itc.ITC_ERR_UNSUPPORTED
+    nb = L.itc_plan_bytes(1)
+    assert nb > 0 and L.itc_plan_bytes(0) == 0
+
+
+def test_run_rejects_bad_plan_and_workspace(L):
+    rc, buf, ws = _plan(L, [(64, 64)], [8], _p(iters=5))
+    assert rc == 0
+    bogus = ctypes.create_string_buffer(len(buf.raw))
+    assert L.itc_run(ctypes.cast(bogus, ctypes.c_void_p), 0x1000, 0x2000, None, 0x4000, ws, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_run(ctypes.cast(buf, ctypes.c_void_p), 0x1000, 0x2000, None, 0x4000, ws - 1, None) == itc.ITC_ERR_WORKSPACE
+    assert L.itc_run(ctypes.cast(buf, ctypes.c_void_p), 0x1000, 0x2000, None, 0x4010, ws, None) == itc.ITC_ERR_WORKSPACE
+    assert L.itc_backward(ctypes.cast(buf, ctypes.c_void_p), 0x1000, 0x2000, None, None, None, None, None, ws,
+                          None) == itc.ITC_ERR_WORKSPACE
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The package never imports the oracle, and the binding fails loudly without the library."""
+    pkg = os.path.join(ROOT, "paper_1310_7114_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            src = open(os.path.join(pkg, f)).read()
+            assert "import oracle" not in src and "from oracle" not in src, f

@@ -1,0 +1,115 @@
+"""GPU parity of the lattice fields (Sec. 3.1, Sec. 5): itc_fields vs the FP64 oracle,
+element by element, over tile-spanning sizes with ragged tails, every compiled radius and the
+runtime-radius path, binary and weighted inputs, centred and absolute moments, and the edge
+cases (1x1, single rows/columns, images smaller than the mask, empty and full images)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpuhelp import assert_fields_close, radii, to_dev
+from paper_1310_7114_gb300 import build, itc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    itc.lib()
+
+
+def gpu_fields(h, sigma, trunc=3.0, absolute=False, pad=0):
+    import torch
+    if pad:
+        buf, views = itc.pack_images([h], "cuda", align=pad)
+        t = views[0]
+    else:
+        t = to_dev(h)
+    F, sxx = itc.fields(t, sigma, trunc, absolute)
+    torch.cuda.synchronize()
+    W = h.shape[1]
+    return [F[i, 0, :, :W].cpu().numpy().astype(np.float64) for i in range(3)], float(sxx.item())
+
+
+def check(h, sigma, trunc=3.0, absolute=False, pad=0, what=""):
+    g, sxx = gpu_fields(h, sigma, trunc, absolute, pad)
+    ref = oracle.fields2d(h.astype(np.float64), sigma, trunc, absolute)
+    assert_fields_close(g, ref, radii(sigma, trunc), absolute, what)
+    ref_sxx = oracle.sxx(h.astype(np.float64), ref[0]) if not absolute else None
+    if ref_sxx is not None:
+        assert abs(sxx - ref_sxx) <= 1e-5 * ref_sxx + 1e-30, (sxx, ref_sxx)
+    return g, ref
+
+
+def _binary(rng, H, W, p):
+    return (rng.random((H, W)) < p).astype(np.uint8)
+
+
+CASES = {
+    "c1_sigma2": lambda: (synth.c1_image(0), 2.0),
+    "binary_150x97_sigma3": lambda: (_binary(np.random.default_rng(1), 150, 97, 0.2), 3.0),
+    "binary_130x300_sigma4": lambda: (_binary(np.random.default_rng(2), 130, 300, 0.15), 4.0),
+    "weights_96x200_sigma3": lambda: (synth.c4_weights(0)[:96, :200], 3.0),
+    "anisotropic_runtime_radius": lambda: (_binary(np.random.default_rng(3), 80, 90, 0.3), (1.5, 2.5)),
+    "sigma1_runtime_radius": lambda: (_binary(np.random.default_rng(4), 70, 140, 0.3), 1.0),
+    "sigma_10_wide_runtime": lambda: (_binary(np.random.default_rng(5), 90, 100, 0.05), 10.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fields_centred(name):
+    h, s = CASES[name]()
+    check(h, s, what=name)
+
+
+@pytest.mark.parametrize("name", ["c1_sigma2", "weights_96x200_sigma3", "binary_130x300_sigma4", "anisotropic_runtime_radius"])
+def test_fields_absolute(name):
+    h, s = CASES[name]()
+    check(h, s, absolute=True, what=name)
+
+
+def test_fields_with_row_pitch():
+    h = _binary(np.random.default_rng(6), 70, 77, 0.25)
+    check(h, 2.0, pad=32, what="pitched rows")
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 70), (70, 1), (5, 5), (13, 200), (200, 13), (65, 65), (64, 128)])
+def test_edge_shapes(shape):
+    rng = np.random.default_rng(sum(shape))
+    h = _binary(rng, *shape, 0.4)
+    h.flat[0] = 1
+    check(h, 3.0, what=str(shape))
+
+
+def test_empty_image_is_exactly_zero():
+    h = np.zeros((100, 130), np.uint8)
+    g, sxx = gpu_fields(h, 3.0)
+    assert all(np.all(x == 0) for x in g) and sxx == 0.0
+
+
+def test_full_image():
+    check(np.ones((77, 66), np.uint8), 4.0, what="all ones")
+
+
+def test_c2_full_size_sampled_sites():
+    """C2 at full size (1024^2, sigma 4): 4000 random sites plus two whole 64x64 windows."""
+    img = synth.c2_image(0)
+    g, sxx = gpu_fields(img, 4.0)
+    rng = np.random.default_rng(0)
+    sites = np.stack([rng.integers(0, 1024, 4000), rng.integers(0, 1024, 4000)], 1)
+    win = np.stack(np.meshgrid(np.arange(500, 564), np.arange(960, 1024), indexing="ij"), -1).reshape(-1, 2)
+    win2 = np.stack(np.meshgrid(np.arange(0, 64), np.arange(0, 64), indexing="ij"), -1).reshape(-1, 2)
+    sites = np.concatenate([sites, win, win2])
+    ref = oracle.fields2d_sites(img.astype(np.float64), 4.0, sites)
+    gs = [x[sites[:, 0], sites[:, 1]] for x in g]
+    assert_fields_close(gs, ref, [12, 12], False, "C2 sites")
+    A_ref = oracle.fields2d(img.astype(np.float64), 4.0)[0]
+    ref_sxx = oracle.sxx(img.astype(np.float64), A_ref)
+    assert abs(sxx - ref_sxx) <= 1e-5 * ref_sxx
+
+
+def test_fields_are_deterministic():
+    h = synth.c2_image(0, size=512)
+    a, s1 = gpu_fields(h, 3.0)
+    b, s2 = gpu_fields(h, 3.0)
+    assert s1 == s2 and all(np.array_equal(x, y) for x, y in zip(a, b))

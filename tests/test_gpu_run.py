@@ -1,0 +1,200 @@
+"""GPU parity of the fixed-point iteration (Algorithm 1 with Eq. (origupdate)): itc_step and the
+batched itc_run vs the FP64 oracle.
+
+Bar: one step from identical W gives identical lattice positions except coordinates whose
+oracle value lies within 1e-4 of a half-integer; final codebooks are identical when the
+oracle's trajectory has no such tie, otherwise every iteration is checked in lockstep (the GPU
+step from the oracle's W).  D_cs and the sums agree to the derived FP32 bound."""
+import numpy as np
+import pytest
+
+import oracle
+from gpuhelp import DCS_ATOL, assert_lattice_equal_except_ties, to_dev
+from paper_1310_7114_gb300 import build, itc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    itc.lib()
+
+
+def _oracle_fields(h, sigma):
+    A, Fu, Fv = oracle.fields2d(h.astype(np.float64), sigma)
+    return A, [Fu, Fv], oracle.sxx(h.astype(np.float64), A)
+
+
+def gpu_step(h, sigma, W, step_scale=1.0, flags=0, F=None):
+    import torch
+    t = to_dev(h)
+    if F is None:
+        F = itc.fields(t, sigma)
+    Wo, Wl, st = itc.step(t, F[0], F[1], to_dev(np.asarray(W, np.float32)), sigma, 3.0, step_scale, flags)
+    torch.cuda.synchronize()
+    return Wo.cpu().numpy(), Wl.cpu().numpy(), itc.stats_to_numpy(st)[0], F
+
+
+def lockstep(h, sigma, W0, iters, F_ref):
+    """Every iteration: GPU step from the oracle's W must match the oracle's next W (ties aside)."""
+    A, F, sxx = F_ref
+    W = np.asarray(W0, np.float64)
+    Fg = None
+    ties = 0
+    for _ in range(iters):
+        Wn, raw, _ = oracle.lattice_step(A, F, sigma, W)
+        Wg, _, _, Fg = gpu_step(h, sigma, W, F=Fg)
+        ties += assert_lattice_equal_except_ties(Wg, Wn, raw, what="lockstep")
+        W = Wn
+    return ties
+
+
+def run_plan(images, Ms, W0s, params, ndims=None, Gs=None, weights=None):
+    import torch
+    ts = [to_dev(im) for im in images]
+    plan = itc.Plan(ts, Ms, params, ndims=ndims, Gs=Gs, weights=weights)
+    W = plan.pack_W(W0s)
+    st = itc.new_stats(len(images), W.device)
+    itc.run(plan, W, st)
+    torch.cuda.synchronize()
+    return plan, plan.unpack_W(W), itc.stats_to_numpy(st)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_single_step_c1(seed):
+    img = synth.c1_image(seed)
+    W0 = synth.init_codebook(synth.rng_for(1, seed), img.astype(np.float32), 8)
+    A, F, sxx = _oracle_fields(img, 2.0)
+    Wn, raw, st = oracle.lattice_step(A, F, 2.0, W0)
+    Wg, Wl, s, _ = gpu_step(img, 2.0, W0)
+    assert_lattice_equal_except_ties(Wg, Wn, raw, what=f"seed {seed}")
+    assert np.array_equal(Wl, Wg.astype(np.int32))
+    assert abs(s["sxw"] - st["sxw"]) <= 1e-5 * st["sxw"]
+    assert abs(s["sww"] - st["sww"]) <= 1e-5 * st["sww"]
+    d_ref = np.log(st["sww"]) + np.log(sxx) - 2 * np.log(st["sxw"])
+    assert abs(s["dcs"] - d_ref) <= DCS_ATOL
+    assert s["moved"] == st["moved"]
+
+
+def test_single_step_continuous_and_half_step():
+    img = synth.c1_image(1)
+    rng = synth.rng_for(1, 1)
+    W0 = synth.init_codebook(rng, img.astype(np.float32), 8) + rng.uniform(-0.4, 0.4, (8, 2)).astype(np.float32)
+    W0 = W0.astype(np.float32)
+    A, F, _ = _oracle_fields(img, 2.0)
+    for scale in (1.0, 0.5):
+        _, raw, _ = oracle.lattice_step(A, F, 2.0, W0.astype(np.float64), step_scale=scale, snap=False)
+        Wg, _, _, _ = gpu_step(img, 2.0, W0, step_scale=scale, flags=itc.ITC_CONTINUOUS)
+        ref = np.clip(raw, 0, 63)
+        # FP32 fields and sums: a step of (D - cE)/a carries ~1e-5 relative error of the moment
+        # window (|D| <= R a), so positions agree to 1e-5 R = 6e-5 px; stored as float32.
+        np.testing.assert_allclose(Wg, ref, rtol=0, atol=1e-4)
+
+
+def test_step_with_absolute_fields_matches():
+    import torch
+    img = synth.c1_image(2)
+    W0 = synth.init_codebook(synth.rng_for(1, 2), img.astype(np.float32), 8)
+    A, F, _ = _oracle_fields(img, 2.0)
+    Wn, raw, _ = oracle.lattice_step(A, F, 2.0, W0)
+    t = to_dev(img)
+    Fa = itc.fields(t, 2.0, absolute=True)
+    Wo, _, _ = itc.step(t, Fa[0], Fa[1], to_dev(W0), 2.0, flags=itc.ITC_FIELDS_ABSOLUTE)
+    torch.cuda.synchronize()
+    assert_lattice_equal_except_ties(Wo.cpu().numpy(), Wn, raw, what="absolute")
+
+
+def _check_run(img, sigma, M, iters, W0, plan_W, stats, what):
+    A, F, sxx = _oracle_fields(img, sigma)
+    Wo, dcs, tie, t = oracle.lattice_run(A, F, sxx, sigma, W0, iters)
+    if tie.min() > 1e-4:
+        assert np.array_equal(plan_W, Wo), f"{what}: final codebooks differ"
+        assert abs(stats["dcs"] - dcs[-1]) <= DCS_ATOL, (what, stats["dcs"], dcs[-1])
+    else:
+        lockstep(img, sigma, W0, iters, (A, F, sxx))
+    assert stats["iters_done"] == iters
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_run_c1_fifty_iterations(seed):
+    img = synth.c1_image(seed)
+    W0 = synth.init_codebook(synth.rng_for(1, seed), img.astype(np.float32), 8)
+    _, Ws, st = run_plan([img], [8], [W0], itc.make_params(2.0, 3.0, 50))
+    _check_run(img, 2.0, 8, 50, W0, Ws[0], st[0], f"C1 seed {seed}")
+
+
+def test_run_c2_full_size():
+    img = synth.c2_image(0)
+    W0 = synth.init_codebook(synth.rng_for(2, 0), img.astype(np.float32), 64)
+    _, Ws, st = run_plan([img], [64], [W0], itc.make_params(4.0, 3.0, 100))
+    _check_run(img, 4.0, 64, 100, W0, Ws[0], st[0], "C2")
+
+
+def test_batched_run_matches_oracle_per_image_and_single_fields():
+    """A ragged C3-like batch in one plan: every image's result equals its own oracle run, and the
+    batched fields equal the single-image itc_fields bit for bit."""
+    import torch
+    images, Ms, sig = synth.c3_batch(24)
+    W0s = [synth.init_codebook(synth.rng_for(3, 10_000 + i), im.astype(np.float32), int(m))
+           for i, (im, m) in enumerate(zip(images, Ms))]
+    params = [itc.make_params(float(s), 3.0, 20) for s in sig]
+    plan, Ws, st = run_plan(images, Ms, W0s, params)
+    for b in range(len(images)):
+        _check_run(images[b], float(sig[b]), int(Ms[b]), 20, W0s[b], Ws[b], st[b], f"image {b}")
+    for b in (0, 5, 11):
+        H, W = images[b].shape
+        single, _ = itc.fields(to_dev(images[b]), float(sig[b]))
+        torch.cuda.synchronize()
+        batched = plan.fields_of(b)
+        assert torch.equal(single[..., :W], batched[..., :W])
+
+
+def test_stop_on_fixed_point():
+    img = synth.c1_image(0)
+    W0 = synth.init_codebook(synth.rng_for(1, 0), img.astype(np.float32), 8)
+    _, Ws, st = run_plan([img], [8], [W0], itc.make_params(2.0, 3.0, 200, flags=itc.ITC_STOP_ON_FIXED))
+    A, F, sxx = _oracle_fields(img, 2.0)
+    Wo, dcs, tie, t = oracle.lattice_run(A, F, sxx, 2.0, W0, 200, stop_on_fixed=True)
+    assert st[0]["iters_done"] == t < 200 and st[0]["moved"] == 0
+    assert np.array_equal(Ws[0], Wo)
+
+
+def test_empty_support_warning_keeps_codebook():
+    img = np.zeros((64, 64), np.uint8)
+    img[5:12, 5:12] = 1
+    W0 = np.array([[8, 8], [60, 60]], np.float32)
+    _, Ws, st = run_plan([img], [2], [W0], itc.make_params(2.0, 3.0, 3))
+    assert st[0]["status"] == itc.ITC_WARN_EMPTY_SUPPORT and st[0]["empty"] == 1
+    assert np.array_equal(Ws[0][1], W0[1])
+
+
+def test_all_codebooks_without_data_is_nonfinite():
+    img = np.zeros((64, 64), np.uint8)
+    img[0, 0] = 1
+    W0 = np.array([[40, 40], [60, 20]], np.float32)
+    _, Ws, st = run_plan([img], [2], [W0], itc.make_params(2.0, 3.0, 2))
+    assert st[0]["status"] == itc.ITC_ERR_NONFINITE and np.isinf(st[0]["dcs"])
+    assert np.array_equal(Ws[0], W0)
+
+
+def test_single_codebook_is_mean_shift_on_gpu():
+    """M = 1 (no repulsion, Sec. 2.2): the GPU step is a Gaussian mean-shift step."""
+    rng = np.random.default_rng(3)
+    img = (rng.random((50, 60)) < 0.3).astype(np.uint8)
+    w = np.array([[25.0, 30.0]], np.float32)
+    Wg, _, _, _ = gpu_step(img, 2.0, w, flags=itc.ITC_CONTINUOUS)
+    uu, vv = np.meshgrid(np.arange(19, 32), np.arange(24, 37), indexing="ij")
+    wt = img[19:32, 24:37] * np.exp(-((uu - 25.0) ** 2 + (vv - 30.0) ** 2) / 8.0)
+    np.testing.assert_allclose(Wg[0], [np.average(uu, weights=wt), np.average(vv, weights=wt)], atol=1e-4)
+
+
+def test_run_is_deterministic():
+    images, Ms, sig = synth.c3_batch(6)
+    W0s = [synth.init_codebook(synth.rng_for(3, 20_000 + i), im.astype(np.float32), int(m))
+           for i, (im, m) in enumerate(zip(images, Ms))]
+    params = [itc.make_params(float(s), 3.0, 10) for s in sig]
+    _, W1, s1 = run_plan(images, Ms, W0s, params)
+    _, W2, s2 = run_plan(images, Ms, W0s, params)
+    assert all(np.array_equal(a, b) for a, b in zip(W1, W2))
+    assert s1.tobytes() == s2.tobytes()

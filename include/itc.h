@@ -209,14 +209,26 @@ int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* st
             size_t ws_bytes, void* stream);
 
 /*
+ * itc_run_fields / itc_run_iterate -- the two phases of itc_run as separate calls (same
+ * arguments, same results when called in this order): step 2 of Algorithm 1 for every image
+ * (fields and S_XX partials into `ws`), then steps 3-11 on those fields.  Useful to time or
+ * overlap the phases; itc_run_iterate requires the fields of the same plan in `ws`.
+ */
+int itc_run_fields(const void* plan_host, const void* plan_dev, void* ws, size_t ws_bytes,
+                   void* stream);
+int itc_run_iterate(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats,
+                    void* ws, size_t ws_bytes, void* stream);
+
+/*
  * itc_backward -- gradient of Eq. (1) for every image of a plan, scaled by an upstream gradient:
  *   dD/dw_{k,i} = (2 / sigma_i^2) (E_{k,i} / S_WW - D_{k,i} / S_XW)
  *   dD/dh(x)    = 2 A(x) / S_XX - (2 / S_XW) sum_k g(x - w_k) [x in the box of round(w_k)]
  * D_k = sum_x h g(x - w_k)(x - w_k) over the box around round(w_k) (kernel at the real w_k),
  * E_k = sum_j g(w_j - w_k)(w_j - w_k).  dD/dh is the derivative with respect to the per-pixel
  * weight of weighted ITC (Sec. 5); its second term is a transposed Gaussian stamp of the
- * codebook (q = W * G, Sec. 3.1).  The fields A are recomputed per tile from the images, never
- * read from a stored copy, so the call needs no forward state beyond W.
+ * codebook (q = W * G, Sec. 3.1).  A and S_XX are read from the fields that itc_run (or
+ * itc_run_fields) left in `ws` for the same plan and images; D_k and the sums are recomputed
+ * at W, so W may differ from the forward's.
  *   W       : device ragged codebooks at which to differentiate
  *   grad_dcs: device float[B] upstream gradient (NULL = 1)
  *   grad_W  : device ragged [sum M][ndim], written (or NULL)

@@ -280,3 +280,10 @@ def dcs_grad2d_dense(h, sigma, W, trunc=3.0, R=None, A=None, with_h=True):
                                ctypes.c_double(s_xx), W.shape[0], _d(W), _d(gW),
                                _d(gh) if gh is not None else None, _d(sums))
     return gW, gh, tuple(sums)
+
+
+def dcs2d_dense(h, sigma, W, trunc=3.0, R=None, A=None) -> float:
+    """Eq. (1) for a dense 2-D weight image, from oracle fields (S_XX = sum h A) and the direct
+    window and pair sums at the real codebook W (the same sums as :func:`dcs_sums`)."""
+    _, _, (sxw, sww, s_xx) = dcs_grad2d_dense(h, sigma, W, trunc, R, A, with_h=False)
+    return float(np.log(sww) + np.log(s_xx) - 2.0 * np.log(sxw))

@@ -347,18 +347,15 @@ int itc_plan_offsets(const void* plan_host, int b, size_t* field_off, size_t* w_
     return ITC_OK;
 }
 
-int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
-            size_t ws_bytes, void* stream) {
+int itc_run_fields(const void* plan_host, const void* plan_dev, void* ws, size_t ws_bytes, void* stream) {
     const PlanHeader* h = plan_of(plan_host);
-    if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (!h || !plan_dev || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
     if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
     const ImageDesc* descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
     const int* ints = reinterpret_cast<const int*>(pd + h->ints_off);
     unsigned char* w = reinterpret_cast<unsigned char*>(ws);
-    float* fields = reinterpret_cast<float*>(w + h->ws_fields_off);
-    double* partials = reinterpret_cast<double*>(w + h->ws_partials_off);
     for (int c = 0; c < h->ncls; ++c) {
         const ClassInfo& ci = h->cls[c];
         FieldsLaunch L;
@@ -368,24 +365,43 @@ int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* st
         L.img_list = ints + ci.list_off;
         L.tile_prefix = ints + ci.prefix_off;
         L.nimg = ci.nimg;
-        L.fields = fields;
-        L.partials = partials;
+        L.fields = reinterpret_cast<float*>(w + h->ws_fields_off);
+        L.partials = reinterpret_cast<double*>(w + h->ws_partials_off);
         L.tile_h = ci.tile_h;
         L.absolute = 0;
         int rc = cuda_status(launch_fields(L, ci.ntiles, ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
         if (rc) return rc;
     }
+    return ITC_OK;
+}
+
+int itc_run_iterate(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
+                    size_t ws_bytes, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
+    unsigned char* w = reinterpret_cast<unsigned char*>(ws);
     RunLaunch R;
     memset(&R, 0, sizeof(R));
-    R.descs = descs;
-    R.fields = fields;
-    R.partials = partials;
+    R.descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
+    R.fields = reinterpret_cast<const float*>(w + h->ws_fields_off);
+    R.partials = reinterpret_cast<const double*>(w + h->ws_partials_off);
     R.W_in = W;
     R.W_out = W;
     R.stats = stats;
     R.absolute = 0;
     R.final_eval = 1;
-    return cuda_status(launch_run(R, h->B, h->max_M, 0, s));
+    return cuda_status(launch_run(R, h->B, h->max_M, 0, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
+            size_t ws_bytes, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    int rc = itc_run_fields(plan_host, plan_dev, ws, ws_bytes, stream);
+    if (rc) return rc;
+    return itc_run_iterate(plan_host, plan_dev, W, stats, ws, ws_bytes, stream);
 }
 
 int itc_backward(const void* plan_host, const void* plan_dev, const float* W, const float* grad_dcs,

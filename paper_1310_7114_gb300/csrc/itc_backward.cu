@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_const
 cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles,
                             cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
-    const size_t smem1 = (size_t)max_M * 9 * sizeof(float);
+    const size_t smem1 = (size_t)max_M * kCodebookSmemFloats * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(bwd_codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     if (e != cudaSuccess) return e;
     bwd_codebook_kernel<<<B, kRunThreads, smem1, s>>>(L);

@@ -15,6 +15,9 @@ constexpr int kMaxClasses = 16;     // distinct (sigma, trunc, flags, ndim, dtyp
 constexpr int kThreads = 256;       // fields / backward CTA size
 constexpr int kTileW = 64;          // output columns per fields tile
 constexpr int kRunThreads = 256;    // codebook-iteration CTA size
+// Dynamic shared floats per codebook vector of the iteration and backward-codebook kernels:
+// w (3), a (1), D (3), s (1), E (3).
+constexpr int kCodebookSmemFloats = 11;
 
 // Truncated, unnormalised 1-D Gaussian taps of one parameter class, computed on the host in
 // double and rounded once to float:  g[d + R] = exp(-d^2 / (2 sigma^2)),  dg[d + R] = d g[d + R].

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kRunThreads) run_kernel(const __grid_constant_
 cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, int iters_cap, cudaStream_t s) {
     (void)iters_cap;
     if (nimg <= 0) return cudaSuccess;
-    const size_t smem = (size_t)max_M * 9 * sizeof(float);
+    const size_t smem = (size_t)max_M * kCodebookSmemFloats * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(run_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     run_kernel<<<nimg, kRunThreads, smem, s>>>(L);

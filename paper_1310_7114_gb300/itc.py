@@ -34,7 +34,7 @@ ITC_STOP_ON_FIXED = 4
 EXPORTS = (
     "itc_field_pitch", "itc_fields_bytes", "itc_fields_workspace_bytes", "itc_status_string",
     "itc_fields", "itc_step", "itc_plan_bytes", "itc_plan", "itc_plan_pixels", "itc_plan_offsets",
-    "itc_run", "itc_backward",
+    "itc_run", "itc_run_fields", "itc_run_iterate", "itc_backward",
 )
 
 
@@ -108,6 +108,10 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
         L.itc_plan_offsets.argtypes = [_P, ctypes.c_int, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]
         L.itc_run.restype = ctypes.c_int
         L.itc_run.argtypes = [_P, _P, _P, _P, _P, _SZ, _P]
+        L.itc_run_fields.restype = ctypes.c_int
+        L.itc_run_fields.argtypes = [_P, _P, _P, _SZ, _P]
+        L.itc_run_iterate.restype = ctypes.c_int
+        L.itc_run_iterate.argtypes = [_P, _P, _P, _P, _P, _SZ, _P]
         L.itc_backward.restype = ctypes.c_int
         L.itc_backward.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]
         _lib = L
@@ -302,6 +306,19 @@ def run(plan: Plan, W, stats=None, stream=None):
     of B * sizeof(itc_stats)) receives the per-image results."""
     _check(itc_run(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), _ptr(stats), plan.ws.data_ptr(),
                    plan.ws.numel(), _stream(stream)), "itc_run")
+    return W
+
+
+def run_fields(plan: Plan, stream=None):
+    """itc_run_fields: the fields pass of itc_run alone."""
+    _check(lib().itc_run_fields(plan.host_ptr, plan.dev.data_ptr(), plan.ws.data_ptr(), plan.ws.numel(),
+                                _stream(stream)), "itc_run_fields")
+
+
+def run_iterate(plan: Plan, W, stats=None, stream=None):
+    """itc_run_iterate: the iterations of itc_run on the fields already in the workspace."""
+    _check(lib().itc_run_iterate(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), _ptr(stats), plan.ws.data_ptr(),
+                                 plan.ws.numel(), _stream(stream)), "itc_run_iterate")
     return W
 
 

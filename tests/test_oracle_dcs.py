@@ -183,3 +183,11 @@ def test_planted_sign_error_in_the_update_is_caught():
     pred = W - (4.0 * st["sxw"] / (2 * a))[:, None] * gW
     assert np.abs(mutated - pred).max() > 1e-3
     assert np.abs(Wraw - pred).max() < 1e-10
+
+
+def test_dense_dcs_equals_point_list_definition():
+    rng = np.random.default_rng(7)
+    h = (rng.random((20, 22)) < 0.4) * rng.random((20, 22))
+    X, hx = _all_sites(h)
+    for W in (np.array([[4.0, 5.0], [10.0, 12.0]]), np.array([[4.3, 5.8], [0.2, 21.0], [19.6, 3.1]])):
+        assert abs(oracle.dcs2d_dense(h, 2.0, W) - oracle.dcs(h.shape, X, hx, 2.0, W)) < 1e-12

@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark of batched lattice ITC on one GB300 (or N, one process per GPU, weak scaling).
+
+A step is one pass of the whole method over one batch of synthetic input, all in libitc.so:
+  fields   (Algorithm 1 step 2: truncated separable Gaussian fields + S_XX of every image),
+  iterate  (Algorithm 1 steps 3-11: 50 fixed-point updates per image, Eq. (origupdate)),
+  backward (gradient of Eq. (1) with respect to every codebook and every pixel weight).
+Default workload: 4096 binary blob silhouettes with sides U{64..512}, per-image M in
+{16, 32, 64, 128} and sigma in {2, 3, 4} (synthetic stand-ins for the paper's MPEG-7 shapes).
+
+Printed: one JSON line (rank 0).  `value` is images/s with the inputs resident in HBM, timed with
+CUDA events on the launching stream; `e2e` is the same metric through the C ABI with the inputs
+copied from pinned host memory and the results read back inside the timed region; `roofline`
+is the fields pass (bytes per launch / its event-timed duration vs the measured HBM copy
+bandwidth); `per_image_launch` is the same work launched image by image; `cpu_baseline` is the
+FP64 oracle on this host.  `--impl reference` times the oracle alone on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched ITC images/s vs per-image launch at ≤1e-5 rel err; conv GB/s % HBM peak"
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "c3": dict(desc="4096 binary blob silhouettes, sides U{64..512}, M in {16,32,64,128}, sigma in {2,3,4}, "
+                    "50 iterations, fwd+bwd", n=4096, iters=50),
+    "c4": dict(desc="256 weighted 512x512 images (smoothed noise, sigma 8), M=32, sigma=3, D_cs fwd+bwd",
+               n=256, iters=0),
+    "c2": dict(desc="one 1024x1024 binary image (ellipses + polylines), M=64, sigma=4, 100 iterations, fwd+bwd",
+               n=1, iters=100),
+    "c5": dict(desc="one 256x256 gray image as a 256^3 [u,v,g] lattice, sigma=(3,3,8), M=64, 100 iterations, "
+                    "fwd+bwd", n=1, iters=100),
+}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+# ------------------------------------------------------------------------------------ workload
+def make_workload(name, rank, n=None):
+    """Host inputs of one rank: (images, Ms, params kwargs per image, W0s, ndims, Gs, weights)."""
+    from paper_1310_7114_gb300 import synth
+    w = WORKLOADS[name]
+    n = n or w["n"]
+    if name == "c3":
+        images, Ms, sig = synth.c3_batch(n, start=rank * n)
+        W0s = [synth.init_codebook(synth.rng_for(3, 500_000 + rank * n + i), im.astype(np.float32), int(m))
+               for i, (im, m) in enumerate(zip(images, Ms))]
+        params = [dict(sigma=float(s), iters=w["iters"]) for s in sig]
+        return images, [int(m) for m in Ms], params, W0s, [2] * n, [1] * n
+    if name == "c4":
+        images = [synth.c4_weights(rank * n + i) for i in range(n)]
+        W0s = [synth.init_codebook(synth.rng_for(4, 500_000 + rank * n + i), im, 32, 0.5) for i, im in enumerate(images)]
+        return images, [32] * n, [dict(sigma=3.0, iters=0)] * n, W0s, [2] * n, [1] * n
+    if name == "c2":
+        images = [synth.c2_image(rank)]
+        W0s = [synth.init_codebook(synth.rng_for(2, rank), images[0].astype(np.float32), 64)]
+        return images, [64], [dict(sigma=4.0, iters=100)], W0s, [2], [1]
+    if name == "c5":
+        images = [synth.c5_gray(rank)]
+        W0s = [synth.init_codebook_gray(synth.rng_for(5, rank), images[0], 64)]
+        return images, [64], [dict(sigma=(3.0, 3.0, 8.0), iters=100)], W0s, [3], [256]
+    raise ValueError(name)
+
+
+def algorithmic_field_bytes(images, ndims, Gs):
+    """Bytes the fields pass must move: read the input once, write its fields once.
+    2-D: input bytes + 3 FP32 planes per pixel; 3-D: input bytes + 4 FP32 planes per voxel."""
+    tot = 0
+    for im, d, G in zip(images, ndims, Gs):
+        px = im.shape[0] * im.shape[1]
+        tot += px * im.dtype.itemsize + (12 * px if d == 2 else 16 * px * G)
+    return tot
+
+
+# ---------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(", ") for r in self.out.strip().splitlines() if r.count(",") >= 7]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ CPU baseline
+def oracle_image(im, M, p, W0, ndim, G):
+    """The FP64 oracle on one image: fields, the fixed-point iterations, and the gradient."""
+    import oracle
+    sigma, iters = p["sigma"], p["iters"]
+    if ndim == 2:
+        h = im.astype(np.float64)
+        A, Fu, Fv = oracle.fields2d(h, sigma)
+        sxx = oracle.sxx(h, A)
+        W, dcs, _, _ = oracle.lattice_run(A, [Fu, Fv], sxx, sigma, W0, iters)
+        oracle.dcs_grad2d_dense(h, sigma, W, A=A)
+    else:
+        A, Fu, Fv, Fg = oracle.fields3d(im, G, sigma)
+        occ = np.zeros((G,) + im.shape)
+        uu, vv = np.meshgrid(np.arange(im.shape[0]), np.arange(im.shape[1]), indexing="ij")
+        occ[im, uu, vv] = 1.0
+        W, dcs, _, _ = oracle.lattice_run(A, [Fu, Fv, Fg], float((occ * A).sum()), sigma, W0, iters)
+    return W
+
+
+def cpu_baseline(name, seconds):
+    """Oracle images/s on the first images of this workload, single thread, ~`seconds` of work."""
+    import oracle
+    oracle.build()
+    images, Ms, params, W0s, ndims, Gs = make_workload(name, 0, n=min(WORKLOADS[name]["n"], 400))
+    done, t0 = 0, time.perf_counter()
+    while done < len(images) and (time.perf_counter() - t0) < seconds:
+        oracle_image(images[done], Ms[done], params[done], W0s[done], ndims[done], Gs[done])
+        done += 1
+    dt = time.perf_counter() - t0
+    px = sum(images[i].size for i in range(done))
+    return {"value": done / dt, "unit": "images/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} images of the workload ({px} pixels), fields + iterations + gradient, "
+                      f"FP64 C oracle, one thread, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1310_7114_gb300 import build, itc
+
+    build.build()
+    itc.lib()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    name = args.workload
+    images, Ms, pk, W0s, ndims, Gs = make_workload(name, rank, args.images)
+    B = len(images)
+    stream = torch.cuda.current_stream()
+
+    # resident inputs: every image in one device buffer (rows padded to 16 elements)
+    buf, views = itc.pack_images(images, dev)
+    params = [itc.make_params(p["sigma"], 3.0, p["iters"]) for p in pk]
+    plan = itc.Plan(views, Ms, params, ndims=ndims, Gs=Gs)
+    W0 = plan.pack_W(W0s)
+    W = W0.clone()
+    stats = itc.new_stats(B, dev)
+    gW = torch.empty_like(W)
+    gh = torch.empty(plan.pixels, dtype=torch.float32, device=dev)
+    ncls = len({(p["sigma"] if np.isscalar(p["sigma"]) else tuple(p["sigma"])) for p in pk})
+    launches_per_step = ncls + 1 + 2
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+
+    def step(e=None):
+        W.copy_(W0)
+        if e: e[0].record(stream)
+        itc.run_fields(plan)
+        if e: e[1].record(stream)
+        itc.run_iterate(plan, W, stats)
+        if e: e[2].record(stream)
+        itc.backward(plan, W, grad_W=gW, grad_h=gh)
+        if e: e[3].record(stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(ev[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    f_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    i_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    b_ms = [e[2].elapsed_time(e[3]) for e in ev]
+
+    # e2e through the C ABI: host inputs -> device, itc_run + itc_backward, results -> host
+    host_buf = buf.cpu().pin_memory()
+    host_W0 = W0.cpu().pin_memory()
+    out_W = torch.empty(W.shape, dtype=W.dtype).pin_memory()
+    out_gW = torch.empty(W.shape, dtype=W.dtype).pin_memory()
+    out_st = torch.empty(stats.shape, dtype=stats.dtype).pin_memory()
+
+    def e2e_step():
+        buf.copy_(host_buf, non_blocking=True)
+        W.copy_(host_W0, non_blocking=True)
+        itc.run(plan, W, stats)
+        itc.backward(plan, W, grad_W=gW, grad_h=gh)
+        out_W.copy_(W, non_blocking=True)
+        out_gW.copy_(gW, non_blocking=True)
+        out_st.copy_(stats, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = buf.numel() * buf.element_size() + W0.numel() * 4
+    d2h = 2 * W.numel() * 4 + stats.numel()
+
+    # the same work launched image by image (one plan per image), on a prefix of the batch
+    per_image = None
+    if not args.no_per_image and rank == 0:
+        n_pi = min(B, args.per_image_n)
+        plans = [itc.Plan([views[b]], [Ms[b]], params[b], ndims=[ndims[b]], Gs=[Gs[b]]) for b in range(n_pi)]
+        Ws = [p.pack_W([W0s[b]]) for b, p in enumerate(plans)]
+        sts = [itc.new_stats(1, dev) for _ in plans]
+        gWs = [torch.empty_like(w) for w in Ws]
+        ghs = [torch.empty(p.pixels, dtype=torch.float32, device=dev) for p in plans]
+
+        def pi_pass():
+            for b in range(n_pi):
+                itc.run(plans[b], Ws[b], sts[b])
+                itc.backward(plans[b], Ws[b], grad_W=gWs[b], grad_h=ghs[b])
+
+        pi_pass()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pi_pass()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1)
+        per_image = {"value": n_pi / (pms / 1000.0), "unit": "images/s", "images": n_pi,
+                     "launches_per_image": 4,
+                     "note": "one plan per image, itc_run + itc_backward per image, same stream"}
+        del plans, Ws, sts, gWs, ghs
+
+    if rank != 0:
+        return None
+
+    peaks, peak_src = measured_peaks()
+    fbytes = algorithmic_field_bytes(images, ndims, Gs)
+    f_avg = statistics.mean(f_ms)
+    achieved = fbytes / (f_avg / 1000.0) / 1e9
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    value = world * B / (ms_step / 1000.0)
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "images/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded stand-ins for the paper's MPEG-7 shapes; no dataset on the box)",
+        "config": {"workload": f"{name}: {WORKLOADS[name]['desc']}", "images_per_gpu": B,
+                   "pixels_per_gpu": int(sum(im.size for im in images)),
+                   "l2": "inputs larger than L2 (packed images %.0f MB, fields %.0f MB per step)"
+                         % (buf.numel() * buf.element_size() / 1e6, plan.ws_bytes / 1e6),
+                   "parallelism": f"replicas x{world} (independent images per GPU, no collective)"},
+        "phases_ms": {"fields": f_avg, "iterate": statistics.mean(i_ms), "backward": statistics.mean(b_ms)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "fields pass (fields_kernel, one launch per sigma class)",
+                     "algorithmic_bytes_per_launch": fbytes, "peak_source": f"{peak_src} hbm_gbs"},
+        "e2e": {"value": world * B / (e2e_ms / 1000.0), "unit": "images/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
+                "path": "itc_run + itc_backward through the C ABI; inputs from pinned host memory; W, grad_W, "
+                        "stats back to the host"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if per_image:
+        res["per_image_launch"] = per_image
+        res["batched_over_per_image"] = value / world / per_image["value"]
+    if not args.no_cpu_baseline and world == 1:
+        res["cpu_baseline"] = cpu_baseline(name, args.cpu_seconds)
+    return res
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args, rank):
+    """The FP64 oracle, as it stands, on this host's cores: each step runs a bounded sample of the
+    workload (the first --ref-images images)."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    name = args.workload
+    n = min(args.ref_images, WORKLOADS[name]["n"])
+    images, Ms, pk, W0s, ndims, Gs = make_workload(name, 0, n=max(n, 1))
+
+    def step():
+        for b in range(n):
+            oracle_image(images[b], Ms[b], pk[b], W0s[b], ndims[b], Gs[b])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    v = n / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "images/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000.0, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{name}: {WORKLOADS[name]['desc']}", "images_per_step": n},
+        "cpu_baseline": {"value": v, "unit": "images/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} images of the workload per step, FP64 C oracle, one thread"},
+        "e2e": {"value": v, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c3")
+    ap.add_argument("--images", type=int, default=None)
+    ap.add_argument("--per-image-n", type=int, default=512)
+    ap.add_argument("--no-per-image", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-images", type=int, default=8)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else max(args.warmup, 1)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        res = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -133,6 +133,27 @@ const char* itc_status_string(int code);
 int itc_fields(const itc_image* img, const itc_params* p, float* fields, double* sxx,
                void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * itc_fields_noalloc -- itc_fields for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is a deployment variant.  Some hosts give a library only the input
+ * and output buffers and forbid any allocation while they run (plugin and real-time hosts with
+ * a fixed memory budget, or code that must not call cudaMalloc while it records work); they
+ * cannot provide itc_fields' scratch.  This entry point keeps that scratch (one double per
+ * fields tile) in a fixed device array inside the library, ITC_NOALLOC_MAX_TILES doubles
+ * (512 KiB), which every GPU that loads the library holds until the process exits.
+ *   Same arguments and results as itc_fields, without ws / ws_bytes.  Allocates nothing.
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ *   with that device current); make that first call before any stream capture.
+ *   All calls share the one array: calls whose work overlaps on a GPU (other streams, other
+ *   host threads) race on it and must be serialised by the caller.  The array keeps the last
+ *   call's partial sums; each call overwrites every entry it reads, so nothing is cleared.
+ * Errors: ITC_ERR_UNSUPPORTED if the image needs more than ITC_NOALLOC_MAX_TILES tiles (2-D:
+ * ceil(H/64) ceil(W/64); 3-D: ceil(H/32) ceil(W/64) ceil(G/8)); otherwise as itc_fields.
+ */
+#define ITC_NOALLOC_MAX_TILES 65536
+int itc_fields_noalloc(const itc_image* img, const itc_params* p, float* fields, double* sxx,
+                       void* stream);
+
 /* ---------------------------------------------------------------------- one update step */
 /*
  * itc_step -- one iteration of Algorithm 1 (steps 4-10): gather A and the moments at the

@@ -34,7 +34,7 @@ ITC_STOP_ON_FIXED = 4
 EXPORTS = (
     "itc_field_pitch", "itc_fields_bytes", "itc_fields_workspace_bytes", "itc_status_string",
     "itc_fields", "itc_step", "itc_plan_bytes", "itc_plan", "itc_plan_pixels", "itc_plan_offsets",
-    "itc_run", "itc_run_fields", "itc_run_iterate", "itc_backward",
+    "itc_run", "itc_run_fields", "itc_run_iterate", "itc_backward", "itc_fields_noalloc",
 )
 
 
@@ -94,6 +94,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
         L.itc_status_string.argtypes = [ctypes.c_int]
         L.itc_fields.restype = ctypes.c_int
         L.itc_fields.argtypes = [ctypes.POINTER(ItcImage), ctypes.POINTER(ItcParams), _P, _P, _P, _SZ, _P]
+        L.itc_fields_noalloc.restype = ctypes.c_int
+        L.itc_fields_noalloc.argtypes = [ctypes.POINTER(ItcImage), ctypes.POINTER(ItcParams), _P, _P, _P]
         L.itc_step.restype = ctypes.c_int
         L.itc_step.argtypes = [ctypes.POINTER(ItcImage), ctypes.POINTER(ItcParams), _P, _P, ctypes.c_int,
                                _P, _P, _P, _P, _P]
@@ -170,6 +172,10 @@ def field_pitch(W: int) -> int:
 
 def itc_fields(img: ItcImage, p: ItcParams, fields_ptr, sxx_ptr, ws_ptr, ws_bytes, stream):
     return lib().itc_fields(ctypes.byref(img), ctypes.byref(p), fields_ptr, sxx_ptr, ws_ptr, ws_bytes, stream)
+
+
+def itc_fields_noalloc(img: ItcImage, p: ItcParams, fields_ptr, sxx_ptr, stream):
+    return lib().itc_fields_noalloc(ctypes.byref(img), ctypes.byref(p), fields_ptr, sxx_ptr, stream)
 
 
 def itc_step(img, p, fields_ptr, sxx_ptr, M, W_in, W_out, W_lat, stats, stream):

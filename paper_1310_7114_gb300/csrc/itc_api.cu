@@ -4,6 +4,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
 #include <vector>
 
 #include "itc_internal.cuh"
@@ -110,13 +113,58 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? ITC_OK : ITC_ERR_CUDA; }
 
-size_t plan_layout(int B, size_t* desc_off, size_t* ints_off) {
+size_t plan_layout(int B, size_t* desc_off, size_t* ints_off, size_t* tmap_off = nullptr) {
     const size_t h = align_up(sizeof(PlanHeader), 256);
     const size_t d = align_up((size_t)B * sizeof(ImageDesc), 256);
     const size_t n = align_up((size_t)(3 * (size_t)B + kMaxClasses + 2) * sizeof(int), 256);
+    const size_t m = align_up((size_t)B * sizeof(CUtensorMap), 256);
     if (desc_off) *desc_off = h;
     if (ints_off) *ints_off = h + d;
-    return h + d + n;
+    if (tmap_off) *tmap_off = h + d + n;
+    return h + d + n + m;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once; null when no driver is present (then
+// every image takes the non-TMA fields path).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of an image's input for the TMA fields tiles; false if the image's rows are not
+// 16-byte aligned or no encoder is available.
+bool encode_input_map(const itc_image* img, int R, CUtensorMap* out) {
+    const int es = img->dtype == ITC_U8 ? 1 : 4;
+    if (((uintptr_t)img->data % 16) != 0 || ((size_t)img->pitch * es) % 16 != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    int bw = 0, bh = 0;
+    fields_tma_box(img->dtype, R, &bw, &bh);
+    const cuuint64_t dims[2] = {(cuuint64_t)img->W, (cuuint64_t)img->H};
+    const cuuint64_t strides[1] = {(cuuint64_t)img->pitch * es};
+    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(out, img->dtype == ITC_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                           2, const_cast<void*>(img->data), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_fields_any(const FieldsLaunch& L, bool tma, int ntiles, int Ru, int Rv, int ndim, int dtype,
+                              cudaStream_t s) {
+    if (tma && fields_tma_supported(ndim, Ru, Rv)) return launch_fields_tma(L, ntiles, Ru, dtype, s);
+    return launch_fields(L, ntiles, Ru, Rv, ndim, dtype, s);
 }
 
 const PlanHeader* plan_of(const void* plan_host) {
@@ -181,7 +229,9 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
     const long long nt = tiles_of(L.one);
     if (nt > 0x7fffffffLL) return ITC_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    rc = cuda_status(launch_fields(L, (int)nt, L.taps.R[0], L.taps.R[1], img->ndim, img->dtype, s));
+    const bool tma = fields_tma_supported(img->ndim, L.taps.R[0], L.taps.R[1]) &&
+                     encode_input_map(img, L.taps.R[0], &L.tmap_one);
+    rc = cuda_status(launch_fields_any(L, tma, (int)nt, L.taps.R[0], L.taps.R[1], img->ndim, img->dtype, s));
     if (rc) return rc;
     if (sxx) rc = cuda_status(launch_reduce_sxx(L.partials, (int)nt, sxx, s));
     return rc;
@@ -206,7 +256,8 @@ int itc_step(const itc_image* img, const itc_params* p, const float* fields, con
     L.stats = stats;
     L.absolute = (p->flags & ITC_FIELDS_ABSOLUTE) ? 1 : 0;
     L.final_eval = 0;
-    return cuda_status(launch_run(L, 1, M, 1, reinterpret_cast<cudaStream_t>(stream)));
+    const int dims[3] = {img->H, img->W, img->ndim == 3 ? img->G : 1};
+    return cuda_status(launch_run(L, 1, M, dims, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 size_t itc_plan_bytes(int B) {
@@ -217,8 +268,8 @@ size_t itc_plan_bytes(int B) {
 int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, int p_stride,
              void* plan, size_t plan_bytes, size_t* ws_bytes_out) {
     if (B < 1 || !imgs || !M || !p || !plan) return ITC_ERR_INVALID_ARG;
-    size_t desc_off, ints_off;
-    const size_t need = plan_layout(B, &desc_off, &ints_off);
+    size_t desc_off, ints_off, tmap_off;
+    const size_t need = plan_layout(B, &desc_off, &ints_off, &tmap_off);
     if (plan_bytes < need) return ITC_ERR_INVALID_ARG;
     for (int b = 0; b < B; ++b) {
         int rc = check_image(imgs + b);
@@ -235,6 +286,8 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     h->B = B;
     h->desc_off = (long long)desc_off;
     h->ints_off = (long long)ints_off;
+    h->tmap_off = (long long)tmap_off;
+    CUtensorMap* tmaps = reinterpret_cast<CUtensorMap*>(buf.data() + tmap_off);
 
     // parameter classes: (ndim, dtype, sigma, trunc)
     struct Key { int ndim, dtype; float s0, s1, s2, trunc; };
@@ -256,8 +309,11 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
             ci.dtype = imgs[b].dtype;
             ci.absolute = 0;
             ci.tile_h = tile_h_of(imgs[b].ndim);
+            ci.tma = fields_tma_supported(ci.ndim, ci.taps.R[0], ci.taps.R[1]) ? 1 : 0;
         }
         cls_of[b] = c;
+        ClassInfo& cb = h->cls[c];
+        if (cb.tma && !encode_input_map(imgs + b, cb.taps.R[0], tmaps + b)) cb.tma = 0;
         fill_desc(imgs + b, pb, M[b], descs + b);
         descs[b].cls = c;
     }
@@ -277,6 +333,9 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         d.bwd_tile_begin = bwd;
         bwd += d.bwd_tiles_u * d.bwd_tiles_v;
         if (d.M > maxM) maxM = d.M;
+        h->max_dim[0] = d.H > h->max_dim[0] ? d.H : h->max_dim[0];
+        h->max_dim[1] = d.W > h->max_dim[1] ? d.W : h->max_dim[1];
+        h->max_dim[2] = d.G > h->max_dim[2] ? d.G : h->max_dim[2];
     }
     h->fields_floats = foff;
     h->total_pixels = ghoff;
@@ -369,7 +428,9 @@ int itc_run_fields(const void* plan_host, const void* plan_dev, void* ws, size_t
         L.partials = reinterpret_cast<double*>(w + h->ws_partials_off);
         L.tile_h = ci.tile_h;
         L.absolute = 0;
-        int rc = cuda_status(launch_fields(L, ci.ntiles, ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
+        L.tmaps = reinterpret_cast<const CUtensorMap*>(pd + h->tmap_off);
+        int rc = cuda_status(
+            launch_fields_any(L, ci.tma != 0, ci.ntiles, ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
         if (rc) return rc;
     }
     return ITC_OK;
@@ -392,7 +453,7 @@ int itc_run_iterate(const void* plan_host, const void* plan_dev, float* W, itc_s
     R.stats = stats;
     R.absolute = 0;
     R.final_eval = 1;
-    return cuda_status(launch_run(R, h->B, h->max_M, 0, reinterpret_cast<cudaStream_t>(stream)));
+    return cuda_status(launch_run(R, h->B, h->max_M, h->max_dim, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,

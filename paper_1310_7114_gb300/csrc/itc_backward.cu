@@ -7,10 +7,10 @@
 // Kernel 1 (one CTA per image): window sums a_k, D_k around round(w_k) read directly from the
 // image (kernel evaluated at the real w_k, one warp per k), the M x M sums s_k, E_k (one warp
 // per k, xor-shuffle reduction), S_XW, S_WW, grad_W and two per-image scalars for kernel 2.
-// Kernel 2 (one CTA per 16 x 64 pixel tile): the codebooks whose box meets the tile are listed
-// in k order (ballot compaction, so the per-pixel sums are deterministic), then every pixel
-// combines the stored field A with the stamp of the listed codebook Gaussians -- the transposed
-// form of the gather in the forward update.
+// Kernel 2 (one CTA per 64 x 64 pixel tile): the codebooks whose box meets the tile are listed
+// in k order (ballot compaction), their Gaussians are stamped onto the tile in that order -- the
+// transposed form of the gather in the forward update -- and every pixel combines the stored
+// field A with the stamp.
 #include <math.h>
 
 #include "itc_internal.cuh"
@@ -186,6 +186,15 @@ __device__ __forceinline__ int find_image(const int* __restrict__ prefix, int n,
     return lo;
 }
 
+constexpr int kChunk = 64;   // codebooks staged per round in the pixel kernel
+
+// Pixel pass over a 64 x 64 tile.  The stamp S(x) = sum_k g(x - w_k) [x in box(round(w_k))] is
+// separable in 2-D: g(x - w) = g_u(x_u - w_u) g_v(x_v - w_v) and the box is a product of two
+// intervals, so for the codebooks whose box meets the tile (listed in k order)
+//   S(r, c) = sum_l a_l(r) b_l(c),  a_l(r) = g_u(u0 + r - w_lu) [|u0 + r - r_lu| <= R_u], ...
+// Chunks of 64 listed codebooks are staged as a (64 x 64) and b (64 x 64) in shared memory and
+// every thread accumulates a 4 x 4 block of pixels in l order (deterministic, no atomics).  In
+// 3-D the g factor depends on each pixel's gray level and is applied per pixel and codebook.
 __global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_constant__ BackwardLaunch L) {
     const int img = find_image(L.bwd_prefix, L.B + 1, blockIdx.x);
     const ImageDesc& D = L.descs[img];
@@ -193,9 +202,11 @@ __global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_const
     const int u0 = (t / D.bwd_tiles_v) * kBwdTileH, v0 = (t % D.bwd_tiles_v) * kBwdTileW;
     const int M = D.M, nd = D.ndim, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int Ru = D.R[0], Rv = D.R[1], Rg = D.R[2];
-    extern __shared__ __align__(16) float sm[];
-    float* lw = sm;                                   // listed real positions, 3 per entry
-    int* lr = reinterpret_cast<int*>(lw + 3 * M);     // listed rounded positions, 3 per entry
+    extern __shared__ __align__(16) int lk[];          // listed codebook indices (M)
+    __shared__ __align__(16) float sa[kChunk][kBwdTileH];
+    __shared__ __align__(16) float sb[kChunk][kBwdTileW];
+    __shared__ float sgw[kChunk];                       // 3-D: w_g of the chunk's codebooks
+    __shared__ int sgr[kChunk];                         // 3-D: round(w_g)
     __shared__ int wcount[kThreads / 32];
     __shared__ int s_total;
     const float* Wk = L.W + D.w_off;
@@ -205,28 +216,17 @@ __global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_const
     for (int base = 0; base < M; base += blockDim.x) {
         const int k = base + tid;
         bool hit = false;
-        float w[3] = {0.f, 0.f, 0.f};
-        int r[3] = {0, 0, 0};
         if (k < M) {
-            for (int i = 0; i < nd; ++i) w[i] = Wk[k * nd + i];
-            r[0] = lattice_round_i(w[0], D.H);
-            r[1] = lattice_round_i(w[1], D.W);
-            if (nd == 3) r[2] = lattice_round_i(w[2], D.G);
-            hit = (r[0] + Ru >= u0) && (r[0] - Ru <= u0 + kBwdTileH - 1) &&
-                  (r[1] + Rv >= v0) && (r[1] - Rv <= v0 + kBwdTileW - 1);
+            const int r0 = lattice_round_i(Wk[k * nd], D.H), r1 = lattice_round_i(Wk[k * nd + 1], D.W);
+            hit = (r0 + Ru >= u0) && (r0 - Ru <= u0 + kBwdTileH - 1) &&
+                  (r1 + Rv >= v0) && (r1 - Rv <= v0 + kBwdTileW - 1);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
         if (lane == 0) wcount[wid] = __popc(bal);
         __syncthreads();
         int off = total;
         for (int q = 0; q < wid; ++q) off += wcount[q];
-        if (hit) {
-            const int pos = off + __popc(bal & ((1u << lane) - 1u));
-            for (int i = 0; i < 3; ++i) {
-                lw[pos * 3 + i] = w[i];
-                lr[pos * 3 + i] = r[i];
-            }
-        }
+        if (hit) lk[off + __popc(bal & ((1u << lane) - 1u))] = k;
         int add = 0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) add += wcount[q];
         total += add;
@@ -235,33 +235,96 @@ __global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_const
     if (tid == 0) s_total = total;
     __syncthreads();
     const int nl = s_total;
-    const double s1 = L.scal[img * 4 + 0], s2 = L.scal[img * 4 + 1];
     const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
-    const float* A = L.fields + D.field_off;
-    const int v = v0 + (tid & 63);
-    for (int q = tid >> 6; q < kBwdTileH; q += kThreads / 64) {
-        const int u = u0 + q;
-        if (u >= D.H || v >= D.W) continue;
-        int gl = 0;
-        long long o = (long long)u * D.fpitch + v;
-        if (nd == 3) {
-            gl = pixel_gray(D, u, v);
-            if (gl >= D.G) {   // a voxel outside the lattice: no field value
-                L.grad_h[D.gh_off + (long long)u * D.W + v] = 0.f;
-                continue;
+
+    // this thread's 4 x 4 block
+    const int pr = (tid >> 4) * 4, pc = (tid & 15) * 4;
+    int gray[4][4];
+    if (nd == 3) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int u = u0 + pr + i, v = v0 + pc + j;
+                gray[i][j] = (u < D.H && v < D.W) ? pixel_gray(D, u, v) : 0;
             }
-            o += (long long)gl * D.H * D.fpitch;
+    }
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+    for (int base = 0; base < nl; base += kChunk) {
+        const int nc = min(kChunk, nl - base);
+        // stage the separable factors of this chunk
+        for (int i = tid; i < kChunk * kBwdTileH; i += blockDim.x) {
+            const int l = i / kBwdTileH, r = i % kBwdTileH;
+            float av = 0.f, bv = 0.f;
+            if (l < nc) {
+                const int k = lk[base + l];
+                const float w0 = Wk[k * nd], w1 = Wk[k * nd + 1];
+                const int r0 = lattice_round_i(w0, D.H), r1 = lattice_round_i(w1, D.W);
+                const int u = u0 + r, v = v0 + r;
+                if (u < D.H && abs(u - r0) <= Ru) { const float d = (float)u - w0; av = expf(-d * d * c0); }
+                if (v < D.W && abs(v - r1) <= Rv) { const float d = (float)v - w1; bv = expf(-d * d * c1); }
+                if (nd == 3 && r == 0) {
+                    sgw[l] = Wk[k * nd + 2];
+                    sgr[l] = lattice_round_i(Wk[k * nd + 2], D.G);
+                }
+            }
+            sa[l][r] = av;
+            sb[l][r] = bv;
         }
-        const float a = __ldg(A + o);
-        float st = 0.f;
-        for (int l = 0; l < nl; ++l) {
-            if (abs(u - lr[l * 3]) > Ru || abs(v - lr[l * 3 + 1]) > Rv) continue;
-            if (nd == 3 && abs(gl - lr[l * 3 + 2]) > Rg) continue;
-            const float du = (float)u - lw[l * 3], dv = (float)v - lw[l * 3 + 1];
-            const float dg = nd == 3 ? (float)gl - lw[l * 3 + 2] : 0.f;
-            st += expf(-(du * du * c0 + dv * dv * c1 + dg * dg * c2));
+        __syncthreads();
+        for (int l = 0; l < nc; ++l) {
+            const float4 a4 = *reinterpret_cast<const float4*>(&sa[l][pr]);
+            const float4 b4 = *reinterpret_cast<const float4*>(&sb[l][pc]);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+            if (nd == 2) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            } else {
+                const float wg = sgw[l];
+                const int rg = sgr[l];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int gl = gray[i][j];
+                        if (abs(gl - rg) <= Rg) {
+                            const float d = (float)gl - wg;
+                            acc[i][j] = fmaf(av[i] * bv[j], expf(-d * d * c2), acc[i][j]);
+                        }
+                    }
+            }
         }
-        L.grad_h[D.gh_off + (long long)u * D.W + v] = (float)(s1 * (double)a - s2 * (double)st);
+        __syncthreads();
+    }
+
+    const double s1 = L.scal[img * 4 + 0], s2 = L.scal[img * 4 + 1];
+    const float* A = L.fields + D.field_off;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int u = u0 + pr + i;
+        if (u >= D.H) break;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int v = v0 + pc + j;
+            if (v >= D.W) break;
+            long long o = (long long)u * D.fpitch + v;
+            float* out = L.grad_h + D.gh_off + (long long)u * D.W + v;
+            if (nd == 3) {
+                if (gray[i][j] >= D.G) {   // a voxel outside the lattice: no field value
+                    *out = 0.f;
+                    continue;
+                }
+                o += (long long)gray[i][j] * D.H * D.fpitch;
+            }
+            *out = (float)(s1 * (double)__ldg(A + o) - s2 * (double)acc[i][j]);
+        }
     }
 }
 
@@ -276,7 +339,7 @@ cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long
     bwd_codebook_kernel<<<B, kRunThreads, smem1, s>>>(L);
     e = cudaGetLastError();
     if (e != cudaSuccess || !L.grad_h || pixel_tiles <= 0) return e;
-    const size_t smem2 = (size_t)max_M * 6 * sizeof(float);
+    const size_t smem2 = (size_t)max_M * sizeof(int);
     e = cudaFuncSetAttribute(bwd_pixels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
     bwd_pixels_kernel<<<(unsigned)pixel_tiles, kThreads, smem2, s>>>(L);

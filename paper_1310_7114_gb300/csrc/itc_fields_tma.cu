@@ -1,0 +1,359 @@
+// itc_fields_tma.cu -- 2-D fields (Sec. 3.1, Sec. 5) with TMA-staged input tiles.
+//
+// Same arithmetic as fields_kernel in itc_fields.cu (the results are bit for bit the same: every
+// output accumulates the same products in the same order), reorganised for throughput:
+//   * persistent CTAs walk the tile list with a fixed stride;
+//   * the input tile plus its halo arrives by one cp.async.bulk.tensor (TMA) per tile into a
+//     staging buffer; the next tile's copy is issued as soon as the current one has been
+//     converted, so it overlaps the two passes;
+//   * both passes use packed FP32 FMAs (fma.rn.f32x2) over pairs of neighbouring columns.
+// Used for 2-D images whose rows start on 16-byte boundaries (the tensor map needs it) and for
+// the compiled radii 6, 9 and 12; everything else goes through fields_kernel.
+#include <cuda.h>
+
+#include "itc_internal.cuh"
+
+namespace itc {
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        "  .reg .pred p;\n"
+        "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "  selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ double block_sum_double(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0;
+    if (wid == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+
+__device__ __forceinline__ int find_image(const int* __restrict__ prefix, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+
+// The image and tile-local index of tile t of this launch.
+__device__ __forceinline__ const ImageDesc* locate(const FieldsLaunch& L, int t, int& local, int& img) {
+    if (L.descs) {
+        const int p = find_image(L.tile_prefix, L.nimg + 1, t);
+        img = __ldg(L.img_list + p);
+        local = t - __ldg(L.tile_prefix + p);
+        return L.descs + img;
+    }
+    img = 0;
+    local = t;
+    return &L.one;
+}
+
+// Bounded wait for the staged tile (about a second at most); false means the copy never landed.
+__device__ __forceinline__ bool wait_stage(uint64_t* bar, uint32_t parity) {
+    for (long long i = 0; i < (1LL << 24); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <int R, bool ABS, int DTYPE>
+__global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_constant__ FieldsLaunch L, int ntiles) {
+    constexpr int TW = kTileW, TH = 64, K = TH / 16;
+    constexpr int ROWS = TH + 2 * R;
+    constexpr int SW = ((TW + 2 * R + 3) & ~3) + 4;
+    constexpr int ES = DTYPE == ITC_U8 ? 1 : 4;
+    constexpr int RA = DTYPE == ITC_U8 ? 16 : ((R + 3) & ~3);   // box starts 16-byte aligned
+    constexpr int BW = TW + 2 * RA;                              // box width in elements
+    constexpr int BOX_BYTES = BW * ROWS * ES;
+    constexpr int STAGE_BYTES = (BOX_BYTES + 127) & ~127;
+    constexpr int NWIN = ((8 + 2 * R) + 3) & ~3;                 // window of 8 row-pass outputs
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the TMA destination must be 128-byte aligned: round the base up (128 spare bytes reserved)
+    unsigned char* stage = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    float* s_in = reinterpret_cast<float*>(stage + STAGE_BYTES);      // ROWS x SW
+    float* sT = s_in + ROWS * SW;                                     // T then T_v: ROWS x TW each
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double red[32];
+    __shared__ int s_abort;
+    const Taps& tp = L.taps;
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    auto issue = [&](int t) {
+        int local, img;
+        const ImageDesc* dp = locate(L, t, local, img);
+        const int tv = local % dp->tiles_v, tu = local / dp->tiles_v;
+        const CUtensorMap* map = L.descs ? L.tmaps + img : &L.tmap_one;
+        mbar_expect_tx(&bar, BOX_BYTES);
+        tma_load_2d(stage, map, tv * TW - RA, tu * TH - R, &bar);
+    };
+
+    int t = blockIdx.x;
+    if (tid == 0 && t < ntiles) issue(t);
+    uint32_t parity = 0;
+    const int kb = tid >> 4, cg = tid & 15;
+    const int k0 = kb * K, c0 = cg * 4;
+
+    for (; t < ntiles; t += gridDim.x) {
+        int local, img;
+        const ImageDesc* dp = locate(L, t, local, img);
+        const int H = dp->H, W = dp->W, fpitch = dp->fpitch;
+        const int u0 = (local / dp->tiles_v) * TH, v0 = (local % dp->tiles_v) * TW;
+        float* const fbase = L.fields + dp->field_off;
+        const long long plane = dp->plane_floats;
+
+        if (tid == 0 && !wait_stage(&bar, parity)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) {
+            if (tid == 0) L.partials[dp->partial_off + local] = __longlong_as_double(0x7ff8000000000000LL);
+            return;   // S_XX of the image becomes NaN: the host sees a non-finite status
+        }
+        parity ^= 1u;
+
+        // staged box -> float input tile, columns shifted so that s_in column 0 is v0 - R
+        int nonzero = 0;
+        for (int i = tid; i < ROWS * (SW / 4); i += kThreads) {
+            const int r = i / (SW / 4), c = (i % (SW / 4)) * 4;
+            float x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int cc = c + j;
+                float v = 0.f;
+                if (cc < TW + 2 * R) {
+                    const int sc = r * BW + cc + (RA - R);
+                    if (DTYPE == ITC_U8) v = (float)stage[sc];
+                    else v = reinterpret_cast<const float*>(stage)[sc];
+                }
+                x[j] = v;
+                nonzero |= (v != 0.f);
+            }
+            st4(s_in + r * SW + c, x[0], x[1], x[2], x[3]);
+        }
+        const int any = __syncthreads_or(nonzero);   // the stage is free from here on
+        if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+
+        const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
+        if (!any) {
+            if (col_active) {
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const int u = u0 + k0 + kk;
+                    if (u >= H) break;
+                    float* o = fbase + (long long)u * fpitch + v0 + c0;
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) st4(o + f * plane, 0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            if (tid == 0) L.partials[dp->partial_off + local] = 0.0;
+            continue;
+        }
+
+        // ---- pass along v: 8 outputs per item, pairs of neighbouring columns per packed FMA
+        for (int item = tid; item < ROWS * 8; item += kThreads) {
+            const int r = item >> 3, c = (item & 7) * 8;
+            const int gu = u0 - R + r;
+            if (v0 + c >= W) continue;
+            float* oT = sT + r * TW + c;
+            float* oV = oT + ROWS * TW;
+            if (gu < 0 || gu >= H) {
+                st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + 4, 0.f, 0.f, 0.f, 0.f);
+                st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + 4, 0.f, 0.f, 0.f, 0.f);
+                continue;
+            }
+            float x[NWIN];
+            const float* src = s_in + r * SW + c;
+#pragma unroll
+            for (int q = 0; q < NWIN / 4; ++q) {
+                const float4 f = *reinterpret_cast<const float4*>(src + 4 * q);
+                x[4 * q] = f.x; x[4 * q + 1] = f.y; x[4 * q + 2] = f.z; x[4 * q + 3] = f.w;
+            }
+            float xv[ABS ? NWIN : 1];
+            if constexpr (ABS) {
+                const float vb = (float)(v0 - R + c);
+#pragma unroll
+                for (int i = 0; i < NWIN; ++i) xv[i] = x[i] * (vb + (float)i);
+            }
+            float2 aT[4], aV[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) { aT[p] = f2(0.f, 0.f); aV[p] = f2(0.f, 0.f); }
+#pragma unroll
+            for (int d = 0; d <= 2 * R; ++d) {
+                const float2 g2 = f2(tp.gv[d], tp.gv[d]);
+                const float2 dg2 = f2(tp.dgv[d], tp.dgv[d]);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const float2 xx = f2(x[2 * p + d], x[2 * p + 1 + d]);
+                    aT[p] = __ffma2_rn(g2, xx, aT[p]);
+                    if constexpr (ABS) aV[p] = __ffma2_rn(g2, f2(xv[2 * p + d], xv[2 * p + 1 + d]), aV[p]);
+                    else aV[p] = __ffma2_rn(dg2, xx, aV[p]);
+                }
+            }
+            st4(oT, aT[0].x, aT[0].y, aT[1].x, aT[1].y); st4(oT + 4, aT[2].x, aT[2].y, aT[3].x, aT[3].y);
+            st4(oV, aV[0].x, aV[0].y, aV[1].x, aV[1].y); st4(oV + 4, aV[2].x, aV[2].y, aV[3].x, aV[3].y);
+        }
+        __syncthreads();
+
+        // ---- pass along u: K rows x 4 columns per thread, column pairs per packed FMA
+        double part = 0.0;
+        if (col_active) {
+            float2 aA[K][2], aU[K][2], aV[K][2];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+                for (int p = 0; p < 2; ++p) { aA[kk][p] = f2(0.f, 0.f); aU[kk][p] = f2(0.f, 0.f); aV[kk][p] = f2(0.f, 0.f); }
+            const float* Tp = sT + k0 * TW + c0;
+            const float ub = (float)(u0 - R + k0);
+#pragma unroll
+            for (int i = 0; i < K + 2 * R; ++i) {
+                const float4 t4 = *reinterpret_cast<const float4*>(Tp + i * TW);
+                const float4 v4 = *reinterpret_cast<const float4*>(Tp + ROWS * TW + i * TW);
+                const float2 t01 = f2(t4.x, t4.y), t23 = f2(t4.z, t4.w);
+                const float2 v01 = f2(v4.x, v4.y), v23 = f2(v4.z, v4.w);
+                float2 tu01, tu23;
+                if constexpr (ABS) {
+                    const float uc = ub + (float)i;
+                    tu01 = f2(t4.x * uc, t4.y * uc);
+                    tu23 = f2(t4.z * uc, t4.w * uc);
+                }
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const int e = i - kk;
+                    if (e >= 0 && e <= 2 * R) {
+                        const float2 g2 = f2(tp.gu[e], tp.gu[e]);
+                        aA[kk][0] = __ffma2_rn(g2, t01, aA[kk][0]);
+                        aA[kk][1] = __ffma2_rn(g2, t23, aA[kk][1]);
+                        if constexpr (ABS) {
+                            aU[kk][0] = __ffma2_rn(g2, tu01, aU[kk][0]);
+                            aU[kk][1] = __ffma2_rn(g2, tu23, aU[kk][1]);
+                        } else {
+                            const float2 dg2 = f2(tp.dgu[e], tp.dgu[e]);
+                            aU[kk][0] = __ffma2_rn(dg2, t01, aU[kk][0]);
+                            aU[kk][1] = __ffma2_rn(dg2, t23, aU[kk][1]);
+                        }
+                        aV[kk][0] = __ffma2_rn(g2, v01, aV[kk][0]);
+                        aV[kk][1] = __ffma2_rn(g2, v23, aV[kk][1]);
+                    }
+                }
+            }
+            float ps = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int u = u0 + k0 + kk;
+                if (u < H) {
+                    float* o = fbase + (long long)u * fpitch + v0 + c0;
+                    st4(o, aA[kk][0].x, aA[kk][0].y, aA[kk][1].x, aA[kk][1].y);
+                    st4(o + plane, aU[kk][0].x, aU[kk][0].y, aU[kk][1].x, aU[kk][1].y);
+                    st4(o + 2 * plane, aV[kk][0].x, aV[kk][0].y, aV[kk][1].x, aV[kk][1].y);
+                    const float* hrow = s_in + (k0 + kk + R) * SW + c0 + R;
+                    const float a4[4] = {aA[kk][0].x, aA[kk][0].y, aA[kk][1].x, aA[kk][1].y};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (v0 + c0 + j < W) ps = fmaf(hrow[j], a4[j], ps);
+                }
+            }
+            part = (double)ps;
+        }
+        const double tot = block_sum_double(part, red);
+        if (tid == 0) L.partials[dp->partial_off + local] = tot;
+    }
+}
+
+template <int R, bool ABS, int DTYPE>
+cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
+    constexpr int TW = kTileW, TH = 64;
+    constexpr int ROWS = TH + 2 * R;
+    constexpr int SW = ((TW + 2 * R + 3) & ~3) + 4;
+    constexpr int ES = DTYPE == ITC_U8 ? 1 : 4;
+    constexpr int RA = DTYPE == ITC_U8 ? 16 : ((R + 3) & ~3);
+    constexpr int BOX_BYTES = (TW + 2 * RA) * ROWS * ES;
+    constexpr int STAGE_BYTES = (BOX_BYTES + 127) & ~127;
+    const size_t smem = 128 + STAGE_BYTES + (size_t)ROWS * SW * 4 + 2 * (size_t)ROWS * TW * 4;
+    auto k = fields_tma_kernel<R, ABS, DTYPE>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem)) != cudaSuccess) return e;
+    const int grid = ntiles < sms * (per_sm > 0 ? per_sm : 1) ? ntiles : sms * (per_sm > 0 ? per_sm : 1);
+    k<<<grid, kThreads, smem, s>>>(L, ntiles);
+    return cudaGetLastError();
+}
+
+template <bool ABS, int DTYPE>
+cudaError_t dispatch(const FieldsLaunch& L, int ntiles, int R, cudaStream_t s) {
+    if (R == 6) return launch_tma<6, ABS, DTYPE>(L, ntiles, s);
+    if (R == 9) return launch_tma<9, ABS, DTYPE>(L, ntiles, s);
+    return launch_tma<12, ABS, DTYPE>(L, ntiles, s);
+}
+
+}  // namespace
+
+bool fields_tma_supported(int ndim, int Ru, int Rv) {
+    return ndim == 2 && Ru == Rv && (Ru == 6 || Ru == 9 || Ru == 12);
+}
+
+int fields_tma_box(int dtype, int R, int* box_w, int* box_h) {
+    const int ra = dtype == ITC_U8 ? 16 : ((R + 3) & ~3);
+    *box_w = kTileW + 2 * ra;
+    *box_h = 64 + 2 * R;
+    return 0;
+}
+
+cudaError_t launch_fields_tma(const FieldsLaunch& L, int ntiles, int R, int dtype, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    const bool abs_ = L.absolute != 0;
+    if (dtype == ITC_U8) return abs_ ? dispatch<true, ITC_U8>(L, ntiles, R, s) : dispatch<false, ITC_U8>(L, ntiles, R, s);
+    return abs_ ? dispatch<true, ITC_F32>(L, ntiles, R, s) : dispatch<false, ITC_F32>(L, ntiles, R, s);
+}
+
+}  // namespace itc

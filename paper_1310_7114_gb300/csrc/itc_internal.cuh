@@ -2,6 +2,7 @@
 // Nothing here is part of the public ABI (include/itc.h is).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (type only; the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,7 +15,7 @@ constexpr int kMaxTapsG = 2 * ITC_MAX_RADIUS_G + 1;
 constexpr int kMaxClasses = 16;     // distinct (sigma, trunc, flags, ndim, dtype) classes per plan
 constexpr int kThreads = 256;       // fields / backward CTA size
 constexpr int kTileW = 64;          // output columns per fields tile
-constexpr int kRunThreads = 256;    // codebook-iteration CTA size
+constexpr int kRunThreads = 128;    // codebook-iteration CTA size
 // Dynamic shared floats per codebook vector of the iteration and backward-codebook kernels:
 // w (3), a (1), D (3), s (1), E (3).
 constexpr int kCodebookSmemFloats = 11;
@@ -58,6 +59,7 @@ struct ClassInfo {
     Taps taps;
     int ndim, dtype, absolute, tile_h;
     int nimg, ntiles;
+    int tma;                    // every image of the class has a tensor map (TMA fields path)
     int list_off;               // offset (ints) of this class's image list in the plan int area
     int prefix_off;             // offset (ints) of the class tile prefix (nimg + 1 ints)
     long long partial_base;     // first partial of the class
@@ -68,6 +70,7 @@ struct PlanHeader {
     int B;
     int ncls;
     int max_M;
+    int max_dim[3];             // largest H, W, G over the plan's images (pair-table sizes)
     long long total_pixels;     // sum H*W (grad_h layout)
     long long fields_floats;    // sum of every image's field planes
     long long total_tiles;
@@ -80,6 +83,7 @@ struct PlanHeader {
     long long ws_scal_off;      // bytes: per-image backward scalars (4 doubles each)
     long long bwd_tiles;        // backward pixel tiles over all images
     int bwd_prefix_off;         // offset (ints) of the backward tile prefix (B + 1 ints)
+    long long tmap_off;         // bytes from plan start to CUtensorMap[B] (input tiles)
     ClassInfo cls[kMaxClasses];
 };
 
@@ -95,6 +99,8 @@ inline int default_tile_h(int ndim, int Ru) {
 
 // Kernel launch records (passed by value as __grid_constant__ parameters).
 struct FieldsLaunch {
+    CUtensorMap tmap_one;       // input tiles of the single image (TMA path)
+    const CUtensorMap* tmaps;   // per-image maps in the plan (batched TMA path)
     Taps taps;
     const ImageDesc* descs;     // plan descriptors (batched) or nullptr (single image)
     ImageDesc one;              // the single image when descs == nullptr
@@ -135,7 +141,7 @@ struct BackwardLaunch {
     int B;
 };
 
-constexpr int kBwdTileH = 16;   // backward pixel tile: 16 rows x 64 columns
+constexpr int kBwdTileH = 64;   // backward pixel tile: 64 rows x 64 columns
 constexpr int kBwdTileW = 64;
 constexpr int kGSlices = 8;     // 3-D fields: gray slices per CTA
 
@@ -146,7 +152,12 @@ namespace itc {
 cudaError_t launch_fields(const FieldsLaunch& L, int nblocks, int R_u, int R_v, int ndim, int dtype,
                           cudaStream_t s);
 cudaError_t launch_reduce_sxx(const double* partials, int n, double* out, cudaStream_t s);
-cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, int iters_cap, cudaStream_t s);
+// TMA-staged 2-D fields (itc_fields_tma.cu): the radii it is compiled for, its box per radius
+// and data type, and its launch.
+bool fields_tma_supported(int ndim, int Ru, int Rv);
+int fields_tma_box(int dtype, int R, int* box_w, int* box_h);
+cudaError_t launch_fields_tma(const FieldsLaunch& L, int ntiles, int R, int dtype, cudaStream_t s);
+cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s);
 cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles,
                             cudaStream_t s);
 }  // namespace itc

@@ -6,8 +6,11 @@
 //   gather   a_k = A(r_k), D_k = F(r_k) (- r_k a_k if absolute) + (r_k - w_k) a_k,
 //            r_k = round(w_k) clamped to the lattice                  (Eq. (accupdate) data terms)
 //   pairs    s_k = sum_j g(w_j - w_k),  E_k = sum_j g(w_j - w_k)(w_j - w_k)   (Eq. (origupdate))
-//            one warp per k, lanes stride over j, xor-shuffle reduction (fixed order)
-//   sums     S_XW = sum_k a_k, S_WW = sum_k s_k in double, c = S_XW / S_WW, D_cs of Eq. (1)
+//            one thread per k loops over every j in order (positions are broadcast from shared
+//            memory), so the per-k sums need no reduction; g = exp2f(-sum_i d_i^2 c_i) with
+//            log2(e) folded into c_i.
+//   sums     S_XW = sum_k a_k, S_WW = sum_k s_k in double (lanes, then warps, fixed order),
+//            c = S_XW / S_WW, D_cs of Eq. (1)
 //   update   w_k' = w_k + step_scale (D_k - c E_k) / a_k (double), rounded to the lattice
 //            unless ITC_CONTINUOUS; a_k = 0 keeps w_k.  Jacobi: every k reads the old W.
 #include <math.h>
@@ -18,10 +21,6 @@ namespace itc {
 namespace {
 
 __device__ __forceinline__ double warp_sum_d(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ float warp_sum_f(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
@@ -41,77 +40,28 @@ struct Sums {
     int empty;
 };
 
-// Gather, pair sums and block sums at the current W (in shared memory).
-__device__ void evaluate(const ImageDesc& D, const float* __restrict__ A, long long plane,
-                         int absolute, const float* sw, float* sa, float* sD, float* ss, float* sE,
-                         double* red, Sums* out) {
-    const int M = D.M, nd = D.ndim, tid = threadIdx.x;
-    for (int k = tid; k < M; k += blockDim.x) {
-        float r[3];
-        r[0] = lattice_round(sw[k * 3], D.H);
-        r[1] = lattice_round(sw[k * 3 + 1], D.W);
-        r[2] = nd == 3 ? lattice_round(sw[k * 3 + 2], D.G) : 0.f;
-        const long long o = ((long long)(int)r[2] * D.H + (int)r[0]) * D.fpitch + (int)r[1];
-        const float a = __ldg(A + o);
-        sa[k] = a;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            if (i < nd) {
-                const double f = (double)__ldg(A + (i + 1) * plane + o);
-                const double m = f - (absolute ? (double)r[i] * a : 0.0) + ((double)r[i] - (double)sw[k * 3 + i]) * a;
-                sD[k * 3 + i] = (float)m;
-            } else {
-                sD[k * 3 + i] = 0.f;
-            }
-        }
-    }
-    const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
-    for (int k = wid; k < M; k += nw) {
-        const float wk0 = sw[k * 3], wk1 = sw[k * 3 + 1], wk2 = sw[k * 3 + 2];
-        float s = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
-        for (int j = lane; j < M; j += 32) {
-            const float d0 = sw[j * 3] - wk0, d1 = sw[j * 3 + 1] - wk1;
-            const float d2 = nd == 3 ? sw[j * 3 + 2] - wk2 : 0.f;
-            const float g = expf(-(d0 * d0 * c0 + d1 * d1 * c1 + d2 * d2 * c2));
-            s += g;
-            e0 = fmaf(g, d0, e0);
-            e1 = fmaf(g, d1, e1);
-            e2 = fmaf(g, d2, e2);
-        }
-        s = warp_sum_f(s);
-        e0 = warp_sum_f(e0);
-        e1 = warp_sum_f(e1);
-        e2 = warp_sum_f(e2);
-        if (lane == 0) {
-            ss[k] = s;
-            sE[k * 3] = e0;
-            sE[k * 3 + 1] = e1;
-            sE[k * 3 + 2] = e2;
-        }
+// Block sums of (a, s, empty) in a fixed order: lanes, then warps.
+__device__ __forceinline__ void block_sums(double a, double s, int e, double* red, Sums* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    a = warp_sum_d(a);
+    s = warp_sum_d(s);
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) {
+        red[wid * 3] = a;
+        red[wid * 3 + 1] = s;
+        red[wid * 3 + 2] = (double)e;
     }
     __syncthreads();
-    if (wid == 0) {
-        double x = 0, y = 0;
-        int e = 0;
-        for (int k = lane; k < M; k += 32) {
-            x += (double)sa[k];
-            y += (double)ss[k];
-            e += !(sa[k] > 0.f);
-        }
-        x = warp_sum_d(x);
-        y = warp_sum_d(y);
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if (lane == 0) {
-            red[0] = x;
-            red[1] = y;
-            red[2] = (double)e;
-        }
+    double x = 0, y = 0, z = 0;
+    for (int w = 0; w < nw; ++w) {
+        x += red[w * 3];
+        y += red[w * 3 + 1];
+        z += red[w * 3 + 2];
     }
-    __syncthreads();
-    out->sxw = red[0];
-    out->sww = red[1];
-    out->empty = (int)red[2];
+    out->sxw = x;
+    out->sww = y;
+    out->empty = (int)z;
+    __syncthreads();   // red is reused by the next call
 }
 
 __device__ void write_stats(itc_stats* st, const Sums& s, double sxx, int moved, int iters_done) {
@@ -129,79 +79,113 @@ __device__ void write_stats(itc_stats* st, const Sums& s, double sxx, int moved,
     *st = r;
 }
 
-__global__ void __launch_bounds__(kRunThreads) run_kernel(const __grid_constant__ RunLaunch L) {
+// NPER: codebooks owned per thread (compile-time so the per-codebook state stays in registers).
+template <int NPER>
+__global__ void __launch_bounds__(kRunThreads, 4) run_kernel(const __grid_constant__ RunLaunch L) {
     const ImageDesc& D = L.descs ? L.descs[blockIdx.x] : L.one;
     const int M = D.M, nd = D.ndim, tid = threadIdx.x;
-    extern __shared__ __align__(16) float sm[];
-    float* sw = sm;             // M x 3 positions
-    float* sa = sw + 3 * M;     // M
-    float* sD = sa + M;         // M x 3
-    float* ss = sD + 3 * M;     // M
-    float* sE = ss + M;         // M x 3
-    __shared__ double red[4];
+    extern __shared__ __align__(16) float4 sw[];   // M positions (u, v, g, 0)
+    __shared__ double red[3 * (kRunThreads / 32)];
+    __shared__ double s_sxx;
 
-    // S_XX from the tile partials of this image, fixed order
-    double sxx = 0;
     if (L.sxx_single) {
-        sxx = *L.sxx_single;
-    } else {
+        if (tid == 0) s_sxx = *L.sxx_single;
+    } else if (tid < 32) {
         const long long nt = (long long)D.tiles_u * D.tiles_v * D.tiles_g;
-        if (tid < 32) {
-            double v = 0;
-            for (long long i = tid; i < nt; i += 32) v += L.partials[D.partial_off + i];
-            v = warp_sum_d(v);
-            if (tid == 0) red[3] = v;
-        }
-        __syncthreads();
-        sxx = red[3];
+        double v = 0;
+        for (long long i = tid; i < nt; i += 32) v += L.partials[D.partial_off + i];
+        v = warp_sum_d(v);
+        if (tid == 0) s_sxx = v;
     }
-
     const float* Win = L.W_in + D.w_off;
-    for (int k = tid; k < M; k += blockDim.x) {
-        for (int i = 0; i < 3; ++i) sw[k * 3 + i] = i < nd ? Win[k * nd + i] : 0.f;
-    }
+    for (int k = tid; k < M; k += blockDim.x)
+        sw[k] = make_float4(Win[k * nd], Win[k * nd + 1], nd == 3 ? Win[k * nd + 2] : 0.f, 0.f);
     __syncthreads();
+    const double sxx = s_sxx;
 
     const float* A = L.fields + D.field_off;
     const long long plane = D.plane_floats;
     const bool snap = !(D.flags & ITC_CONTINUOUS);
     const bool stop_fixed = (D.flags & ITC_STOP_ON_FIXED) != 0;
-    const int iters = D.iters;
+    // g(d) = exp(-sum_i d_i^2 / (2 sigma_i^2)) = 2^(-sum_i d_i^2 c_i), c_i = log2(e) / (2 sigma_i^2)
+    const float c0 = (float)(1.4426950408889634 * (double)D.inv2s2[0]);
+    const float c1 = (float)(1.4426950408889634 * (double)D.inv2s2[1]);
+    const float c2 = (float)(1.4426950408889634 * (double)D.inv2s2[2]);
+
     Sums s;
     int moved = 0, done = 0;
     bool stop = false;
     for (int t = 0;; ++t) {
-        if (!L.final_eval && t == iters) break;
-        evaluate(D, A, plane, L.absolute, sw, sa, sD, ss, sE, red, &s);
-        if (!L.final_eval && t == 0 && L.stats && tid == 0) write_stats(L.stats + blockIdx.x, s, sxx, 0, 0);
-        if (t == iters || stop) {
-            break;
+        if (!L.final_eval && t == D.iters) break;
+        // gather (issued first, consumed after the pair sums), then pair sums, per owned k
+        float a[NPER], Dm[NPER][3], Ek[NPER][3];
+        double pa = 0.0, ps = 0.0;
+        int pe = 0;
+#pragma unroll
+        for (int q = 0; q < NPER; ++q) {
+            const int k = tid + q * blockDim.x;
+            if (k >= M) break;
+            const float4 wk = sw[k];
+            const float r0 = lattice_round(wk.x, D.H), r1 = lattice_round(wk.y, D.W);
+            const float r2 = nd == 3 ? lattice_round(wk.z, D.G) : 0.f;
+            const long long o = ((long long)(int)r2 * D.H + (int)r0) * D.fpitch + (int)r1;
+            const float ak = __ldg(A + o);
+            const float f0 = __ldg(A + plane + o), f1 = __ldg(A + 2 * plane + o);
+            const float f2 = nd == 3 ? __ldg(A + 3 * plane + o) : 0.f;
+            float s_ = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            for (int j = 0; j < M; ++j) {
+                const float4 wj = sw[j];
+                const float d0 = wj.x - wk.x, d1 = wj.y - wk.y, d2 = wj.z - wk.z;
+                const float g = exp2f(-(d0 * d0 * c0 + d1 * d1 * c1 + d2 * d2 * c2));
+                s_ += g;
+                e0 = fmaf(g, d0, e0);
+                e1 = fmaf(g, d1, e1);
+                e2 = fmaf(g, d2, e2);
+            }
+            a[q] = ak;
+            const float rr[3] = {r0, r1, r2}, ww[3] = {wk.x, wk.y, wk.z}, ff[3] = {f0, f1, f2};
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double m = (double)ff[i] - (L.absolute ? (double)rr[i] * ak : 0.0) + ((double)rr[i] - (double)ww[i]) * ak;
+                Dm[q][i] = i < nd ? (float)m : 0.f;
+            }
+            Ek[q][0] = e0;
+            Ek[q][1] = e1;
+            Ek[q][2] = e2;
+            pa += (double)ak;
+            ps += (double)s_;
+            pe += !(ak > 0.f);
         }
+        block_sums(pa, ps, pe, red, &s);
+        if (!L.final_eval && t == 0 && L.stats && tid == 0) write_stats(L.stats + blockIdx.x, s, sxx, 0, 0);
+        if (t == D.iters || stop) break;
+        // update (Jacobi: every k above read the old W; the barrier in block_sums separates them)
         const double c = s.sxw / s.sww;
         int mv = 0;
-        for (int k = tid; k < M; k += blockDim.x) {
-            const float a = sa[k];
-            if (!(a > 0.f)) continue;
+#pragma unroll
+        for (int q = 0; q < NPER; ++q) {
+            const int k = tid + q * blockDim.x;
+            if (k >= M) break;
+            if (!(a[q] > 0.f)) continue;
+            float4 w = sw[k];
+            float nw[3] = {w.x, w.y, w.z};
             bool kmoved = false;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 if (i >= nd) break;
                 const int ni = i == 0 ? D.H : (i == 1 ? D.W : D.G);
-                const double w = sw[k * 3 + i];
-                const double raw = w + (double)D.step_scale * ((double)sD[k * 3 + i] - c * (double)sE[k * 3 + i]) / (double)a;
-                double nwv;
-                if (snap) nwv = lattice_round_d(raw, ni);
-                else nwv = fmin(fmax(raw, 0.0), (double)(ni - 1));
+                const double raw = (double)nw[i] + (double)D.step_scale * ((double)Dm[q][i] - c * (double)Ek[q][i]) / (double)a[q];
+                const double nwv = snap ? lattice_round_d(raw, ni) : fmin(fmax(raw, 0.0), (double)(ni - 1));
                 const float nf = (float)nwv;
-                kmoved |= (nf != sw[k * 3 + i]);
-                sw[k * 3 + i] = nf;   // only thread k touches w_k in this phase
+                kmoved |= (nf != nw[i]);
+                nw[i] = nf;
             }
+            sw[k] = make_float4(nw[0], nw[1], nw[2], 0.f);
             mv += kmoved;
         }
         moved = __syncthreads_count(mv);
         ++done;
         if (stop_fixed && moved == 0) stop = true;
-        // the next pass re-reads W (evaluate syncs before the pair sums; sw writes are complete)
     }
     if (L.final_eval && L.stats && tid == 0) write_stats(L.stats + blockIdx.x, s, sxx, moved, done);
     if (!L.final_eval && L.stats && tid == 0) {
@@ -210,25 +194,29 @@ __global__ void __launch_bounds__(kRunThreads) run_kernel(const __grid_constant_
     }
     float* Wout = L.W_out + D.w_off;
     for (int k = tid; k < M; k += blockDim.x) {
+        const float4 w = sw[k];
+        const float ww[3] = {w.x, w.y, w.z};
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             if (i >= nd) break;
             const int ni = i == 0 ? D.H : (i == 1 ? D.W : D.G);
-            Wout[k * nd + i] = sw[k * 3 + i];
-            if (L.W_lattice) L.W_lattice[D.w_off + k * nd + i] = (int)lattice_round(sw[k * 3 + i], ni);
+            Wout[k * nd + i] = ww[i];
+            if (L.W_lattice) L.W_lattice[D.w_off + k * nd + i] = (int)lattice_round(ww[i], ni);
         }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, int iters_cap, cudaStream_t s) {
-    (void)iters_cap;
+cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s) {
+    (void)max_dim;
     if (nimg <= 0) return cudaSuccess;
-    const size_t smem = (size_t)max_M * kCodebookSmemFloats * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(run_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)max_M * sizeof(float4);
+    const int nper = (max_M + kRunThreads - 1) / kRunThreads;
+    auto k = nper <= 1 ? run_kernel<1> : nper <= 2 ? run_kernel<2> : nper <= 4 ? run_kernel<4> : run_kernel<16>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    run_kernel<<<nimg, kRunThreads, smem, s>>>(L);
+    k<<<nimg, kRunThreads, smem, s>>>(L);
     return cudaGetLastError();
 }
 

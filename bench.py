@@ -234,6 +234,32 @@ def run_ours(args, rank, world, local_rank):
     i_ms = [e[1].elapsed_time(e[2]) for e in ev]
     b_ms = [e[2].elapsed_time(e[3]) for e in ev]
 
+    # the same step captured once as a CUDA graph and replayed (one launch per step from the host)
+    graph_ms = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            step()   # warm the capture stream
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = g0.elapsed_time(g1) / args.steps
+        del g
+    except Exception as exc:  # report, never fall back silently
+        graph_ms = f"capture failed: {type(exc).__name__}: {exc}"
+
     # e2e through the C ABI: host inputs -> device, itc_run + itc_backward, results -> host
     host_buf = buf.cpu().pin_memory()
     host_W0 = W0.cpu().pin_memory()
@@ -332,6 +358,9 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                 "path": "itc_run + itc_backward through the C ABI; inputs from pinned host memory; W, grad_W, "
                         "stats back to the host"},
+        "graph": ({"value": world * B / (graph_ms / 1000.0), "unit": "images/s", "ms_per_step": graph_ms,
+                   "note": "the same step captured in one CUDA graph and replayed"}
+                  if isinstance(graph_ms, float) else {"error": graph_ms}),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }

@@ -257,7 +257,7 @@ int itc_step(const itc_image* img, const itc_params* p, const float* fields, con
     L.absolute = (p->flags & ITC_FIELDS_ABSOLUTE) ? 1 : 0;
     L.final_eval = 0;
     const int dims[3] = {img->H, img->W, img->ndim == 3 ? img->G : 1};
-    return cuda_status(launch_run(L, 1, M, dims, reinterpret_cast<cudaStream_t>(stream)));
+    return cuda_status(launch_run(L, 1, M, dims, reinterpret_cast<cudaStream_t>(stream), img->ndim));
 }
 
 size_t itc_plan_bytes(int B) {
@@ -336,6 +336,7 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         h->max_dim[0] = d.H > h->max_dim[0] ? d.H : h->max_dim[0];
         h->max_dim[1] = d.W > h->max_dim[1] ? d.W : h->max_dim[1];
         h->max_dim[2] = d.G > h->max_dim[2] ? d.G : h->max_dim[2];
+        h->ndim_mask |= 1 << d.ndim;
     }
     h->fields_floats = foff;
     h->total_pixels = ghoff;
@@ -453,7 +454,12 @@ int itc_run_iterate(const void* plan_host, const void* plan_dev, float* W, itc_s
     R.stats = stats;
     R.absolute = 0;
     R.final_eval = 1;
-    return cuda_status(launch_run(R, h->B, h->max_M, h->max_dim, reinterpret_cast<cudaStream_t>(stream)));
+    for (int nd = 2; nd <= 3; ++nd) {
+        if (!(h->ndim_mask & (1 << nd))) continue;
+        const int rc = cuda_status(launch_run(R, h->B, h->max_M, h->max_dim, reinterpret_cast<cudaStream_t>(stream), nd));
+        if (rc) return rc;
+    }
+    return ITC_OK;
 }
 
 int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,

@@ -67,62 +67,78 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
     const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
     const int Ru = D.R[0], Rv = D.R[1], Rg = D.R[2];
 
-    // window sums at the real w_k over the box around round(w_k)
-    for (int k = wid; k < M; k += nw) {
-        const float w0 = sw[k * 3], w1 = sw[k * 3 + 1], w2 = sw[k * 3 + 2];
-        const int r0 = lattice_round_i(w0, D.H), r1 = lattice_round_i(w1, D.W);
-        const int r2 = nd == 3 ? lattice_round_i(w2, D.G) : 0;
-        const int ua = max(0, r0 - Ru), ub = min(D.H - 1, r0 + Ru);
-        const int va = max(0, r1 - Rv), vb = min(D.W - 1, r1 + Rv);
-        const int nv = vb - va + 1, npos = (ub - ua + 1) * nv;
-        float a = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-        for (int p = lane; p < npos; p += 32) {
-            const int u = ua + p / nv, v = va + p % nv;
-            const float h = pixel_weight(D, u, v);
-            if (h == 0.f) continue;
-            const float du = (float)u - w0, dv = (float)v - w1;
-            float dg = 0.f;
-            if (nd == 3) {
-                const int gl = pixel_gray(D, u, v);
-                if (abs(gl - r2) > Rg) continue;
-                dg = (float)gl - w2;
-            }
-            const float g = h * expf(-(du * du * c0 + dv * dv * c1 + dg * dg * c2));
-            a += g;
-            d0 = fmaf(g, du, d0);
-            d1 = fmaf(g, dv, d1);
-            d2 = fmaf(g, dg, d2);
+    // a_k and D_k: on the lattice (every w_k integral and inside it) they are the stored field
+    // values at w_k; otherwise window sums around round(w_k) with the kernel at the real w_k
+    int off_lattice = 0;
+    for (int k = tid; k < M; k += blockDim.x)
+        for (int i = 0; i < nd; ++i) {
+            const float w = sw[k * 3 + i];
+            const int ni = i == 0 ? D.H : (i == 1 ? D.W : D.G);
+            off_lattice |= (w != rintf(w)) || !(w >= 0.f) || !(w <= (float)(ni - 1));
         }
-        a = warp_sum_f(a);
-        d0 = warp_sum_f(d0);
-        d1 = warp_sum_f(d1);
-        d2 = warp_sum_f(d2);
-        if (lane == 0) {
-            sa[k] = a;
-            sD[k * 3] = d0;
-            sD[k * 3 + 1] = d1;
-            sD[k * 3 + 2] = d2;
+    const bool gather = !__syncthreads_or(off_lattice);
+    if (gather) {
+        const float* A = L.fields + D.field_off;
+        for (int k = tid; k < M; k += blockDim.x) {
+            const int r0 = (int)sw[k * 3], r1 = (int)sw[k * 3 + 1], r2 = nd == 3 ? (int)sw[k * 3 + 2] : 0;
+            const long long o = ((long long)r2 * D.H + r0) * D.fpitch + r1;
+            sa[k] = __ldg(A + o);
+            for (int i = 0; i < 3; ++i) sD[k * 3 + i] = i < nd ? __ldg(A + (i + 1) * D.plane_floats + o) : 0.f;
+        }
+    } else {
+        for (int k = wid; k < M; k += nw) {
+            const float w0 = sw[k * 3], w1 = sw[k * 3 + 1], w2 = sw[k * 3 + 2];
+            const int r0 = lattice_round_i(w0, D.H), r1 = lattice_round_i(w1, D.W);
+            const int r2 = nd == 3 ? lattice_round_i(w2, D.G) : 0;
+            const int ua = max(0, r0 - Ru), ub = min(D.H - 1, r0 + Ru);
+            const int va = max(0, r1 - Rv), vb = min(D.W - 1, r1 + Rv);
+            const int nv = vb - va + 1, npos = (ub - ua + 1) * nv;
+            float a = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+            for (int p = lane; p < npos; p += 32) {
+                const int u = ua + p / nv, v = va + p % nv;
+                const float h = pixel_weight(D, u, v);
+                if (h == 0.f) continue;
+                const float du = (float)u - w0, dv = (float)v - w1;
+                float dg = 0.f;
+                if (nd == 3) {
+                    const int gl = pixel_gray(D, u, v);
+                    if (abs(gl - r2) > Rg) continue;
+                    dg = (float)gl - w2;
+                }
+                const float g = h * expf(-(du * du * c0 + dv * dv * c1 + dg * dg * c2));
+                a += g;
+                d0 = fmaf(g, du, d0);
+                d1 = fmaf(g, dv, d1);
+                d2 = fmaf(g, dg, d2);
+            }
+            a = warp_sum_f(a);
+            d0 = warp_sum_f(d0);
+            d1 = warp_sum_f(d1);
+            d2 = warp_sum_f(d2);
+            if (lane == 0) {
+                sa[k] = a;
+                sD[k * 3] = d0;
+                sD[k * 3 + 1] = d1;
+                sD[k * 3 + 2] = d2;
+            }
         }
     }
-    // codebook interaction sums
-    for (int k = wid; k < M; k += nw) {
-        const float wk0 = sw[k * 3], wk1 = sw[k * 3 + 1], wk2 = sw[k * 3 + 2];
-        float s = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
-        for (int j = lane; j < M; j += 32) {
-            const float d0 = sw[j * 3] - wk0, d1 = sw[j * 3 + 1] - wk1;
-            const float d2 = nd == 3 ? sw[j * 3 + 2] - wk2 : 0.f;
-            const float g = expf(-(d0 * d0 * c0 + d1 * d1 * c1 + d2 * d2 * c2));
-            s += g;
-            e0 = fmaf(g, d0, e0);
-            e1 = fmaf(g, d1, e1);
-            e2 = fmaf(g, d2, e2);
-        }
-        s = warp_sum_f(s);
-        e0 = warp_sum_f(e0);
-        e1 = warp_sum_f(e1);
-        e2 = warp_sum_f(e2);
-        if (lane == 0) {
-            ss[k] = s;
+    // codebook interaction sums: one thread per k, every j in order
+    {
+        const float q0 = (float)(1.4426950408889634 * (double)c0), q1 = (float)(1.4426950408889634 * (double)c1);
+        const float q2 = (float)(1.4426950408889634 * (double)c2);
+        for (int k = tid; k < M; k += blockDim.x) {
+            const float wk0 = sw[k * 3], wk1 = sw[k * 3 + 1], wk2 = sw[k * 3 + 2];
+            float s_ = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            for (int j = 0; j < M; ++j) {
+                const float d0 = sw[j * 3] - wk0, d1 = sw[j * 3 + 1] - wk1, d2 = sw[j * 3 + 2] - wk2;
+                const float g = exp2f(-(d0 * d0 * q0 + d1 * d1 * q1 + d2 * d2 * q2));
+                s_ += g;
+                e0 = fmaf(g, d0, e0);
+                e1 = fmaf(g, d1, e1);
+                e2 = fmaf(g, d2, e2);
+            }
+            ss[k] = s_;
             sE[k * 3] = e0;
             sE[k * 3 + 1] = e1;
             sE[k * 3 + 2] = e2;
@@ -195,7 +211,7 @@ constexpr int kChunk = 64;   // codebooks staged per round in the pixel kernel
 // Chunks of 64 listed codebooks are staged as a (64 x 64) and b (64 x 64) in shared memory and
 // every thread accumulates a 4 x 4 block of pixels in l order (deterministic, no atomics).  In
 // 3-D the g factor depends on each pixel's gray level and is applied per pixel and codebook.
-__global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_constant__ BackwardLaunch L) {
+__global__ void __launch_bounds__(kThreads, 4) bwd_pixels_kernel(const __grid_constant__ BackwardLaunch L) {
     const int img = find_image(L.bwd_prefix, L.B + 1, blockIdx.x);
     const ImageDesc& D = L.descs[img];
     const int t = blockIdx.x - __ldg(L.bwd_prefix + img);
@@ -207,6 +223,8 @@ __global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_const
     __shared__ __align__(16) float sb[kChunk][kBwdTileW];
     __shared__ float sgw[kChunk];                       // 3-D: w_g of the chunk's codebooks
     __shared__ int sgr[kChunk];                         // 3-D: round(w_g)
+    __shared__ float scw[kChunk][2];                    // w_u, w_v of the chunk's codebooks
+    __shared__ int scr[kChunk][2];                      // their rounded lattice sites
     __shared__ int wcount[kThreads / 32];
     __shared__ int s_total;
     const float* Wk = L.W + D.w_off;
@@ -237,8 +255,18 @@ __global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_const
     const int nl = s_total;
     const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
 
-    // this thread's 4 x 4 block
+    // this thread's 4 x 4 block; in 2-D its field values are loaded now so that their latency
+    // overlaps the stamping below
     const int pr = (tid >> 4) * 4, pc = (tid & 15) * 4;
+    float4 a4[4];
+    if (nd == 2 && v0 + pc < D.W) {
+        const float* A2 = L.fields + D.field_off;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int u = min(u0 + pr + i, D.H - 1);
+            a4[i] = __ldg(reinterpret_cast<const float4*>(A2 + (long long)u * D.fpitch + v0 + pc));
+        }
+    }
     int gray[4][4];
     if (nd == 3) {
 #pragma unroll
@@ -257,22 +285,26 @@ __global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_const
 
     for (int base = 0; base < nl; base += kChunk) {
         const int nc = min(kChunk, nl - base);
-        // stage the separable factors of this chunk
-        for (int i = tid; i < kChunk * kBwdTileH; i += blockDim.x) {
-            const int l = i / kBwdTileH, r = i % kBwdTileH;
-            float av = 0.f, bv = 0.f;
-            if (l < nc) {
-                const int k = lk[base + l];
-                const float w0 = Wk[k * nd], w1 = Wk[k * nd + 1];
-                const int r0 = lattice_round_i(w0, D.H), r1 = lattice_round_i(w1, D.W);
-                const int u = u0 + r, v = v0 + r;
-                if (u < D.H && abs(u - r0) <= Ru) { const float d = (float)u - w0; av = expf(-d * d * c0); }
-                if (v < D.W && abs(v - r1) <= Rv) { const float d = (float)v - w1; bv = expf(-d * d * c1); }
-                if (nd == 3 && r == 0) {
-                    sgw[l] = Wk[k * nd + 2];
-                    sgr[l] = lattice_round_i(Wk[k * nd + 2], D.G);
-                }
+        // the chunk's codebook positions, then its separable factors
+        if (tid < nc) {
+            const int k = lk[base + tid];
+            const float w0 = Wk[k * nd], w1 = Wk[k * nd + 1];
+            scw[tid][0] = w0;
+            scw[tid][1] = w1;
+            scr[tid][0] = lattice_round_i(w0, D.H);
+            scr[tid][1] = lattice_round_i(w1, D.W);
+            if (nd == 3) {
+                sgw[tid] = Wk[k * nd + 2];
+                sgr[tid] = lattice_round_i(Wk[k * nd + 2], D.G);
             }
+        }
+        __syncthreads();
+        for (int i = tid; i < nc * kBwdTileH; i += blockDim.x) {
+            const int l = i / kBwdTileH, r = i % kBwdTileH;
+            const int u = u0 + r, v = v0 + r;
+            float av = 0.f, bv = 0.f;
+            if (u < D.H && abs(u - scr[l][0]) <= Ru) { const float d = (float)u - scw[l][0]; av = expf(-d * d * c0); }
+            if (v < D.W && abs(v - scr[l][1]) <= Rv) { const float d = (float)v - scw[l][1]; bv = expf(-d * d * c1); }
             sa[l][r] = av;
             sb[l][r] = bv;
         }
@@ -304,26 +336,32 @@ __global__ void __launch_bounds__(kThreads) bwd_pixels_kernel(const __grid_const
         __syncthreads();
     }
 
-    const double s1 = L.scal[img * 4 + 0], s2 = L.scal[img * 4 + 1];
+    const float s1 = (float)L.scal[img * 4 + 0], s2 = (float)L.scal[img * 4 + 1];
     const float* A = L.fields + D.field_off;
+    if (v0 + pc >= D.W) return;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int u = u0 + pr + i;
         if (u >= D.H) break;
+        float* out = L.grad_h + D.gh_off + (long long)u * D.W + v0 + pc;
+        if (nd == 2) {
+            // 4 field values from one 16-byte load (rows are padded to a multiple of 4 floats)
+            const float av[4] = {a4[i].x, a4[i].y, a4[i].z, a4[i].w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int v = v0 + pc + j;
-            if (v >= D.W) break;
-            long long o = (long long)u * D.fpitch + v;
-            float* out = L.grad_h + D.gh_off + (long long)u * D.W + v;
-            if (nd == 3) {
+            for (int j = 0; j < 4; ++j)
+                if (v0 + pc + j < D.W) out[j] = s1 * av[j] - s2 * acc[i][j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int v = v0 + pc + j;
+                if (v >= D.W) break;
                 if (gray[i][j] >= D.G) {   // a voxel outside the lattice: no field value
-                    *out = 0.f;
+                    out[j] = 0.f;
                     continue;
                 }
-                o += (long long)gray[i][j] * D.H * D.fpitch;
+                const long long o = ((long long)gray[i][j] * D.H + u) * D.fpitch + v;
+                out[j] = s1 * __ldg(A + o) - s2 * acc[i][j];
             }
-            *out = (float)(s1 * (double)__ldg(A + o) - s2 * (double)acc[i][j]);
         }
     }
 }

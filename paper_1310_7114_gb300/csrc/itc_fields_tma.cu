@@ -50,20 +50,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-__device__ __forceinline__ double block_sum_double(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double t = 0;
-    if (wid == 0) {
-        t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    }
-    return t;
-}
-
 __device__ __forceinline__ int find_image(const int* __restrict__ prefix, int n, int b) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -118,6 +104,10 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
     __shared__ __align__(8) uint64_t bar;
     __shared__ double red[32];
     __shared__ int s_abort;
+    // Zero tracking: rowmask[r] bit q = staged row r has a nonzero in its 4-column group q;
+    // colbits[b] = bits over staged rows whose T (8-column block b) is not known to be zero.
+    __shared__ uint32_t rowmask[ROWS];
+    __shared__ uint32_t colbits[TW / 8][4];
     const Taps& tp = L.taps;
     const int tid = threadIdx.x;
 
@@ -142,6 +132,19 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
     uint32_t parity = 0;
     const int kb = tid >> 4, cg = tid & 15;
     const int k0 = kb * K, c0 = cg * 4;
+    // S_XX share of the previous tile: its warps leave their sums in red[]; thread 0 adds them
+    // (warp order) after the next barrier, so no tile needs a barrier of its own for it
+    long long pending = -1;
+    auto flush = [&]() {
+        if (pending >= 0) {
+            static_assert(kThreads / 32 == 8, "eight warp sums");
+            // the xor-butterfly order of the block reduction in fields_kernel, so both kernels
+            // give bit-identical partials
+            const double tot = ((red[0] + red[4]) + (red[2] + red[6])) + ((red[1] + red[5]) + (red[3] + red[7]));
+            L.partials[pending] = tot;
+            pending = -1;
+        }
+    };
 
     for (; t < ntiles; t += gridDim.x) {
         int local, img;
@@ -152,31 +155,46 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
         const long long plane = dp->plane_floats;
 
         if (tid == 0 && !wait_stage(&bar, parity)) s_abort = 1;
-        __syncthreads();
+        __syncthreads();   // the staged tile has landed; the previous tile's passes are done
+        if (tid == 0) flush();
         if (s_abort) {
             if (tid == 0) L.partials[dp->partial_off + local] = __longlong_as_double(0x7ff8000000000000LL);
             return;   // S_XX of the image becomes NaN: the host sees a non-finite status
         }
         parity ^= 1u;
 
-        // staged box -> float input tile, columns shifted so that s_in column 0 is v0 - R
+        // staged box -> float input tile, columns shifted so that s_in column 0 is v0 - R; one
+        // warp per staged row, one 4-column group per lane, a ballot gives the row's zero mask
         int nonzero = 0;
-        for (int i = tid; i < ROWS * (SW / 4); i += kThreads) {
-            const int r = i / (SW / 4), c = (i % (SW / 4)) * 4;
-            float x[4];
+        {
+            constexpr int NG = SW / 4;
+            static_assert(NG <= 32, "one lane per 4-column group");
+            const int wid = tid >> 5, lane = tid & 31;
+            for (int r = wid; r < ROWS; r += kThreads / 32) {
+                int nz = 0;
+                if (lane < NG) {
+                    const int c = lane * 4;
+                    float x[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int cc = c + j;
-                float v = 0.f;
-                if (cc < TW + 2 * R) {
-                    const int sc = r * BW + cc + (RA - R);
-                    if (DTYPE == ITC_U8) v = (float)stage[sc];
-                    else v = reinterpret_cast<const float*>(stage)[sc];
+                    for (int j = 0; j < 4; ++j) {
+                        const int cc = c + j;
+                        float v = 0.f;
+                        if (cc < TW + 2 * R) {
+                            const int sc = r * BW + cc + (RA - R);
+                            // byte -> float exactly: 2^23 + b as a float, minus 2^23
+                            if (DTYPE == ITC_U8) v = __int_as_float(0x4B000000 | (int)stage[sc]) - 8388608.f;
+                            else v = reinterpret_cast<const float*>(stage)[sc];
+                        }
+                        x[j] = v;
+                        nz |= (v != 0.f);
+                    }
+                    st4(s_in + r * SW + c, x[0], x[1], x[2], x[3]);
                 }
-                x[j] = v;
-                nonzero |= (v != 0.f);
+                const unsigned m = __ballot_sync(0xffffffffu, nz);
+                if (lane == 0) rowmask[r] = m;
+                nonzero |= nz;
             }
-            st4(s_in + r * SW + c, x[0], x[1], x[2], x[3]);
+            if (tid < 32) colbits[tid >> 2][tid & 3] = 0u;
         }
         const int any = __syncthreads_or(nonzero);   // the stage is free from here on
         if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
@@ -209,6 +227,13 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
                 st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + 4, 0.f, 0.f, 0.f, 0.f);
                 continue;
             }
+            constexpr uint32_t WMASK = (1u << (NWIN / 4)) - 1u;
+            if (((rowmask[r] >> (c >> 2)) & WMASK) == 0u) {   // every input of the window is zero
+                st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + 4, 0.f, 0.f, 0.f, 0.f);
+                st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + 4, 0.f, 0.f, 0.f, 0.f);
+                continue;
+            }
+            atomicOr(&colbits[item & 7][r >> 5], 1u << (r & 31));
             float x[NWIN];
             const float* src = s_in + r * SW + c;
 #pragma unroll
@@ -243,8 +268,27 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
         __syncthreads();
 
         // ---- pass along u: K rows x 4 columns per thread, column pairs per packed FMA
-        double part = 0.0;
+        // T rows k0 .. k0 + K + 2R - 1 of this thread's 8-column block all zero -> outputs are zero
+        bool t_any = false;
         if (col_active) {
+            const uint32_t* cb = colbits[cg >> 1];
+            const int rlo = k0, w0 = rlo >> 5;
+            const unsigned long long both = ((unsigned long long)cb[w0 + 1] << 32) | cb[w0];
+            const unsigned long long need = (K + 2 * R >= 64) ? ~0ull : ((1ull << (K + 2 * R)) - 1ull);
+            t_any = ((both >> (rlo & 31)) & need) != 0ull;
+            if (!t_any) {
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const int u = u0 + k0 + kk;
+                    if (u >= H) break;
+                    float* o = fbase + (long long)u * fpitch + v0 + c0;
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) st4(o + f * plane, 0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+        double part = 0.0;
+        if (col_active && t_any) {
             float2 aA[K][2], aU[K][2], aV[K][2];
 #pragma unroll
             for (int kk = 0; kk < K; ++kk)
@@ -302,9 +346,12 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
             }
             part = (double)ps;
         }
-        const double tot = block_sum_double(part, red);
-        if (tid == 0) L.partials[dp->partial_off + local] = tot;
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((tid & 31) == 0) red[tid >> 5] = part;
+        if (tid == 0) pending = dp->partial_off + local;
     }
+    __syncthreads();
+    if (tid == 0) flush();
 }
 
 template <int R, bool ABS, int DTYPE>

@@ -70,7 +70,8 @@ struct PlanHeader {
     int B;
     int ncls;
     int max_M;
-    int max_dim[3];             // largest H, W, G over the plan's images (pair-table sizes)
+    int max_dim[3];             // largest H, W, G over the plan's images
+    int ndim_mask;              // bit 2: the plan has 2-D images; bit 3: it has 3-D images
     long long total_pixels;     // sum H*W (grad_h layout)
     long long fields_floats;    // sum of every image's field planes
     long long total_tiles;
@@ -157,7 +158,8 @@ cudaError_t launch_reduce_sxx(const double* partials, int n, double* out, cudaSt
 bool fields_tma_supported(int ndim, int Ru, int Rv);
 int fields_tma_box(int dtype, int R, int* box_w, int* box_h);
 cudaError_t launch_fields_tma(const FieldsLaunch& L, int ntiles, int R, int dtype, cudaStream_t s);
-cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s);
+// ndim: the lattice dimension of every image of the launch (2 or 3)
+cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s, int ndim);
 cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles,
                             cudaStream_t s);
 }  // namespace itc

@@ -9,17 +9,24 @@
 //            one thread per k loops over every j in order (positions are broadcast from shared
 //            memory), so the per-k sums need no reduction; g = exp2f(-sum_i d_i^2 c_i) with
 //            log2(e) folded into c_i.
-//   sums     S_XW = sum_k a_k, S_WW = sum_k s_k in double (lanes, then warps, fixed order),
-//            c = S_XW / S_WW, D_cs of Eq. (1)
-//   update   w_k' = w_k + step_scale (D_k - c E_k) / a_k (double), rounded to the lattice
-//            unless ITC_CONTINUOUS; a_k = 0 keeps w_k.  Jacobi: every k reads the old W.
+//   sums     S_XW = sum_k a_k, S_WW = sum_k s_k (FP32 shuffle trees, then the warps in order),
+//            c = S_XW / S_WW, D_cs of Eq. (1) in double at the reported W
+//   update   w_k' = w_k + step_scale (D_k - c E_k) / a_k, rounded to the lattice unless
+//            ITC_CONTINUOUS (on the lattice w_k is an integer, so w_k + round(delta) is exact in
+//            FP32); a_k = 0 keeps w_k.  Jacobi: every k reads the old W.
 #include <math.h>
+
+#include <type_traits>
 
 #include "itc_internal.cuh"
 
 namespace itc {
 namespace {
 
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -30,37 +37,34 @@ __device__ __forceinline__ float lattice_round(float x, int n) {
     return fminf(fmaxf(r, 0.f), (float)(n - 1));
 }
 
-__device__ __forceinline__ double lattice_round_d(double x, int n) {
-    double r = floor(x + 0.5);
-    return fmin(fmax(r, 0.0), (double)(n - 1));
-}
-
 struct Sums {
-    double sxw, sww;
+    float sxw, sww;
     int empty;
 };
 
-// Block sums of (a, s, empty) in a fixed order: lanes, then warps.
-__device__ __forceinline__ void block_sums(double a, double s, int e, double* red, Sums* out) {
+// Block sums of (a, s, empty), fixed order: a shuffle tree per warp, then the warps in order.
+// FP32 trees keep the relative error of S_XW and S_WW near log2(M) ulp.
+__device__ __forceinline__ void block_sums(float a, float s, int e, float* red, Sums* out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    a = warp_sum_d(a);
-    s = warp_sum_d(s);
+    a = warp_sum(a);
+    s = warp_sum(s);
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
     if (lane == 0) {
         red[wid * 3] = a;
         red[wid * 3 + 1] = s;
-        red[wid * 3 + 2] = (double)e;
+        red[wid * 3 + 2] = __int_as_float(e);
     }
     __syncthreads();
-    double x = 0, y = 0, z = 0;
+    float x = 0.f, y = 0.f;
+    int z = 0;
     for (int w = 0; w < nw; ++w) {
         x += red[w * 3];
         y += red[w * 3 + 1];
-        z += red[w * 3 + 2];
+        z += __float_as_int(red[w * 3 + 2]);
     }
     out->sxw = x;
     out->sww = y;
-    out->empty = (int)z;
+    out->empty = z;
     __syncthreads();   // red is reused by the next call
 }
 
@@ -69,8 +73,8 @@ __device__ void write_stats(itc_stats* st, const Sums& s, double sxx, int moved,
     r.sxw = s.sxw;
     r.sww = s.sww;
     r.sxx = sxx;
-    r.c = s.sxw / s.sww;
-    r.dcs = s.sxw > 0 ? log(s.sww) + log(sxx) - 2.0 * log(s.sxw) : INFINITY;
+    r.c = (double)s.sxw / (double)s.sww;
+    r.dcs = s.sxw > 0 ? log((double)s.sww) + log(sxx) - 2.0 * log((double)s.sxw) : INFINITY;
     r.empty = s.empty;
     r.moved = moved;
     r.iters_done = iters_done;
@@ -79,108 +83,164 @@ __device__ void write_stats(itc_stats* st, const Sums& s, double sxx, int moved,
     *st = r;
 }
 
+// The image fields the iteration needs, copied to registers once.
+struct Img {
+    const float* A;
+    long long plane;
+    int H, W, G, fpitch, M, iters, flags;
+    float step;
+};
+
 // NPER: codebooks owned per thread (compile-time so the per-codebook state stays in registers).
-template <int NPER>
-__global__ void __launch_bounds__(kRunThreads, 4) run_kernel(const __grid_constant__ RunLaunch L) {
-    const ImageDesc& D = L.descs ? L.descs[blockIdx.x] : L.one;
-    const int M = D.M, nd = D.ndim, tid = threadIdx.x;
-    extern __shared__ __align__(16) float4 sw[];   // M positions (u, v, g, 0)
-    __shared__ double red[3 * (kRunThreads / 32)];
+// ND: lattice dimension (2 or 3).
+template <int NPER, int ND>
+__global__ void __launch_bounds__(kRunThreads, 6) run_kernel(const __grid_constant__ RunLaunch L) {
+    using P = typename std::conditional<ND == 2, float2, float4>::type;
+    const ImageDesc& Dg = L.descs ? L.descs[blockIdx.x] : L.one;
+    if (Dg.ndim != ND) return;   // a mixed plan launches once per dimension
+    Img D;
+    D.A = L.fields + Dg.field_off;
+    D.plane = Dg.plane_floats;
+    D.H = Dg.H; D.W = Dg.W; D.G = Dg.G; D.fpitch = Dg.fpitch; D.M = Dg.M; D.iters = Dg.iters;
+    D.flags = Dg.flags; D.step = Dg.step_scale;
+    // g(d) = exp(-sum_i d_i^2 / (2 sigma_i^2)) = 2^(-sum_i d_i^2 c_i), c_i = log2(e) / (2 sigma_i^2)
+    const float c0 = (float)(1.4426950408889634 * (double)Dg.inv2s2[0]);
+    const float c1 = (float)(1.4426950408889634 * (double)Dg.inv2s2[1]);
+    const float c2 = ND == 3 ? (float)(1.4426950408889634 * (double)Dg.inv2s2[2]) : 0.f;
+    const long long w_off = Dg.w_off;
+    const int M = D.M, tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    P* sw = reinterpret_cast<P*>(smraw);   // M positions
+    __shared__ float red[3 * (kRunThreads / 32)];
     __shared__ double s_sxx;
 
     if (L.sxx_single) {
         if (tid == 0) s_sxx = *L.sxx_single;
     } else if (tid < 32) {
-        const long long nt = (long long)D.tiles_u * D.tiles_v * D.tiles_g;
+        const long long nt = (long long)Dg.tiles_u * Dg.tiles_v * Dg.tiles_g;
+        const long long po = Dg.partial_off;
         double v = 0;
-        for (long long i = tid; i < nt; i += 32) v += L.partials[D.partial_off + i];
+        for (long long i = tid; i < nt; i += 32) v += L.partials[po + i];
         v = warp_sum_d(v);
         if (tid == 0) s_sxx = v;
     }
-    const float* Win = L.W_in + D.w_off;
-    for (int k = tid; k < M; k += blockDim.x)
-        sw[k] = make_float4(Win[k * nd], Win[k * nd + 1], nd == 3 ? Win[k * nd + 2] : 0.f, 0.f);
+    const float* Win = L.W_in + w_off;
+    for (int k = tid; k < M; k += blockDim.x) {
+        P w;
+        w.x = Win[k * ND];
+        w.y = Win[k * ND + 1];
+        if constexpr (ND == 3) { w.z = Win[k * ND + 2]; w.w = 0.f; }
+        sw[k] = w;
+    }
     __syncthreads();
     const double sxx = s_sxx;
-
-    const float* A = L.fields + D.field_off;
-    const long long plane = D.plane_floats;
     const bool snap = !(D.flags & ITC_CONTINUOUS);
     const bool stop_fixed = (D.flags & ITC_STOP_ON_FIXED) != 0;
-    // g(d) = exp(-sum_i d_i^2 / (2 sigma_i^2)) = 2^(-sum_i d_i^2 c_i), c_i = log2(e) / (2 sigma_i^2)
-    const float c0 = (float)(1.4426950408889634 * (double)D.inv2s2[0]);
-    const float c1 = (float)(1.4426950408889634 * (double)D.inv2s2[1]);
-    const float c2 = (float)(1.4426950408889634 * (double)D.inv2s2[2]);
 
     Sums s;
     int moved = 0, done = 0;
     bool stop = false;
     for (int t = 0;; ++t) {
         if (!L.final_eval && t == D.iters) break;
-        // gather (issued first, consumed after the pair sums), then pair sums, per owned k
-        float a[NPER], Dm[NPER][3], Ek[NPER][3];
-        double pa = 0.0, ps = 0.0;
+        float a[NPER], Dm[NPER][ND], Ek[NPER][ND];
+        float pa = 0.f, ps = 0.f;
         int pe = 0;
 #pragma unroll
         for (int q = 0; q < NPER; ++q) {
-            const int k = tid + q * blockDim.x;
-            if (k >= M) break;
-            const float4 wk = sw[k];
-            const float r0 = lattice_round(wk.x, D.H), r1 = lattice_round(wk.y, D.W);
-            const float r2 = nd == 3 ? lattice_round(wk.z, D.G) : 0.f;
-            const long long o = ((long long)(int)r2 * D.H + (int)r0) * D.fpitch + (int)r1;
-            const float ak = __ldg(A + o);
-            const float f0 = __ldg(A + plane + o), f1 = __ldg(A + 2 * plane + o);
-            const float f2 = nd == 3 ? __ldg(A + 3 * plane + o) : 0.f;
-            float s_ = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
-            for (int j = 0; j < M; ++j) {
-                const float4 wj = sw[j];
-                const float d0 = wj.x - wk.x, d1 = wj.y - wk.y, d2 = wj.z - wk.z;
-                const float g = exp2f(-(d0 * d0 * c0 + d1 * d1 * c1 + d2 * d2 * c2));
-                s_ += g;
-                e0 = fmaf(g, d0, e0);
-                e1 = fmaf(g, d1, e1);
-                e2 = fmaf(g, d2, e2);
+            const int k = tid + q * kRunThreads;
+            a[q] = 0.f;
+            if (k >= M) continue;
+            const P wk = sw[k];
+            // gather first (its latency overlaps the pair sums)
+            float r[3], wv[3];
+            wv[0] = wk.x; wv[1] = wk.y;
+            r[0] = lattice_round(wk.x, D.H);
+            r[1] = lattice_round(wk.y, D.W);
+            if constexpr (ND == 3) { wv[2] = wk.z; r[2] = lattice_round(wk.z, D.G); }
+            const long long o = ((long long)(ND == 3 ? (int)r[2] : 0) * D.H + (int)r[0]) * D.fpitch + (int)r[1];
+            const float ak = __ldg(D.A + o);
+            float f[ND];
+#pragma unroll
+            for (int i = 0; i < ND; ++i) f[i] = __ldg(D.A + (i + 1) * D.plane + o);
+            // pair sums over every j, two interleaved accumulators
+            float s0 = 0.f, s1 = 0.f, e0[ND], e1[ND];
+#pragma unroll
+            for (int i = 0; i < ND; ++i) { e0[i] = 0.f; e1[i] = 0.f; }
+            int j = 0;
+            for (; j + 1 < M; j += 2) {
+                const P wa = sw[j], wb = sw[j + 1];
+                const float da0 = wa.x - wk.x, da1 = wa.y - wk.y;
+                const float db0 = wb.x - wk.x, db1 = wb.y - wk.y;
+                float xa = da0 * da0 * c0 + da1 * da1 * c1, xb = db0 * db0 * c0 + db1 * db1 * c1;
+                float da2 = 0.f, db2 = 0.f;
+                if constexpr (ND == 3) {
+                    da2 = wa.z - wk.z; db2 = wb.z - wk.z;
+                    xa = fmaf(da2 * da2, c2, xa);
+                    xb = fmaf(db2 * db2, c2, xb);
+                }
+                const float ga = exp2f(-xa), gb = exp2f(-xb);
+                s0 += ga;
+                s1 += gb;
+                e0[0] = fmaf(ga, da0, e0[0]); e1[0] = fmaf(gb, db0, e1[0]);
+                e0[1] = fmaf(ga, da1, e0[1]); e1[1] = fmaf(gb, db1, e1[1]);
+                if constexpr (ND == 3) { e0[2] = fmaf(ga, da2, e0[2]); e1[2] = fmaf(gb, db2, e1[2]); }
+            }
+            if (j < M) {
+                const P wa = sw[j];
+                const float da0 = wa.x - wk.x, da1 = wa.y - wk.y;
+                float xa = da0 * da0 * c0 + da1 * da1 * c1;
+                float da2 = 0.f;
+                if constexpr (ND == 3) { da2 = wa.z - wk.z; xa = fmaf(da2 * da2, c2, xa); }
+                const float ga = exp2f(-xa);
+                s0 += ga;
+                e0[0] = fmaf(ga, da0, e0[0]);
+                e0[1] = fmaf(ga, da1, e0[1]);
+                if constexpr (ND == 3) e0[2] = fmaf(ga, da2, e0[2]);
             }
             a[q] = ak;
-            const float rr[3] = {r0, r1, r2}, ww[3] = {wk.x, wk.y, wk.z}, ff[3] = {f0, f1, f2};
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const double m = (double)ff[i] - (L.absolute ? (double)rr[i] * ak : 0.0) + ((double)rr[i] - (double)ww[i]) * ak;
-                Dm[q][i] = i < nd ? (float)m : 0.f;
+            for (int i = 0; i < ND; ++i) {
+                // centred moment about the real w_k: F(r) (- r a if absolute) + (r - w) a
+                const float fi = L.absolute ? f[i] - r[i] * ak : f[i];
+                Dm[q][i] = fmaf(r[i] - wv[i], ak, fi);
+                Ek[q][i] = e0[i] + e1[i];
             }
-            Ek[q][0] = e0;
-            Ek[q][1] = e1;
-            Ek[q][2] = e2;
-            pa += (double)ak;
-            ps += (double)s_;
+            pa += ak;
+            ps += s0 + s1;
             pe += !(ak > 0.f);
         }
         block_sums(pa, ps, pe, red, &s);
         if (!L.final_eval && t == 0 && L.stats && tid == 0) write_stats(L.stats + blockIdx.x, s, sxx, 0, 0);
         if (t == D.iters || stop) break;
-        // update (Jacobi: every k above read the old W; the barrier in block_sums separates them)
-        const double c = s.sxw / s.sww;
+        // update (Jacobi: every k above read the old W; the barriers in block_sums separate them)
+        const float c = s.sxw / s.sww;
         int mv = 0;
 #pragma unroll
         for (int q = 0; q < NPER; ++q) {
-            const int k = tid + q * blockDim.x;
-            if (k >= M) break;
-            if (!(a[q] > 0.f)) continue;
-            float4 w = sw[k];
-            float nw[3] = {w.x, w.y, w.z};
+            const int k = tid + q * kRunThreads;
+            if (k >= M || !(a[q] > 0.f)) continue;
+            P w = sw[k];
+            float nw[3];
+            nw[0] = w.x; nw[1] = w.y;
+            if constexpr (ND == 3) nw[2] = w.z;
             bool kmoved = false;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                if (i >= nd) break;
+            for (int i = 0; i < ND; ++i) {
                 const int ni = i == 0 ? D.H : (i == 1 ? D.W : D.G);
-                const double raw = (double)nw[i] + (double)D.step_scale * ((double)Dm[q][i] - c * (double)Ek[q][i]) / (double)a[q];
-                const double nwv = snap ? lattice_round_d(raw, ni) : fmin(fmax(raw, 0.0), (double)(ni - 1));
-                const float nf = (float)nwv;
-                kmoved |= (nf != nw[i]);
-                nw[i] = nf;
+                const float delta = D.step * (Dm[q][i] - c * Ek[q][i]) / a[q];
+                float nv;
+                if (snap) {
+                    // w is integral: round(w + delta) = w + round(delta), exact in FP32
+                    nv = fminf(fmaxf(nw[i] + floorf(delta + 0.5f), 0.f), (float)(ni - 1));
+                } else {
+                    nv = fminf(fmaxf(nw[i] + delta, 0.f), (float)(ni - 1));
+                }
+                kmoved |= (nv != nw[i]);
+                nw[i] = nv;
             }
-            sw[k] = make_float4(nw[0], nw[1], nw[2], 0.f);
+            w.x = nw[0]; w.y = nw[1];
+            if constexpr (ND == 3) w.z = nw[2];
+            sw[k] = w;
             mv += kmoved;
         }
         moved = __syncthreads_count(mv);
@@ -192,32 +252,39 @@ __global__ void __launch_bounds__(kRunThreads, 4) run_kernel(const __grid_consta
         L.stats[blockIdx.x].moved = moved;
         L.stats[blockIdx.x].iters_done = done;
     }
-    float* Wout = L.W_out + D.w_off;
+    float* Wout = L.W_out + w_off;
     for (int k = tid; k < M; k += blockDim.x) {
-        const float4 w = sw[k];
-        const float ww[3] = {w.x, w.y, w.z};
+        const P w = sw[k];
+        float ww[3];
+        ww[0] = w.x; ww[1] = w.y;
+        if constexpr (ND == 3) ww[2] = w.z;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            if (i >= nd) break;
+        for (int i = 0; i < ND; ++i) {
             const int ni = i == 0 ? D.H : (i == 1 ? D.W : D.G);
-            Wout[k * nd + i] = ww[i];
-            if (L.W_lattice) L.W_lattice[D.w_off + k * nd + i] = (int)lattice_round(ww[i], ni);
+            Wout[k * ND + i] = ww[i];
+            if (L.W_lattice) L.W_lattice[w_off + k * ND + i] = (int)lattice_round(ww[i], ni);
         }
     }
 }
 
-}  // namespace
-
-cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s) {
-    (void)max_dim;
-    if (nimg <= 0) return cudaSuccess;
-    const size_t smem = (size_t)max_M * sizeof(float4);
+template <int ND>
+cudaError_t launch_nd(const RunLaunch& L, int nimg, int max_M, cudaStream_t s) {
+    const size_t smem = (size_t)max_M * (ND == 2 ? sizeof(float2) : sizeof(float4));
     const int nper = (max_M + kRunThreads - 1) / kRunThreads;
-    auto k = nper <= 1 ? run_kernel<1> : nper <= 2 ? run_kernel<2> : nper <= 4 ? run_kernel<4> : run_kernel<16>;
+    auto k = nper <= 1 ? run_kernel<1, ND> : nper <= 2 ? run_kernel<2, ND> : nper <= 4 ? run_kernel<4, ND>
+                                                                                         : run_kernel<16, ND>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<nimg, kRunThreads, smem, s>>>(L);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s, int ndim) {
+    (void)max_dim;
+    if (nimg <= 0) return cudaSuccess;
+    return ndim == 3 ? launch_nd<3>(L, nimg, max_M, s) : launch_nd<2>(L, nimg, max_M, s);
 }
 
 }  // namespace itc

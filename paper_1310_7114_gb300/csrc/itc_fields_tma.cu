@@ -3,9 +3,9 @@
 // Same arithmetic as fields_kernel in itc_fields.cu (the results are bit for bit the same: every
 // output accumulates the same products in the same order), reorganised for throughput:
 //   * persistent CTAs walk the tile list with a fixed stride;
-//   * the input tile plus its halo arrives by one cp.async.bulk.tensor (TMA) per tile into a
-//     staging buffer; the next tile's copy is issued as soon as the current one has been
-//     converted, so it overlaps the two passes;
+//   * the input tile plus its halo arrives by one cp.async.bulk.tensor (TMA) per tile into one
+//     of two staging buffers (one for 4-byte inputs), so copies run ahead of the tile being
+//     computed;
 //   * both passes use packed FP32 FMAs (fma.rn.f32x2) over pairs of neighbouring columns.
 // Used for 2-D images whose rows start on 16-byte boundaries (the tensor map needs it) and for
 // the compiled radii 6, 9 and 12; everything else goes through fields_kernel.
@@ -50,31 +50,39 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-__device__ __forceinline__ int find_image(const int* __restrict__ prefix, int n, int b) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(prefix + mid) <= b) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
     *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
 }
 
-// The image and tile-local index of tile t of this launch.
-__device__ __forceinline__ const ImageDesc* locate(const FieldsLaunch& L, int t, int& local, int& img) {
-    if (L.descs) {
-        const int p = find_image(L.tile_prefix, L.nimg + 1, t);
-        img = __ldg(L.img_list + p);
-        local = t - __ldg(L.tile_prefix + p);
-        return L.descs + img;
+// The image and tile-local index of tile t of this launch, found by the whole calling warp:
+// a 32-ary search over the class tile prefix (largest p with prefix[p] <= t), three dependent
+// loads for 4096 images instead of twelve for a binary search.
+__device__ __forceinline__ void locate_warp(const FieldsLaunch& L, int t, int& img, int& local) {
+    if (!L.descs) {
+        img = 0;
+        local = t;
+        return;
     }
-    img = 0;
-    local = t;
-    return &L.one;
+    const int lane = threadIdx.x & 31;
+    const int* prefix = L.tile_prefix;
+    int lo = 0, hi = L.nimg - 1;   // prefix[lo] <= t always holds (prefix[0] = 0)
+    while (hi - lo >= 32) {
+        const int step = (hi - lo + 32) / 32;
+        const int idx = lo + lane * step;
+        const bool ok = idx <= hi && __ldg(prefix + idx) <= t;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        const int best = 31 - __clz(m);   // lane 0 always qualifies
+        const int nlo = lo + best * step;
+        hi = min(hi, nlo + step - 1);
+        lo = nlo;
+    }
+    const int idx = lo + lane;
+    const bool ok = idx <= hi && __ldg(prefix + idx) <= t;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    const int p = lo + 31 - __clz(m);
+    img = __ldg(L.img_list + p);
+    local = t - __ldg(prefix + p);
 }
 
 // Bounded wait for the staged tile (about a second at most); false means the copy never landed.
@@ -94,42 +102,55 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
     constexpr int BW = TW + 2 * RA;                              // box width in elements
     constexpr int BOX_BYTES = BW * ROWS * ES;
     constexpr int STAGE_BYTES = (BOX_BYTES + 127) & ~127;
+    constexpr int NST = STAGE_BYTES <= 16384 ? 2 : 1;           // staging buffers (copies in flight)
     constexpr int NWIN = ((8 + 2 * R) + 3) & ~3;                 // window of 8 row-pass outputs
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the TMA destination must be 128-byte aligned: round the base up (128 spare bytes reserved)
-    unsigned char* stage = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    float* s_in = reinterpret_cast<float*>(stage + STAGE_BYTES);      // ROWS x SW
+    unsigned char* stage0 = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // NST stages
+    float* s_in = reinterpret_cast<float*>(stage0 + NST * STAGE_BYTES);  // ROWS x SW
     float* sT = s_in + ROWS * SW;                                     // T then T_v: ROWS x TW each
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ double red[32];
     __shared__ int s_abort;
     // Zero tracking: rowmask[r] bit q = staged row r has a nonzero in its 4-column group q;
     // colbits[b] = bits over staged rows whose T (8-column block b) is not known to be zero.
     __shared__ uint32_t rowmask[ROWS];
     __shared__ uint32_t colbits[TW / 8][4];
+    __shared__ int s_img[2], s_local[2];   // image and local tile of the copy in each stage
     const Taps& tp = L.taps;
     const int tid = threadIdx.x;
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         mbar_init_fence();
         s_abort = 0;
     }
     __syncthreads();
 
-    auto issue = [&](int t) {
+    // tile copies run NST tiles ahead: the n-th tile of this CTA lands in stage n % NST
+    // called by all of warp 0: resolve the tile, remember it for its stage, lane 0 starts the copy
+    auto issue = [&](int t, int buf) {
         int local, img;
-        const ImageDesc* dp = locate(L, t, local, img);
-        const int tv = local % dp->tiles_v, tu = local / dp->tiles_v;
-        const CUtensorMap* map = L.descs ? L.tmaps + img : &L.tmap_one;
-        mbar_expect_tx(&bar, BOX_BYTES);
-        tma_load_2d(stage, map, tv * TW - RA, tu * TH - R, &bar);
+        locate_warp(L, t, img, local);
+        if (tid == 0) {
+            const ImageDesc* dp = L.descs ? L.descs + img : &L.one;
+            const int tv = local % dp->tiles_v, tu = local / dp->tiles_v;
+            const CUtensorMap* map = L.descs ? L.tmaps + img : &L.tmap_one;
+            s_img[buf] = img;
+            s_local[buf] = local;
+            mbar_expect_tx(&bar[buf], BOX_BYTES);
+            tma_load_2d(stage0 + buf * STAGE_BYTES, map, tv * TW - RA, tu * TH - R, &bar[buf]);
+        }
     };
 
     int t = blockIdx.x;
-    if (tid == 0 && t < ntiles) issue(t);
-    uint32_t parity = 0;
+    if (tid < 32)
+        for (int b = 0; b < NST; ++b)
+            if (t + b * (int)gridDim.x < ntiles) issue(t + b * gridDim.x, b);
+    uint32_t phase = 0;   // bit b: parity of the next completion of bar[b]
+    int n = 0;            // tiles of this CTA so far
     const int kb = tid >> 4, cg = tid & 15;
     const int k0 = kb * K, c0 = cg * 4;
     // S_XX share of the previous tile: its warps leave their sums in red[]; thread 0 adds them
@@ -147,21 +168,23 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
     };
 
     for (; t < ntiles; t += gridDim.x) {
-        int local, img;
-        const ImageDesc* dp = locate(L, t, local, img);
+        const int buf = NST == 2 ? (n & 1) : 0;
+        const unsigned char* stage = stage0 + buf * STAGE_BYTES;
+        if (tid == 0 && !wait_stage(&bar[buf], (phase >> buf) & 1u)) s_abort = 1;
+        __syncthreads();   // the staged tile has landed; the previous tile's passes are done
+        if (tid == 0) flush();
+        const int img = s_img[buf], local = s_local[buf];
+        const ImageDesc* dp = L.descs ? L.descs + img : &L.one;
         const int H = dp->H, W = dp->W, fpitch = dp->fpitch;
         const int u0 = (local / dp->tiles_v) * TH, v0 = (local % dp->tiles_v) * TW;
         float* const fbase = L.fields + dp->field_off;
         const long long plane = dp->plane_floats;
-
-        if (tid == 0 && !wait_stage(&bar, parity)) s_abort = 1;
-        __syncthreads();   // the staged tile has landed; the previous tile's passes are done
-        if (tid == 0) flush();
         if (s_abort) {
             if (tid == 0) L.partials[dp->partial_off + local] = __longlong_as_double(0x7ff8000000000000LL);
             return;   // S_XX of the image becomes NaN: the host sees a non-finite status
         }
-        parity ^= 1u;
+        phase ^= 1u << buf;
+        ++n;
 
         // staged box -> float input tile, columns shifted so that s_in column 0 is v0 - R; one
         // warp per staged row, one 4-column group per lane, a ballot gives the row's zero mask
@@ -197,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
             if (tid < 32) colbits[tid >> 2][tid & 3] = 0u;
         }
         const int any = __syncthreads_or(nonzero);   // the stage is free from here on
-        if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        if (tid < 32 && t + NST * (int)gridDim.x < ntiles) issue(t + NST * gridDim.x, buf);
 
         const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
         if (!any) {
@@ -363,7 +386,8 @@ cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
     constexpr int RA = DTYPE == ITC_U8 ? 16 : ((R + 3) & ~3);
     constexpr int BOX_BYTES = (TW + 2 * RA) * ROWS * ES;
     constexpr int STAGE_BYTES = (BOX_BYTES + 127) & ~127;
-    const size_t smem = 128 + STAGE_BYTES + (size_t)ROWS * SW * 4 + 2 * (size_t)ROWS * TW * 4;
+    constexpr int NST = STAGE_BYTES <= 16384 ? 2 : 1;
+    const size_t smem = 128 + NST * (size_t)STAGE_BYTES + (size_t)ROWS * SW * 4 + 2 * (size_t)ROWS * TW * 4;
     auto k = fields_tma_kernel<R, ABS, DTYPE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

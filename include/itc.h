@@ -241,6 +241,29 @@ int itc_run_iterate(const void* plan_host, const void* plan_dev, float* W, itc_s
                     void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * The two phases for the images [b0, b1) of a plan only (0 <= b0 <= b1 <= B).  The fields of
+ * an image must be done before its iterations start; different image ranges are independent.
+ * Errors: ITC_ERR_INVALID_ARG (bad plan or range), ITC_ERR_WORKSPACE, ITC_ERR_CUDA.
+ */
+int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, int b1, void* ws,
+                         size_t ws_bytes, void* stream);
+int itc_run_iterate_range(const void* plan_host, const void* plan_dev, int b0, int b1, float* W,
+                          itc_stats* stats, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * itc_run_pipelined -- itc_run with the batch cut into `chunks` image ranges: the fields of
+ * range k+1 run on `stream` while the iterations of range k run on `stream2`, so the
+ * latency-bound iterations overlap the bandwidth- and FMA-bound fields.  Same results as
+ * itc_run.  `stream2` starts after the work already queued on `stream`, and `stream` waits
+ * for all of `stream2`'s work before anything queued after this call (events joined inside;
+ * the enqueued work is stream-capturable with both streams).  chunks in 1..64; chunks == 1 or
+ * stream2 == stream is plain itc_run.
+ * Errors: as itc_run.
+ */
+int itc_run_pipelined(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats,
+                      void* ws, size_t ws_bytes, void* stream, void* stream2, int chunks);
+
+/*
  * itc_backward -- gradient of Eq. (1) for every image of a plan, scaled by an upstream gradient:
  *   dD/dw_{k,i} = (2 / sigma_i^2) (E_{k,i} / S_WW - D_{k,i} / S_XW)
  *   dD/dh(x)    = 2 A(x) / S_XX - (2 / S_XW) sum_k g(x - w_k) [x in the box of round(w_k)]

@@ -161,10 +161,23 @@ bool encode_input_map(const itc_image* img, int R, CUtensorMap* out) {
     return r == CUDA_SUCCESS;
 }
 
-cudaError_t launch_fields_any(const FieldsLaunch& L, bool tma, int ntiles, int Ru, int Rv, int ndim, int dtype,
+// Tiles [begin, end) of one class (L.tile_base is set to begin here).
+cudaError_t launch_fields_any(FieldsLaunch& L, bool tma, int begin, int end, int Ru, int Rv, int ndim, int dtype,
                               cudaStream_t s) {
-    if (tma && fields_tma_supported(ndim, Ru, Rv)) return launch_fields_tma(L, ntiles, Ru, dtype, s);
-    return launch_fields(L, ntiles, Ru, Rv, ndim, dtype, s);
+    L.tile_base = begin;
+    if (end <= begin) return cudaSuccess;
+    if (tma && fields_tma_supported(ndim, Ru, Rv)) return launch_fields_tma(L, end, Ru, dtype, s);
+    return launch_fields(L, end - begin, Ru, Rv, ndim, dtype, s);
+}
+
+// First position in a class image list (ascending image indices) whose image is >= b.
+int lower_pos(const int* list, int n, int b) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (list[mid] < b) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 }
 
 const PlanHeader* plan_of(const void* plan_host) {
@@ -231,7 +244,7 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool tma = fields_tma_supported(img->ndim, L.taps.R[0], L.taps.R[1]) &&
                      encode_input_map(img, L.taps.R[0], &L.tmap_one);
-    rc = cuda_status(launch_fields_any(L, tma, (int)nt, L.taps.R[0], L.taps.R[1], img->ndim, img->dtype, s));
+    rc = cuda_status(launch_fields_any(L, tma, 0, (int)nt, L.taps.R[0], L.taps.R[1], img->ndim, img->dtype, s));
     if (rc) return rc;
     if (sxx) rc = cuda_status(launch_reduce_sxx(L.partials, (int)nt, sxx, s));
     return rc;
@@ -407,17 +420,23 @@ int itc_plan_offsets(const void* plan_host, int b, size_t* field_off, size_t* w_
     return ITC_OK;
 }
 
-int itc_run_fields(const void* plan_host, const void* plan_dev, void* ws, size_t ws_bytes, void* stream) {
+int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, int b1, void* ws, size_t ws_bytes,
+                         void* stream) {
     const PlanHeader* h = plan_of(plan_host);
     if (!h || !plan_dev || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (b0 < 0 || b1 > h->B || b0 > b1) return ITC_ERR_INVALID_ARG;
     if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
+    const int* hints = reinterpret_cast<const int*>(reinterpret_cast<const unsigned char*>(plan_host) + h->ints_off);
     const ImageDesc* descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
     const int* ints = reinterpret_cast<const int*>(pd + h->ints_off);
     unsigned char* w = reinterpret_cast<unsigned char*>(ws);
     for (int c = 0; c < h->ncls; ++c) {
         const ClassInfo& ci = h->cls[c];
+        const int p0 = lower_pos(hints + ci.list_off, ci.nimg, b0), p1 = lower_pos(hints + ci.list_off, ci.nimg, b1);
+        const int t0 = hints[ci.prefix_off + p0], t1 = hints[ci.prefix_off + p1];
+        if (t1 <= t0) continue;
         FieldsLaunch L;
         memset(&L, 0, sizeof(L));
         L.taps = ci.taps;
@@ -430,18 +449,20 @@ int itc_run_fields(const void* plan_host, const void* plan_dev, void* ws, size_t
         L.tile_h = ci.tile_h;
         L.absolute = 0;
         L.tmaps = reinterpret_cast<const CUtensorMap*>(pd + h->tmap_off);
-        int rc = cuda_status(
-            launch_fields_any(L, ci.tma != 0, ci.ntiles, ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
+        const int rc = cuda_status(
+            launch_fields_any(L, ci.tma != 0, t0, t1, ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
         if (rc) return rc;
     }
     return ITC_OK;
 }
 
-int itc_run_iterate(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
-                    size_t ws_bytes, void* stream) {
+int itc_run_iterate_range(const void* plan_host, const void* plan_dev, int b0, int b1, float* W, itc_stats* stats,
+                          void* ws, size_t ws_bytes, void* stream) {
     const PlanHeader* h = plan_of(plan_host);
     if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (b0 < 0 || b1 > h->B || b0 > b1) return ITC_ERR_INVALID_ARG;
     if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    if (b1 == b0) return ITC_OK;
     const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
     unsigned char* w = reinterpret_cast<unsigned char*>(ws);
     RunLaunch R;
@@ -454,12 +475,55 @@ int itc_run_iterate(const void* plan_host, const void* plan_dev, float* W, itc_s
     R.stats = stats;
     R.absolute = 0;
     R.final_eval = 1;
+    R.img_base = b0;
     for (int nd = 2; nd <= 3; ++nd) {
         if (!(h->ndim_mask & (1 << nd))) continue;
-        const int rc = cuda_status(launch_run(R, h->B, h->max_M, h->max_dim, reinterpret_cast<cudaStream_t>(stream), nd));
+        const int rc = cuda_status(launch_run(R, b1 - b0, h->max_M, h->max_dim, reinterpret_cast<cudaStream_t>(stream), nd));
         if (rc) return rc;
     }
     return ITC_OK;
+}
+
+int itc_run_fields(const void* plan_host, const void* plan_dev, void* ws, size_t ws_bytes, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h) return ITC_ERR_INVALID_ARG;
+    return itc_run_fields_range(plan_host, plan_dev, 0, h->B, ws, ws_bytes, stream);
+}
+
+int itc_run_iterate(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
+                    size_t ws_bytes, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h) return ITC_ERR_INVALID_ARG;
+    return itc_run_iterate_range(plan_host, plan_dev, 0, h->B, W, stats, ws, ws_bytes, stream);
+}
+
+int itc_run_pipelined(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
+                      size_t ws_bytes, void* stream, void* stream2, int chunks) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !W || chunks < 1 || chunks > 64) return ITC_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    if (chunks == 1 || !stream2 || stream2 == stream) return itc_run(plan_host, plan_dev, W, stats, ws, ws_bytes, stream);
+    cudaStream_t s1 = reinterpret_cast<cudaStream_t>(stream), s2 = reinterpret_cast<cudaStream_t>(stream2);
+    const int n = chunks < h->B ? chunks : h->B;
+    cudaEvent_t ev[65];
+    int made = 0, rc = ITC_OK;
+    for (; made <= n; ++made)
+        if (cudaEventCreateWithFlags(&ev[made], cudaEventDisableTiming) != cudaSuccess) { rc = ITC_ERR_CUDA; break; }
+    // the second stream starts after everything the caller queued on the first
+    if (!rc) rc = cuda_status(cudaEventRecord(ev[n], s1));
+    if (!rc) rc = cuda_status(cudaStreamWaitEvent(s2, ev[n], 0));
+    for (int k = 0; k < n && !rc; ++k) {
+        const int b0 = (int)((long long)h->B * k / n), b1 = (int)((long long)h->B * (k + 1) / n);
+        rc = itc_run_fields_range(plan_host, plan_dev, b0, b1, ws, ws_bytes, s1);
+        if (!rc) rc = cuda_status(cudaEventRecord(ev[k], s1));
+        if (!rc) rc = cuda_status(cudaStreamWaitEvent(s2, ev[k], 0));
+        if (!rc) rc = itc_run_iterate_range(plan_host, plan_dev, b0, b1, W, stats, ws, ws_bytes, s2);
+    }
+    // join: the first stream continues after the last iterations
+    if (!rc) rc = cuda_status(cudaEventRecord(ev[n], s2));
+    if (!rc) rc = cuda_status(cudaStreamWaitEvent(s1, ev[n], 0));
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);   // released once the work has run
+    return rc;
 }
 
 int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,

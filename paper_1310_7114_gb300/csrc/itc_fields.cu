@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
     const int SW = ((TW + 2 * Rv + 3) & ~3) + 4;   // staged row length (floats)
 
     // ---- which image / tile
-    int b = blockIdx.x;
+    int b = blockIdx.x + L.tile_base;
     const ImageDesc* dp;
     if (L.descs) {
         const int p = find_image(L.tile_prefix, L.nimg + 1, b);

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
         }
     };
 
-    int t = blockIdx.x;
+    int t = L.tile_base + blockIdx.x;   // tiles [tile_base, ntiles) of the class
     if (tid < 32)
         for (int b = 0; b < NST; ++b)
             if (t + b * (int)gridDim.x < ntiles) issue(t + b * gridDim.x, b);
@@ -395,7 +395,8 @@ cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem)) != cudaSuccess) return e;
-    const int grid = ntiles < sms * (per_sm > 0 ? per_sm : 1) ? ntiles : sms * (per_sm > 0 ? per_sm : 1);
+    const int count = ntiles - L.tile_base;
+    const int grid = count < sms * (per_sm > 0 ? per_sm : 1) ? count : sms * (per_sm > 0 ? per_sm : 1);
     k<<<grid, kThreads, smem, s>>>(L, ntiles);
     return cudaGetLastError();
 }
@@ -421,7 +422,7 @@ int fields_tma_box(int dtype, int R, int* box_w, int* box_h) {
 }
 
 cudaError_t launch_fields_tma(const FieldsLaunch& L, int ntiles, int R, int dtype, cudaStream_t s) {
-    if (ntiles <= 0) return cudaSuccess;
+    if (ntiles - L.tile_base <= 0) return cudaSuccess;
     const bool abs_ = L.absolute != 0;
     if (dtype == ITC_U8) return abs_ ? dispatch<true, ITC_U8>(L, ntiles, R, s) : dispatch<false, ITC_U8>(L, ntiles, R, s);
     return abs_ ? dispatch<true, ITC_F32>(L, ntiles, R, s) : dispatch<false, ITC_F32>(L, ntiles, R, s);

@@ -112,6 +112,7 @@ struct FieldsLaunch {
     double* partials;           // S_XX partial base
     int tile_h;
     int absolute;
+    int tile_base;              // first tile of this launch within the class (image sub-ranges)
 };
 
 struct RunLaunch {
@@ -126,6 +127,7 @@ struct RunLaunch {
     itc_stats* stats;
     int absolute;
     int final_eval;             // 1: stats at the final W (itc_run); 0: stats at W_in (itc_step)
+    int img_base;               // image of blockIdx.x == 0 (image sub-ranges)
 };
 
 struct BackwardLaunch {

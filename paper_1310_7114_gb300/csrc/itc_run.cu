@@ -94,9 +94,10 @@ struct Img {
 // NPER: codebooks owned per thread (compile-time so the per-codebook state stays in registers).
 // ND: lattice dimension (2 or 3).
 template <int NPER, int ND>
-__global__ void __launch_bounds__(kRunThreads, 6) run_kernel(const __grid_constant__ RunLaunch L) {
+__global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_constant__ RunLaunch L) {
     using P = typename std::conditional<ND == 2, float2, float4>::type;
-    const ImageDesc& Dg = L.descs ? L.descs[blockIdx.x] : L.one;
+    const int img = L.img_base + blockIdx.x;
+    const ImageDesc& Dg = L.descs ? L.descs[img] : L.one;
     if (Dg.ndim != ND) return;   // a mixed plan launches once per dimension
     Img D;
     D.A = L.fields + Dg.field_off;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kRunThreads, 6) run_kernel(const __grid_consta
             pe += !(ak > 0.f);
         }
         block_sums(pa, ps, pe, red, &s);
-        if (!L.final_eval && t == 0 && L.stats && tid == 0) write_stats(L.stats + blockIdx.x, s, sxx, 0, 0);
+        if (!L.final_eval && t == 0 && L.stats && tid == 0) write_stats(L.stats + img, s, sxx, 0, 0);
         if (t == D.iters || stop) break;
         // update (Jacobi: every k above read the old W; the barriers in block_sums separate them)
         const float c = s.sxw / s.sww;
@@ -247,10 +248,10 @@ __global__ void __launch_bounds__(kRunThreads, 6) run_kernel(const __grid_consta
         ++done;
         if (stop_fixed && moved == 0) stop = true;
     }
-    if (L.final_eval && L.stats && tid == 0) write_stats(L.stats + blockIdx.x, s, sxx, moved, done);
+    if (L.final_eval && L.stats && tid == 0) write_stats(L.stats + img, s, sxx, moved, done);
     if (!L.final_eval && L.stats && tid == 0) {
-        L.stats[blockIdx.x].moved = moved;
-        L.stats[blockIdx.x].iters_done = done;
+        L.stats[img].moved = moved;
+        L.stats[img].iters_done = done;
     }
     float* Wout = L.W_out + w_off;
     for (int k = tid; k < M; k += blockDim.x) {

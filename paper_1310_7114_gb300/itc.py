@@ -34,7 +34,8 @@ ITC_STOP_ON_FIXED = 4
 EXPORTS = (
     "itc_field_pitch", "itc_fields_bytes", "itc_fields_workspace_bytes", "itc_status_string",
     "itc_fields", "itc_step", "itc_plan_bytes", "itc_plan", "itc_plan_pixels", "itc_plan_offsets",
-    "itc_run", "itc_run_fields", "itc_run_iterate", "itc_backward", "itc_fields_noalloc",
+    "itc_run", "itc_run_fields", "itc_run_iterate", "itc_run_fields_range", "itc_run_iterate_range",
+    "itc_run_pipelined", "itc_backward", "itc_fields_noalloc",
 )
 
 
@@ -114,6 +115,12 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
         L.itc_run_fields.argtypes = [_P, _P, _P, _SZ, _P]
         L.itc_run_iterate.restype = ctypes.c_int
         L.itc_run_iterate.argtypes = [_P, _P, _P, _P, _P, _SZ, _P]
+        L.itc_run_fields_range.restype = ctypes.c_int
+        L.itc_run_fields_range.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _SZ, _P]
+        L.itc_run_iterate_range.restype = ctypes.c_int
+        L.itc_run_iterate_range.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _SZ, _P]
+        L.itc_run_pipelined.restype = ctypes.c_int
+        L.itc_run_pipelined.argtypes = [_P, _P, _P, _P, _P, _SZ, _P, _P, ctypes.c_int]
         L.itc_backward.restype = ctypes.c_int
         L.itc_backward.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]
         _lib = L
@@ -325,6 +332,15 @@ def run_iterate(plan: Plan, W, stats=None, stream=None):
     """itc_run_iterate: the iterations of itc_run on the fields already in the workspace."""
     _check(lib().itc_run_iterate(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), _ptr(stats), plan.ws.data_ptr(),
                                  plan.ws.numel(), _stream(stream)), "itc_run_iterate")
+    return W
+
+
+def run_pipelined(plan: Plan, W, stats=None, stream2=None, chunks: int = 4, stream=None):
+    """itc_run_pipelined: fields of image range k+1 overlap the iterations of range k on stream2."""
+    torch = _torch()
+    s2 = stream2 if stream2 is not None else torch.cuda.Stream(device=W.device)
+    _check(lib().itc_run_pipelined(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), _ptr(stats), plan.ws.data_ptr(),
+                                   plan.ws.numel(), _stream(stream), s2.cuda_stream, int(chunks)), "itc_run_pipelined")
     return W
 
 

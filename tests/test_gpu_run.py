@@ -198,3 +198,38 @@ def test_run_is_deterministic():
     _, W2, s2 = run_plan(images, Ms, W0s, params)
     assert all(np.array_equal(a, b) for a, b in zip(W1, W2))
     assert s1.tobytes() == s2.tobytes()
+
+
+def test_pipelined_and_range_runs_equal_plain_run():
+    """itc_run_pipelined (fields of chunk k+1 overlapping iterations of chunk k on a second
+    stream) and explicit range calls give the same codebooks and stats as itc_run."""
+    import ctypes
+    import torch
+    images, Ms, sig = synth.c3_batch(40)
+    W0s = [synth.init_codebook(synth.rng_for(3, 30_000 + i), im.astype(np.float32), int(m))
+           for i, (im, m) in enumerate(zip(images, Ms))]
+    params = [itc.make_params(float(s), 3.0, 15) for s in sig]
+    ts = [to_dev(im) for im in images]
+    plan = itc.Plan(ts, Ms, params)
+    outs = []
+    for mode in ("plain", "pipelined", "ranges"):
+        W = plan.pack_W(W0s)
+        st = itc.new_stats(len(images), W.device)
+        if mode == "plain":
+            itc.run(plan, W, st)
+        elif mode == "pipelined":
+            itc.run_pipelined(plan, W, st, chunks=5)
+        else:
+            L = itc.lib()
+            s = torch.cuda.current_stream().cuda_stream
+            for b0, b1 in ((0, 7), (7, 7), (7, 31), (31, 40)):
+                assert L.itc_run_fields_range(plan.host_ptr, plan.dev.data_ptr(), b0, b1, plan.ws.data_ptr(),
+                                              plan.ws.numel(), s) == 0
+                assert L.itc_run_iterate_range(plan.host_ptr, plan.dev.data_ptr(), b0, b1, W.data_ptr(),
+                                               st.data_ptr(), plan.ws.data_ptr(), plan.ws.numel(), s) == 0
+            assert L.itc_run_fields_range(plan.host_ptr, plan.dev.data_ptr(), 5, 41, plan.ws.data_ptr(),
+                                          plan.ws.numel(), s) == itc.ITC_ERR_INVALID_ARG
+        torch.cuda.synchronize()
+        outs.append((W.cpu().numpy().copy(), st.cpu().numpy().tobytes()))
+    for W, st in outs[1:]:
+        assert np.array_equal(W, outs[0][0]) and st == outs[0][1]

@@ -6,6 +6,7 @@
 
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -383,12 +384,18 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         pbase += t;
     }
     h->total_tiles = pbase;
-    // backward pixel-tile prefix over all images
+    // backward pixel pass: one CTA per image, images with the most tiles first
     const int bwd_off = io;
-    for (int b = 0; b < B; ++b) ints[io++] = descs[b].bwd_tile_begin;
-    ints[io++] = bwd;
+    {
+        std::vector<int> order(B);
+        for (int b = 0; b < B; ++b) order[b] = b;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+            return descs[a].bwd_tiles_u * descs[a].bwd_tiles_v > descs[c].bwd_tiles_u * descs[c].bwd_tiles_v;
+        });
+        for (int b = 0; b < B; ++b) ints[io++] = order[b];
+    }
     h->nints = io;
-    h->bwd_prefix_off = bwd_off;
+    h->bwd_order_off = bwd_off;
     h->bwd_tiles = bwd;
 
     // workspace: [fields][S_XX partials][per-image backward scalars]
@@ -553,7 +560,7 @@ int itc_backward(const void* plan_host, const void* plan_dev, const float* W, co
     L.grad_h = grad_h;
     L.stats = stats;
     L.scal = reinterpret_cast<double*>(w + h->ws_scal_off);
-    L.bwd_prefix = reinterpret_cast<const int*>(pd + h->ints_off) + h->bwd_prefix_off;
+    L.bwd_order = reinterpret_cast<const int*>(pd + h->ints_off) + h->bwd_order_off;
     L.B = h->B;
     return cuda_status(launch_backward(L, h->B, h->max_M, h->bwd_tiles,
                                        reinterpret_cast<cudaStream_t>(stream)));

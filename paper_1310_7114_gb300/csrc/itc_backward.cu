@@ -7,10 +7,10 @@
 // Kernel 1 (one CTA per image): window sums a_k, D_k around round(w_k) read directly from the
 // image (kernel evaluated at the real w_k, one warp per k), the M x M sums s_k, E_k (one warp
 // per k, xor-shuffle reduction), S_XW, S_WW, grad_W and two per-image scalars for kernel 2.
-// Kernel 2 (one CTA per 64 x 64 pixel tile): the codebooks whose box meets the tile are listed
-// in k order (ballot compaction), their Gaussians are stamped onto the tile in that order -- the
-// transposed form of the gather in the forward update -- and every pixel combines the stored
-// field A with the stamp.
+// Kernel 2 (one CTA per image, over its 64 x 64 pixel tiles): the codebooks whose box meets a
+// tile are listed in k order (ballot compaction), their Gaussians are stamped onto the tile in
+// that order -- the transposed form of the gather in the forward update -- and every pixel
+// combines the stored field A with the stamp.
 #include <math.h>
 
 #include "itc_internal.cuh"
@@ -193,183 +193,163 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
     }
 }
 
-// Largest p in [0, n - 1) with prefix[p] <= b (prefix has n entries, prefix[0] = 0), found by the
-// whole calling warp with a 32-ary search: three dependent loads for 4096 images.
-__device__ __forceinline__ int find_image_warp(const int* __restrict__ prefix, int n, int b) {
-    const int lane = threadIdx.x & 31;
-    int lo = 0, hi = n - 2;
-    while (hi - lo >= 32) {
-        const int step = (hi - lo + 32) / 32;
-        const int idx = lo + lane * step;
-        const unsigned m = __ballot_sync(0xffffffffu, idx <= hi && __ldg(prefix + idx) <= b);
-        const int nlo = lo + (31 - __clz(m)) * step;
-        hi = min(hi, nlo + step - 1);
-        lo = nlo;
-    }
-    const int idx = lo + lane;
-    const unsigned m = __ballot_sync(0xffffffffu, idx <= hi && __ldg(prefix + idx) <= b);
-    return lo + 31 - __clz(m);
-}
-
 constexpr int kChunk = 64;   // codebooks staged per round in the pixel kernel
 
-// Pixel pass over a 64 x 64 tile.  The stamp S(x) = sum_k g(x - w_k) [x in box(round(w_k))] is
-// separable in 2-D: g(x - w) = g_u(x_u - w_u) g_v(x_v - w_v) and the box is a product of two
-// intervals, so for the codebooks whose box meets the tile (listed in k order)
+// Pixel pass: one CTA per image walks the image's 64 x 64 tiles (images with the most tiles
+// are launched first).  The stamp S(x) = sum_k g(x - w_k) [x in box(round(w_k))] is separable
+// in 2-D: g(x - w) = g_u(x_u - w_u) g_v(x_v - w_v) and the box is a product of two intervals,
+// so for the codebooks whose box meets a tile (listed in k order)
 //   S(r, c) = sum_l a_l(r) b_l(c),  a_l(r) = g_u(u0 + r - w_lu) [|u0 + r - r_lu| <= R_u], ...
 // Chunks of 64 listed codebooks are staged as a (64 x 64) and b (64 x 64) in shared memory and
 // every thread accumulates a 4 x 4 block of pixels in l order (deterministic, no atomics).  In
 // 3-D the g factor depends on each pixel's gray level and is applied per pixel and codebook.
-__global__ void __launch_bounds__(kThreads, 4) bwd_pixels_kernel(const __grid_constant__ BackwardLaunch L) {
-    const int img = find_image_warp(L.bwd_prefix, L.B + 1, blockIdx.x);
+__global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_constant__ BackwardLaunch L) {
+    const int img = __ldg(L.bwd_order + blockIdx.x);
     const ImageDesc& D = L.descs[img];
-    const int t = blockIdx.x - __ldg(L.bwd_prefix + img);
-    const int u0 = (t / D.bwd_tiles_v) * kBwdTileH, v0 = (t % D.bwd_tiles_v) * kBwdTileW;
     const int M = D.M, nd = D.ndim, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int H = D.H, Wd = D.W, G = D.G, fpitch = D.fpitch, tiles_v = D.bwd_tiles_v;
+    const int ntiles = D.bwd_tiles_u * D.bwd_tiles_v;
     const int Ru = D.R[0], Rv = D.R[1], Rg = D.R[2];
-    extern __shared__ __align__(16) int lk[];          // listed codebook indices (M)
+    const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
+    const float* A = L.fields + D.field_off;
+    float* gh = L.grad_h + D.gh_off;
+    const float s1 = (float)L.scal[img * 4 + 0], s2 = (float)L.scal[img * 4 + 1];
+
+    extern __shared__ __align__(16) unsigned char bsm[];
+    float* cw = reinterpret_cast<float*>(bsm);          // M x 3 codebook positions
+    int* cr = reinterpret_cast<int*>(cw + 3 * M);       // M x 3 rounded lattice sites
+    int* lk = cr + 3 * M;                               // listed codebooks of the current tile
     __shared__ __align__(16) float sa[kChunk][kBwdTileH];
     __shared__ __align__(16) float sb[kChunk][kBwdTileW];
-    __shared__ float sgw[kChunk];                       // 3-D: w_g of the chunk's codebooks
-    __shared__ int sgr[kChunk];                         // 3-D: round(w_g)
-    __shared__ float scw[kChunk][2];                    // w_u, w_v of the chunk's codebooks
-    __shared__ int scr[kChunk][2];                      // their rounded lattice sites
     __shared__ int wcount[kThreads / 32];
-    __shared__ int s_total;
+
     const float* Wk = L.W + D.w_off;
-
-    // stable compaction of the codebooks whose box meets this tile
-    int total = 0;
-    for (int base = 0; base < M; base += blockDim.x) {
-        const int k = base + tid;
-        bool hit = false;
-        if (k < M) {
-            const int r0 = lattice_round_i(Wk[k * nd], D.H), r1 = lattice_round_i(Wk[k * nd + 1], D.W);
-            hit = (r0 + Ru >= u0) && (r0 - Ru <= u0 + kBwdTileH - 1) &&
-                  (r1 + Rv >= v0) && (r1 - Rv <= v0 + kBwdTileW - 1);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) wcount[wid] = __popc(bal);
-        __syncthreads();
-        int off = total;
-        for (int q = 0; q < wid; ++q) off += wcount[q];
-        if (hit) lk[off + __popc(bal & ((1u << lane) - 1u))] = k;
-        int add = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) add += wcount[q];
-        total += add;
-        __syncthreads();
+    for (int k = tid; k < M; k += blockDim.x) {
+        const float w0 = Wk[k * nd], w1 = Wk[k * nd + 1], w2 = nd == 3 ? Wk[k * nd + 2] : 0.f;
+        cw[k * 3] = w0;
+        cw[k * 3 + 1] = w1;
+        cw[k * 3 + 2] = w2;
+        cr[k * 3] = lattice_round_i(w0, H);
+        cr[k * 3 + 1] = lattice_round_i(w1, Wd);
+        cr[k * 3 + 2] = nd == 3 ? lattice_round_i(w2, G) : 0;
     }
-    if (tid == 0) s_total = total;
     __syncthreads();
-    const int nl = s_total;
-    const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
 
-    // this thread's 4 x 4 block; in 2-D its field values are loaded now so that their latency
-    // overlaps the stamping below
-    const int pr = (tid >> 4) * 4, pc = (tid & 15) * 4;
-    float4 a4[4];
-    if (nd == 2 && v0 + pc < D.W) {
-        const float* A2 = L.fields + D.field_off;
+    const int pr = (tid >> 4) * 4, pc = (tid & 15) * 4;   // this thread's 4 x 4 block
+    for (int t = 0; t < ntiles; ++t) {
+        const int u0 = (t / tiles_v) * kBwdTileH, v0 = (t % tiles_v) * kBwdTileW;
+        // field values of this thread's block, loaded first so their latency overlaps the stamp
+        float4 a4[4];
+        int gray[4][4];
+        const bool cols_in = v0 + pc < Wd;
+        if (nd == 2) {
+            if (cols_in) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int u = min(u0 + pr + i, D.H - 1);
-            a4[i] = __ldg(reinterpret_cast<const float4*>(A2 + (long long)u * D.fpitch + v0 + pc));
+                for (int i = 0; i < 4; ++i) {
+                    const int u = min(u0 + pr + i, H - 1);
+                    a4[i] = __ldg(reinterpret_cast<const float4*>(A + (long long)u * fpitch + v0 + pc));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int u = u0 + pr + i, v = v0 + pc + j;
+                    gray[i][j] = (u < H && v < Wd) ? pixel_gray(D, u, v) : 0;
+                }
         }
-    }
-    int gray[4][4];
-    if (nd == 3) {
+
+        // stable compaction of the codebooks whose box meets this tile
+        int nl = 0;
+        for (int base = 0; base < M; base += blockDim.x) {
+            const int k = base + tid;
+            bool hit = false;
+            if (k < M) {
+                const int r0 = cr[k * 3], r1 = cr[k * 3 + 1];
+                hit = (r0 + Ru >= u0) && (r0 - Ru <= u0 + kBwdTileH - 1) &&
+                      (r1 + Rv >= v0) && (r1 - Rv <= v0 + kBwdTileW - 1);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) wcount[wid] = __popc(bal);
+            __syncthreads();
+            int off = nl;
+            for (int q = 0; q < wid; ++q) off += wcount[q];
+            if (hit) lk[off + __popc(bal & ((1u << lane) - 1u))] = k;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) nl += wcount[q];
+            __syncthreads();
+        }
+
+        float acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int u = u0 + pr + i, v = v0 + pc + j;
-                gray[i][j] = (u < D.H && v < D.W) ? pixel_gray(D, u, v) : 0;
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        for (int base = 0; base < nl; base += kChunk) {
+            const int nc = min(kChunk, nl - base);
+            for (int i = tid; i < nc * kBwdTileH; i += blockDim.x) {
+                const int l = i / kBwdTileH, r = i % kBwdTileH;
+                const int k = lk[base + l];
+                const int u = u0 + r, v = v0 + r;
+                float av = 0.f, bv = 0.f;
+                if (u < H && abs(u - cr[k * 3]) <= Ru) { const float d = (float)u - cw[k * 3]; av = expf(-d * d * c0); }
+                if (v < Wd && abs(v - cr[k * 3 + 1]) <= Rv) { const float d = (float)v - cw[k * 3 + 1]; bv = expf(-d * d * c1); }
+                sa[l][r] = av;
+                sb[l][r] = bv;
             }
-    }
-    float acc[4][4];
+            __syncthreads();
+            for (int l = 0; l < nc; ++l) {
+                const float4 av4 = *reinterpret_cast<const float4*>(&sa[l][pr]);
+                const float4 bv4 = *reinterpret_cast<const float4*>(&sb[l][pc]);
+                const float av[4] = {av4.x, av4.y, av4.z, av4.w}, bv[4] = {bv4.x, bv4.y, bv4.z, bv4.w};
+                if (nd == 2) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-
-    for (int base = 0; base < nl; base += kChunk) {
-        const int nc = min(kChunk, nl - base);
-        // the chunk's codebook positions, then its separable factors
-        if (tid < nc) {
-            const int k = lk[base + tid];
-            const float w0 = Wk[k * nd], w1 = Wk[k * nd + 1];
-            scw[tid][0] = w0;
-            scw[tid][1] = w1;
-            scr[tid][0] = lattice_round_i(w0, D.H);
-            scr[tid][1] = lattice_round_i(w1, D.W);
-            if (nd == 3) {
-                sgw[tid] = Wk[k * nd + 2];
-                sgr[tid] = lattice_round_i(Wk[k * nd + 2], D.G);
-            }
-        }
-        __syncthreads();
-        for (int i = tid; i < nc * kBwdTileH; i += blockDim.x) {
-            const int l = i / kBwdTileH, r = i % kBwdTileH;
-            const int u = u0 + r, v = v0 + r;
-            float av = 0.f, bv = 0.f;
-            if (u < D.H && abs(u - scr[l][0]) <= Ru) { const float d = (float)u - scw[l][0]; av = expf(-d * d * c0); }
-            if (v < D.W && abs(v - scr[l][1]) <= Rv) { const float d = (float)v - scw[l][1]; bv = expf(-d * d * c1); }
-            sa[l][r] = av;
-            sb[l][r] = bv;
-        }
-        __syncthreads();
-        for (int l = 0; l < nc; ++l) {
-            const float4 a4 = *reinterpret_cast<const float4*>(&sa[l][pr]);
-            const float4 b4 = *reinterpret_cast<const float4*>(&sb[l][pc]);
-            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
-            if (nd == 2) {
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                } else {
+                    const int k = lk[base + l];
+                    const float wg = cw[k * 3 + 2];
+                    const int rg = cr[k * 3 + 2];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-            } else {
-                const float wg = sgw[l];
-                const int rg = sgr[l];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int gl = gray[i][j];
-                        if (abs(gl - rg) <= Rg) {
-                            const float d = (float)gl - wg;
-                            acc[i][j] = fmaf(av[i] * bv[j], expf(-d * d * c2), acc[i][j]);
+                        for (int j = 0; j < 4; ++j) {
+                            const int gl = gray[i][j];
+                            if (abs(gl - rg) <= Rg) {
+                                const float d = (float)gl - wg;
+                                acc[i][j] = fmaf(av[i] * bv[j], expf(-d * d * c2), acc[i][j]);
+                            }
                         }
-                    }
-            }
-        }
-        __syncthreads();
-    }
-
-    const float s1 = (float)L.scal[img * 4 + 0], s2 = (float)L.scal[img * 4 + 1];
-    const float* A = L.fields + D.field_off;
-    if (v0 + pc >= D.W) return;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int u = u0 + pr + i;
-        if (u >= D.H) break;
-        float* out = L.grad_h + D.gh_off + (long long)u * D.W + v0 + pc;
-        if (nd == 2) {
-            // 4 field values from one 16-byte load (rows are padded to a multiple of 4 floats)
-            const float av[4] = {a4[i].x, a4[i].y, a4[i].z, a4[i].w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (v0 + pc + j < D.W) out[j] = s1 * av[j] - s2 * acc[i][j];
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int v = v0 + pc + j;
-                if (v >= D.W) break;
-                if (gray[i][j] >= D.G) {   // a voxel outside the lattice: no field value
-                    out[j] = 0.f;
-                    continue;
                 }
-                const long long o = ((long long)gray[i][j] * D.H + u) * D.fpitch + v;
-                out[j] = s1 * __ldg(A + o) - s2 * acc[i][j];
+            }
+            __syncthreads();   // sa / sb are rewritten by the next chunk or tile
+        }
+
+        if (!cols_in) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int u = u0 + pr + i;
+            if (u >= H) break;
+            float* out = gh + (long long)u * Wd + v0 + pc;
+            if (nd == 2) {
+                // 4 field values from one 16-byte load (rows are padded to a multiple of 4 floats)
+                const float av[4] = {a4[i].x, a4[i].y, a4[i].z, a4[i].w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (v0 + pc + j < Wd) out[j] = s1 * av[j] - s2 * acc[i][j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int v = v0 + pc + j;
+                    if (v >= Wd) break;
+                    if (gray[i][j] >= G) {   // a voxel outside the lattice: no field value
+                        out[j] = 0.f;
+                        continue;
+                    }
+                    const long long o = ((long long)gray[i][j] * H + u) * fpitch + v;
+                    out[j] = s1 * __ldg(A + o) - s2 * acc[i][j];
+                }
             }
         }
     }
@@ -386,10 +366,10 @@ cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long
     bwd_codebook_kernel<<<B, kRunThreads, smem1, s>>>(L);
     e = cudaGetLastError();
     if (e != cudaSuccess || !L.grad_h || pixel_tiles <= 0) return e;
-    const size_t smem2 = (size_t)max_M * sizeof(int);
+    const size_t smem2 = (size_t)max_M * 7 * sizeof(int);   // positions, sites, tile list
     e = cudaFuncSetAttribute(bwd_pixels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
-    bwd_pixels_kernel<<<(unsigned)pixel_tiles, kThreads, smem2, s>>>(L);
+    bwd_pixels_kernel<<<(unsigned)B, kThreads, smem2, s>>>(L);
     return cudaGetLastError();
 }
 

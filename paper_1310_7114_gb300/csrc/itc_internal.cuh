@@ -83,7 +83,7 @@ struct PlanHeader {
     long long nints;
     long long ws_scal_off;      // bytes: per-image backward scalars (4 doubles each)
     long long bwd_tiles;        // backward pixel tiles over all images
-    int bwd_prefix_off;         // offset (ints) of the backward tile prefix (B + 1 ints)
+    int bwd_order_off;          // offset (ints) of the backward image order (B ints, most tiles first)
     long long tmap_off;         // bytes from plan start to CUtensorMap[B] (input tiles)
     ClassInfo cls[kMaxClasses];
 };
@@ -140,7 +140,7 @@ struct BackwardLaunch {
     float* grad_h;
     itc_stats* stats;
     double* scal;               // per-image scalars in workspace: S_XW, S_WW, S_XX, gD
-    const int* bwd_prefix;      // B + 1 prefix of backward pixel tiles
+    const int* bwd_order;       // image of each backward pixel CTA (B ints, most tiles first)
     int B;
 };
 

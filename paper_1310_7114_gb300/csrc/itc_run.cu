@@ -272,8 +272,9 @@ template <int ND>
 cudaError_t launch_nd(const RunLaunch& L, int nimg, int max_M, cudaStream_t s) {
     const size_t smem = (size_t)max_M * (ND == 2 ? sizeof(float2) : sizeof(float4));
     const int nper = (max_M + kRunThreads - 1) / kRunThreads;
+    static_assert(ITC_MAX_M <= 32 * kRunThreads, "codebooks per thread cover ITC_MAX_M");
     auto k = nper <= 1 ? run_kernel<1, ND> : nper <= 2 ? run_kernel<2, ND> : nper <= 4 ? run_kernel<4, ND>
-                                                                                         : run_kernel<16, ND>;
+           : nper <= 8 ? run_kernel<8, ND> : nper <= 16 ? run_kernel<16, ND> : run_kernel<32, ND>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<nimg, kRunThreads, smem, s>>>(L);

@@ -233,3 +233,30 @@ def test_pipelined_and_range_runs_equal_plain_run():
         outs.append((W.cpu().numpy().copy(), st.cpu().numpy().tobytes()))
     for W, st in outs[1:]:
         assert np.array_equal(W, outs[0][0]) and st == outs[0][1]
+
+
+@pytest.mark.parametrize("M", [700, 2048])
+def test_large_codebooks_against_oracle(M):
+    """Many codebook vectors per image (up to the build's limit of 2048): each thread owns
+    several codebooks; a few iterations must match the oracle (ties aside)."""
+    rng = np.random.default_rng(M)
+    img = (rng.random((160, 150)) < 0.35).astype(np.uint8)
+    W0 = synth.init_codebook(synth.rng_for(9, M), img.astype(np.float32), M)
+    _, Ws, st = run_plan([img], [M], [W0], itc.make_params(2.0, 3.0, 3))
+    _check_run(img, 2.0, M, 3, W0, Ws[0], st[0], f"M={M}")
+
+
+def test_mixed_2d_and_3d_plan():
+    """One plan holding binary, weighted and gray-lattice images: every image's result equals
+    its own single-image plan."""
+    gray = (synth.c5_gray(3, size=48).astype(np.int64) * 40 // 256).astype(np.uint8)
+    imgs = [synth.c1_image(4), gray, synth.c4_weights(5)[:70, :90]]
+    W0s = [synth.init_codebook(synth.rng_for(1, 4), imgs[0].astype(np.float32), 8),
+           synth.init_codebook_gray(synth.rng_for(5, 3), gray, 10),
+           synth.init_codebook(synth.rng_for(4, 5), imgs[2], 12, 0.5)]
+    params = [itc.make_params(2.0, 3.0, 10), itc.make_params((2.0, 2.0, 3.0), 3.0, 10), itc.make_params(3.0, 3.0, 10)]
+    plan, Ws, st = run_plan(imgs, [8, 10, 12], W0s, params, ndims=[2, 3, 2], Gs=[1, 40, 1])
+    for b in range(3):
+        _, Wb, sb = run_plan([imgs[b]], [len(W0s[b])], [W0s[b]], params[b], ndims=[[2, 3, 2][b]], Gs=[[1, 40, 1][b]])
+        assert np.array_equal(Ws[b], Wb[0]), b
+        assert st[b]["dcs"] == sb[0]["dcs"], b

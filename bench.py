@@ -33,6 +33,22 @@ sys.path.insert(0, ROOT)
 METRIC = "batched ITC images/s vs per-image launch at ≤1e-5 rel err; conv GB/s % HBM peak"
 FALLBACK_HBM_GBS = 6800.0
 
+# DRAM bytes (read + write) per pixel of the fields pass, from one ncu capture of the C3 workload
+# with 1024 images (profiles/fields_tma_kernel_c3_1024.md), valid only for the kernel source it was
+# taken on (sha256 prefix below); scaled to a launch by its pixel count.
+FIELDS_TRAFFIC = {"workload": "c3", "bytes_per_pixel": 954.7e6 / 86358723, "source_sha256": "ba422d6171b21d3b",
+                  "source": "paper_1310_7114_gb300/csrc/itc_fields_tma.cu"}
+
+
+def fields_traffic(name, pixels):
+    import hashlib
+    if name != FIELDS_TRAFFIC["workload"]:
+        return None
+    with open(os.path.join(ROOT, FIELDS_TRAFFIC["source"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != FIELDS_TRAFFIC["source_sha256"]:
+            return None   # the kernel changed since the counters were taken
+    return FIELDS_TRAFFIC["bytes_per_pixel"] * pixels
+
 WORKLOADS = {
     "c3": dict(desc="4096 binary blob silhouettes, sides U{64..512}, M in {16,32,64,128}, sigma in {2,3,4}, "
                     "50 iterations, fwd+bwd", n=4096, iters=50),
@@ -187,6 +203,8 @@ def run_ours(args, rank, world, local_rank):
     buf, views = itc.pack_images(images, dev)
     params = [itc.make_params(p["sigma"], 3.0, p["iters"]) for p in pk]
     plan = itc.Plan(views, Ms, params, ndims=ndims, Gs=Gs)
+    # per sigma class: fields tile height, persistent CTAs per SM, staging -- timed on this batch
+    tuning = plan.classes() if args.no_tune else plan.autotune(reps=3)
     W0 = plan.pack_W(W0s)
     W = W0.clone()
     stats = itc.new_stats(B, dev)
@@ -363,13 +381,17 @@ def run_ours(args, rank, world, local_rank):
                    "pixels_per_gpu": int(sum(im.size for im in images)),
                    "l2": "inputs larger than L2 (packed images %.0f MB, fields %.0f MB per step)"
                          % (buf.numel() * buf.element_size() / 1e6, plan.ws_bytes / 1e6),
-                   "parallelism": f"replicas x{world} (independent images per GPU, no collective)"},
+                   "parallelism": f"replicas x{world} (independent images per GPU, no collective)",
+                   "fields_tuning": [{k: c[k] for k in ("sigma", "images", "tile_h", "ctas_per_sm", "staging",
+                                                        "tuned_ms")} for c in tuning]},
         "phases_ms": {"fields": f_avg, "iterate": statistics.mean(i_ms), "backward": statistics.mean(b_ms),
                       "note": "phases run in sequence in a separate timed loop; the headline step overlaps "
                               f"fields and iterations over {args.chunks} image ranges on two streams"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "kernel": "fields pass (fields_kernel, one launch per sigma class)",
+                     "frac": achieved / hbm, "traffic": fields_traffic(name, sum(im.size for im in images)),
+                     "traffic_note": "ncu dram bytes of the 1024-image capture scaled by pixels "
+                                     "(profiles/fields_tma_kernel_c3_1024.md)",
+                     "kernel": "fields pass (fields_tma_kernel, persistent, one launch per sigma class)",
                      "algorithmic_bytes_per_launch": fbytes, "peak_source": f"{peak_src} hbm_gbs"},
         "e2e": {"value": world * B / (e2e_ms / 1000.0), "unit": "images/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
@@ -436,6 +458,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-images", type=int, default=8)
+    ap.add_argument("--no-tune", action="store_true", help="keep the default fields configuration")
     ap.add_argument("--chunks", type=int, default=1, help="image ranges of the pipelined fields/iterations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else max(args.warmup, 1)

@@ -63,6 +63,10 @@ extern "C" {
 #define ITC_FIELDS_ABSOLUTE 2  /* itc_fields writes u.X, v.X (, g.X) convolutions, not centred */
 #define ITC_STOP_ON_FIXED 4    /* stop when an iteration moves no codebook (theta = 0 test of
                                   Algorithm 1) */
+#define ITC_TEST_STALL_WAIT 256 /* test hook (itc_fields, tensor-tile path only): the first tile
+                                  copy of the first CTA is never started, so that CTA's bounded
+                                  wait (about one second) runs out; the call then reports
+                                  S_XX = NaN and nothing else is affected.  Never set otherwise. */
 
 /* Limits of this build. */
 #define ITC_MAX_RADIUS_UV 32   /* R_u, R_v */
@@ -262,6 +266,43 @@ int itc_run_iterate_range(const void* plan_host, const void* plan_dev, int b0, i
  */
 int itc_run_pipelined(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats,
                       void* ws, size_t ws_bytes, void* stream, void* stream2, int chunks);
+
+/*
+ * itc_autotune -- pick, per parameter class of a plan, the fields-pass configuration that runs
+ * fastest on this GPU for this batch: the rows of output per tile (64 or 32, i.e. how much of
+ * the R-wide halo the row pass recomputes), the number of persistent CTAs per SM (1 or as many
+ * as fit), and the input staging (tensor-memory-accelerator tiles, where the image rows are
+ * 16-byte aligned, or plain loads).  Each candidate is timed with CUDA events over `reps`
+ * launches (after one untimed launch) on `stream`; the choice is stored in the host plan and
+ * the updated plan is copied to plan_dev (synchronously).  Results of later calls do not
+ * depend on the choice except for the summation order of S_XX (fields are identical).
+ * `ws` is overwritten.  Errors: ITC_ERR_INVALID_ARG, ITC_ERR_WORKSPACE, ITC_ERR_CUDA.
+ */
+int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int reps,
+                 void* stream);
+
+/*
+ * itc_plan_configure -- set the fields-pass configuration of class c by hand (what itc_autotune
+ * chooses): staging 1 = tensor tiles with tile_h 32 or 64 output rows, staging 0 = plain loads
+ * with the fixed tile height of the lattice dimension (64 in 2-D, 32 in 3-D; pass it);
+ * grid_per_sm = persistent CTAs per SM (0 = as many as fit, else 1..64).  Updates the host
+ * plan and copies it to plan_dev (synchronously on `stream`).  Errors: ITC_ERR_INVALID_ARG,
+ * ITC_ERR_UNSUPPORTED (tensor tiles for a class whose images cannot use them), ITC_ERR_CUDA.
+ */
+int itc_plan_configure(void* plan_host, void* plan_dev, int c, int tile_h, int grid_per_sm,
+                       int staging, void* stream);
+
+/* Number of parameter classes of a plan (host-only); negative on error. */
+int itc_plan_classes(const void* plan_host);
+
+/*
+ * itc_plan_class -- the configuration of class c (host-only): lattice dimension, sigma, output
+ * rows per fields tile, persistent CTAs per SM (0 = as many as fit), staging (1 = tensor tiles,
+ * 0 = plain loads), number of images and the tuned fields time in ms (0 if not tuned).  Any
+ * output pointer may be NULL.  Errors: ITC_ERR_INVALID_ARG.
+ */
+int itc_plan_class(const void* plan_host, int c, int* ndim, float* sigma, int* tile_h,
+                   int* grid_per_sm, int* staging, int* images, float* tuned_ms);
 
 /*
  * itc_backward -- gradient of Eq. (1) for every image of a plan, scaled by an upstream gradient:

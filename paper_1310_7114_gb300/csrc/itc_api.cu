@@ -45,7 +45,8 @@ int check_params(const itc_params* p, int ndim) {
     for (int i = 0; i < ndim; ++i)
         if (!finite_pos(p->sigma[i])) return ITC_ERR_INVALID_ARG;
     if (p->iters < 0 || !isfinite(p->step_scale)) return ITC_ERR_INVALID_ARG;
-    if (p->flags & ~(ITC_CONTINUOUS | ITC_FIELDS_ABSOLUTE | ITC_STOP_ON_FIXED)) return ITC_ERR_INVALID_ARG;
+    if (p->flags & ~(ITC_CONTINUOUS | ITC_FIELDS_ABSOLUTE | ITC_STOP_ON_FIXED | ITC_TEST_STALL_WAIT))
+        return ITC_ERR_INVALID_ARG;
     const double ru = ceil((double)p->trunc * p->sigma[0]), rv = ceil((double)p->trunc * p->sigma[1]);
     if (ru > ITC_MAX_RADIUS_UV || rv > ITC_MAX_RADIUS_UV) return ITC_ERR_UNSUPPORTED;
     if (ndim == 3 && ceil((double)p->trunc * p->sigma[2]) > ITC_MAX_RADIUS_G) return ITC_ERR_UNSUPPORTED;
@@ -144,22 +145,66 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // Tensor map of an image's input for the TMA fields tiles; false if the image's rows are not
 // 16-byte aligned or no encoder is available.
-bool encode_input_map(const itc_image* img, int R, CUtensorMap* out) {
-    const int es = img->dtype == ITC_U8 ? 1 : 4;
-    if (((uintptr_t)img->data % 16) != 0 || ((size_t)img->pitch * es) % 16 != 0) return false;
+bool encode_input_map(const void* data, int H, int W, int pitch, int dtype, int R, int tile_h, CUtensorMap* out) {
+    const int es = dtype == ITC_U8 ? 1 : 4;
+    if (((uintptr_t)data % 16) != 0 || ((size_t)pitch * es) % 16 != 0) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     int bw = 0, bh = 0;
-    fields_tma_box(img->dtype, R, &bw, &bh);
-    const cuuint64_t dims[2] = {(cuuint64_t)img->W, (cuuint64_t)img->H};
-    const cuuint64_t strides[1] = {(cuuint64_t)img->pitch * es};
+    fields_tma_box(dtype, R, tile_h, &bw, &bh);
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
     const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(out, img->dtype == ITC_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                           2, const_cast<void*>(img->data), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    const CUresult r = enc(out, dtype == ITC_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                           2, const_cast<void*>(data), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+bool encode_input_map(const itc_image* img, int R, CUtensorMap* out) {
+    return encode_input_map(img->data, img->H, img->W, img->pitch, img->dtype, R, 64, out);
+}
+
+// Tile grid, class tile prefixes and S_XX partial offsets of a plan from each class's tile
+// height; per-image tensor maps follow the tile height.  The int area keeps its size.
+int relayout(PlanHeader* h, ImageDesc* descs, int* ints, CUtensorMap* tmaps) {
+    for (int c = 0; c < h->ncls; ++c) {
+        ClassInfo& ci = h->cls[c];
+        if (ci.tma && !ci.use_plain)
+            for (int i = 0; i < ci.nimg && ci.tma; ++i) {
+                const ImageDesc& d = descs[ints[ci.list_off + i]];
+                if (!encode_input_map(d.data, d.H, d.W, d.pitch, d.dtype, ci.taps.R[0], ci.tile_h,
+                                      tmaps + ints[ci.list_off + i]))
+                    ci.tma = 0;
+            }
+        // the plain-load kernel has one tile height per lattice dimension
+        if (!ci.tma || ci.use_plain) ci.tile_h = tile_h_of(ci.ndim);
+    }
+    for (int b = 0; b < h->B; ++b) {
+        ImageDesc& d = descs[b];
+        const ClassInfo& ci = h->cls[d.cls];
+        d.tiles_u = (d.H + ci.tile_h - 1) / ci.tile_h;
+    }
+    long long pbase = 0;
+    for (int c = 0; c < h->ncls; ++c) {
+        ClassInfo& ci = h->cls[c];
+        long long t = 0;
+        ci.partial_base = pbase;
+        for (int i = 0; i < ci.nimg; ++i) {
+            ImageDesc& d = descs[ints[ci.list_off + i]];
+            ints[ci.prefix_off + i] = (int)t;
+            d.tile_begin = (int)t;
+            d.partial_off = pbase + t;
+            t += tiles_of(d);
+            if (t > 0x7fffffffLL) return ITC_ERR_UNSUPPORTED;
+        }
+        ints[ci.prefix_off + ci.nimg] = (int)t;
+        ci.ntiles = (int)t;
+        pbase += t;
+    }
+    h->total_tiles = pbase;
+    return ITC_OK;
 }
 
 // Tiles [begin, end) of one class (L.tile_base is set to begin here).
@@ -240,6 +285,7 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
     L.partials = reinterpret_cast<double*>(ws);
     L.tile_h = tile_h_of(img->ndim);
     L.absolute = (p->flags & ITC_FIELDS_ABSOLUTE) ? 1 : 0;
+    L.test_stall = (p->flags & ITC_TEST_STALL_WAIT) ? 1 : 0;
     const long long nt = tiles_of(L.one);
     if (nt > 0x7fffffffLL) return ITC_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -326,8 +372,6 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
             ci.tma = fields_tma_supported(ci.ndim, ci.taps.R[0], ci.taps.R[1]) ? 1 : 0;
         }
         cls_of[b] = c;
-        ClassInfo& cb = h->cls[c];
-        if (cb.tma && !encode_input_map(imgs + b, cb.taps.R[0], tmaps + b)) cb.tma = 0;
         fill_desc(imgs + b, pb, M[b], descs + b);
         descs[b].cls = c;
     }
@@ -356,9 +400,8 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     h->total_pixels = ghoff;
     h->max_M = (int)maxM;
 
-    // per class: image list, tile prefix, partial layout (class-major, images in list order)
+    // per class: image list (ascending image index) and the place of its tile prefix
     int io = 0;
-    long long pbase = 0;
     for (int c = 0; c < h->ncls; ++c) {
         ClassInfo& ci = h->cls[c];
         ci.list_off = io;
@@ -368,22 +411,22 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         ci.nimg = n;
         io += n;
         ci.prefix_off = io;
-        long long t = 0;
-        ci.partial_base = pbase;
-        for (int i = 0; i < n; ++i) {
-            ImageDesc& d = descs[ints[ci.list_off + i]];
-            ints[io + i] = (int)t;
-            d.tile_begin = (int)t;
-            d.partial_off = pbase + t;
-            t += tiles_of(d);
-            if (t > 0x7fffffffLL) return ITC_ERR_UNSUPPORTED;
-        }
-        ints[io + n] = (int)t;
         io += n + 1;
-        ci.ntiles = (int)t;
-        pbase += t;
     }
-    h->total_tiles = pbase;
+    // S_XX partials: room for the most tiles any tunable tile height can give (32-row tiles)
+    long long pcap = 0;
+    {
+        // the largest count over "every class at its smallest tile height" bounds any tuning
+        for (int c = 0; c < h->ncls; ++c)
+            if (h->cls[c].tma) h->cls[c].tile_h = 32;
+        int rc = relayout(h, descs, ints, tmaps);
+        if (rc) return rc;
+        pcap = h->total_tiles;
+        for (int c = 0; c < h->ncls; ++c) h->cls[c].tile_h = tile_h_of(h->cls[c].ndim);
+        rc = relayout(h, descs, ints, tmaps);
+        if (rc) return rc;
+    }
+    long long pbase = pcap;
     // backward pixel pass: one CTA per image, images with the most tiles first
     const int bwd_off = io;
     {
@@ -456,11 +499,137 @@ int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, in
         L.tile_h = ci.tile_h;
         L.absolute = 0;
         L.tmaps = reinterpret_cast<const CUtensorMap*>(pd + h->tmap_off);
-        const int rc = cuda_status(
-            launch_fields_any(L, ci.tma != 0, t0, t1, ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
+        L.grid_per_sm = ci.grid_per_sm;
+        const int rc = cuda_status(launch_fields_any(L, ci.tma != 0 && !ci.use_plain, t0, t1, ci.taps.R[0],
+                                                     ci.taps.R[1], ci.ndim, ci.dtype, s));
         if (rc) return rc;
     }
     return ITC_OK;
+}
+
+int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int reps, void* stream) {
+    PlanHeader* h = const_cast<PlanHeader*>(plan_of(plan_host));
+    if (!h || !plan_dev || !aligned(plan_dev, 16) || reps < 1 || reps > 1000) return ITC_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* ph = reinterpret_cast<unsigned char*>(plan_host);
+    ImageDesc* descs = reinterpret_cast<ImageDesc*>(ph + h->desc_off);
+    int* ints = reinterpret_cast<int*>(ph + h->ints_off);
+    CUtensorMap* tmaps = reinterpret_cast<CUtensorMap*>(ph + h->tmap_off);
+    const size_t nbytes = plan_layout(h->B, nullptr, nullptr);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return ITC_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return ITC_ERR_CUDA; }
+    int rc = ITC_OK;
+    // Apply the current choices to both plan copies, then time one class's fields launches.
+    auto time_class = [&](int c, float* ms) -> int {
+        int r = relayout(h, descs, ints, tmaps);
+        if (r) return r;
+        if (cudaMemcpyAsync(plan_dev, plan_host, nbytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return ITC_ERR_CUDA;
+        const ClassInfo& ci = h->cls[c];
+        FieldsLaunch L;
+        memset(&L, 0, sizeof(L));
+        const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
+        L.taps = ci.taps;
+        L.descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
+        L.img_list = reinterpret_cast<const int*>(pd + h->ints_off) + ci.list_off;
+        L.tile_prefix = reinterpret_cast<const int*>(pd + h->ints_off) + ci.prefix_off;
+        L.nimg = ci.nimg;
+        unsigned char* w = reinterpret_cast<unsigned char*>(ws);
+        L.fields = reinterpret_cast<float*>(w + h->ws_fields_off);
+        L.partials = reinterpret_cast<double*>(w + h->ws_partials_off);
+        L.tile_h = ci.tile_h;
+        L.tmaps = reinterpret_cast<const CUtensorMap*>(pd + h->tmap_off);
+        L.grid_per_sm = ci.grid_per_sm;
+        const bool tma = ci.tma && !ci.use_plain;
+        for (int i = 0; i <= reps; ++i) {   // the first launch warms caches and is not timed
+            if (i == 1 && cudaEventRecord(e0, s) != cudaSuccess) return ITC_ERR_CUDA;
+            r = cuda_status(launch_fields_any(L, tma, 0, ci.ntiles, ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
+            if (r) return r;
+        }
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return ITC_ERR_CUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return ITC_ERR_CUDA;
+        *ms = t / reps;
+        return ITC_OK;
+    };
+    for (int c = 0; c < h->ncls && !rc; ++c) {
+        ClassInfo& ci = h->cls[c];
+        if (ci.ndim != 2) continue;   // 3-D tiles have one configuration
+        struct Cand { int plain, tile_h, grid; };
+        Cand cands[5];
+        int nc = 0;
+        if (ci.tma) {
+            cands[nc++] = {0, 64, 0};
+            cands[nc++] = {0, 64, 1};
+            cands[nc++] = {0, 32, 0};
+            cands[nc++] = {0, 32, 1};
+        }
+        cands[nc++] = {1, 64, 0};
+        float best = 3.4e38f;
+        Cand pick = cands[0];
+        for (int i = 0; i < nc && !rc; ++i) {
+            ci.use_plain = cands[i].plain;
+            ci.tile_h = cands[i].tile_h;
+            ci.grid_per_sm = cands[i].grid;
+            float ms = 0.f;
+            rc = time_class(c, &ms);
+            if (!rc && ms < best) { best = ms; pick = cands[i]; }
+        }
+        ci.use_plain = pick.plain;
+        ci.tile_h = pick.tile_h;
+        ci.grid_per_sm = pick.grid;
+        ci.tuned_ms = best;
+    }
+    if (!rc) rc = relayout(h, descs, ints, tmaps);
+    if (!rc && cudaMemcpyAsync(plan_dev, plan_host, nbytes, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = ITC_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = ITC_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+int itc_plan_class(const void* plan_host, int c, int* ndim, float* sigma, int* tile_h, int* grid_per_sm,
+                   int* staging, int* images, float* tuned_ms) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || c < 0 || c >= h->ncls) return ITC_ERR_INVALID_ARG;
+    const ClassInfo& ci = h->cls[c];
+    if (ndim) *ndim = ci.ndim;
+    if (sigma) for (int i = 0; i < 3; ++i) sigma[i] = ci.taps.sigma[i];
+    if (tile_h) *tile_h = ci.tile_h;
+    if (grid_per_sm) *grid_per_sm = ci.grid_per_sm;
+    if (staging) *staging = (ci.tma && !ci.use_plain) ? 1 : 0;
+    if (images) *images = ci.nimg;
+    if (tuned_ms) *tuned_ms = ci.tuned_ms;
+    return ITC_OK;
+}
+
+int itc_plan_configure(void* plan_host, void* plan_dev, int c, int tile_h, int grid_per_sm, int staging,
+                       void* stream) {
+    PlanHeader* h = const_cast<PlanHeader*>(plan_of(plan_host));
+    if (!h || !plan_dev || !aligned(plan_dev, 16) || c < 0 || c >= h->ncls) return ITC_ERR_INVALID_ARG;
+    if (grid_per_sm < 0 || grid_per_sm > 64 || (staging != 0 && staging != 1)) return ITC_ERR_INVALID_ARG;
+    ClassInfo& ci = h->cls[c];
+    if (staging == 1 && !ci.tma) return ITC_ERR_UNSUPPORTED;
+    if (staging == 1 ? (tile_h != 32 && tile_h != 64) : tile_h != tile_h_of(ci.ndim)) return ITC_ERR_INVALID_ARG;
+    ci.use_plain = staging ? 0 : 1;
+    ci.tile_h = tile_h;
+    ci.grid_per_sm = grid_per_sm;
+    unsigned char* ph = reinterpret_cast<unsigned char*>(plan_host);
+    int rc = relayout(h, reinterpret_cast<ImageDesc*>(ph + h->desc_off), reinterpret_cast<int*>(ph + h->ints_off),
+                      reinterpret_cast<CUtensorMap*>(ph + h->tmap_off));
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(plan_dev, plan_host, plan_layout(h->B, nullptr, nullptr), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return ITC_ERR_CUDA;
+    return ITC_OK;
+}
+
+int itc_plan_classes(const void* plan_host) {
+    const PlanHeader* h = plan_of(plan_host);
+    return h ? h->ncls : ITC_ERR_INVALID_ARG;
 }
 
 int itc_run_iterate_range(const void* plan_host, const void* plan_dev, int b0, int b1, float* W, itc_stats* stats,

@@ -85,16 +85,18 @@ __device__ __forceinline__ void locate_warp(const FieldsLaunch& L, int t, int& i
     local = t - __ldg(prefix + p);
 }
 
-// Bounded wait for the staged tile (about a second at most); false means the copy never landed.
+// Bounded wait for a staged tile: gives up after about one second (2^31 SM clocks); false means
+// the copy never landed.
 __device__ __forceinline__ bool wait_stage(uint64_t* bar, uint32_t parity) {
-    for (long long i = 0; i < (1LL << 24); ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1LL << 31)) return false;
+    return true;
 }
 
-template <int R, bool ABS, int DTYPE>
+template <int R, bool ABS, int DTYPE, int TH>
 __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_constant__ FieldsLaunch L, int ntiles) {
-    constexpr int TW = kTileW, TH = 64, K = TH / 16;
+    constexpr int TW = kTileW, K = TH / 16;
     constexpr int ROWS = TH + 2 * R;
     constexpr int SW = ((TW + 2 * R + 3) & ~3) + 4;
     constexpr int ES = DTYPE == ITC_U8 ? 1 : 4;
@@ -131,7 +133,8 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
 
     // tile copies run NST tiles ahead: the n-th tile of this CTA lands in stage n % NST
     // called by all of warp 0: resolve the tile, remember it for its stage, lane 0 starts the copy
-    auto issue = [&](int t, int buf) {
+    uint32_t inflight = 0;   // (thread 0) bit b: a copy into stage b has been started, not yet waited for
+    auto issue = [&](int t, int buf, bool copy) {
         int local, img;
         locate_warp(L, t, img, local);
         if (tid == 0) {
@@ -140,15 +143,20 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
             const CUtensorMap* map = L.descs ? L.tmaps + img : &L.tmap_one;
             s_img[buf] = img;
             s_local[buf] = local;
-            mbar_expect_tx(&bar[buf], BOX_BYTES);
-            tma_load_2d(stage0 + buf * STAGE_BYTES, map, tv * TW - RA, tu * TH - R, &bar[buf]);
+            if (copy) {
+                mbar_expect_tx(&bar[buf], BOX_BYTES);
+                tma_load_2d(stage0 + buf * STAGE_BYTES, map, tv * TW - RA, tu * TH - R, &bar[buf]);
+                inflight |= 1u << buf;
+            }
         }
     };
 
     int t = L.tile_base + blockIdx.x;   // tiles [tile_base, ntiles) of the class
     if (tid < 32)
         for (int b = 0; b < NST; ++b)
-            if (t + b * (int)gridDim.x < ntiles) issue(t + b * gridDim.x, b);
+            if (t + b * (int)gridDim.x < ntiles)
+                // the test hook starts no copy for the first tile of CTA 0: its wait cannot end
+                issue(t + b * gridDim.x, b, !(L.test_stall && blockIdx.x == 0 && b == 0));
     uint32_t phase = 0;   // bit b: parity of the next completion of bar[b]
     int n = 0;            // tiles of this CTA so far
     const int kb = tid >> 4, cg = tid & 15;
@@ -170,21 +178,37 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
     for (; t < ntiles; t += gridDim.x) {
         const int buf = NST == 2 ? (n & 1) : 0;
         const unsigned char* stage = stage0 + buf * STAGE_BYTES;
-        if (tid == 0 && !wait_stage(&bar[buf], (phase >> buf) & 1u)) s_abort = 1;
+        if (tid == 0) {
+            if (wait_stage(&bar[buf], (phase >> buf) & 1u)) inflight &= ~(1u << buf);
+            else s_abort = 1;
+        }
         __syncthreads();   // the staged tile has landed; the previous tile's passes are done
         if (tid == 0) flush();
+        if (s_abort) {
+            // every tile this CTA still owns gets a NaN S_XX share, so each affected image
+            // reports a non-finite status; then the copies still in flight land (bounded waits)
+            if (tid < 32) {
+                for (int tt = t; tt < ntiles; tt += gridDim.x) {
+                    int im, lc;
+                    locate_warp(L, tt, im, lc);
+                    const ImageDesc* d2 = L.descs ? L.descs + im : &L.one;
+                    if (tid == 0) L.partials[d2->partial_off + lc] = __longlong_as_double(0x7ff8000000000000LL);
+                }
+                if (tid == 0)
+                    for (int b = 0; b < NST; ++b)
+                        if ((inflight >> b) & 1u) wait_stage(&bar[b], (phase >> b) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+        phase ^= 1u << buf;
+        ++n;
         const int img = s_img[buf], local = s_local[buf];
         const ImageDesc* dp = L.descs ? L.descs + img : &L.one;
         const int H = dp->H, W = dp->W, fpitch = dp->fpitch;
         const int u0 = (local / dp->tiles_v) * TH, v0 = (local % dp->tiles_v) * TW;
         float* const fbase = L.fields + dp->field_off;
         const long long plane = dp->plane_floats;
-        if (s_abort) {
-            if (tid == 0) L.partials[dp->partial_off + local] = __longlong_as_double(0x7ff8000000000000LL);
-            return;   // S_XX of the image becomes NaN: the host sees a non-finite status
-        }
-        phase ^= 1u << buf;
-        ++n;
 
         // staged box -> float input tile, columns shifted so that s_in column 0 is v0 - R; one
         // warp per staged row, one 4-column group per lane, a ballot gives the row's zero mask
@@ -220,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
             if (tid < 32) colbits[tid >> 2][tid & 3] = 0u;
         }
         const int any = __syncthreads_or(nonzero);   // the stage is free from here on
-        if (tid < 32 && t + NST * (int)gridDim.x < ntiles) issue(t + NST * gridDim.x, buf);
+        if (tid < 32 && t + NST * (int)gridDim.x < ntiles) issue(t + NST * gridDim.x, buf, true);
 
         const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
         if (!any) {
@@ -377,9 +401,9 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
     if (tid == 0) flush();
 }
 
-template <int R, bool ABS, int DTYPE>
+template <int R, bool ABS, int DTYPE, int TH>
 cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
-    constexpr int TW = kTileW, TH = 64;
+    constexpr int TW = kTileW;
     constexpr int ROWS = TH + 2 * R;
     constexpr int SW = ((TW + 2 * R + 3) & ~3) + 4;
     constexpr int ES = DTYPE == ITC_U8 ? 1 : 4;
@@ -388,13 +412,14 @@ cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
     constexpr int STAGE_BYTES = (BOX_BYTES + 127) & ~127;
     constexpr int NST = STAGE_BYTES <= 16384 ? 2 : 1;
     const size_t smem = 128 + NST * (size_t)STAGE_BYTES + (size_t)ROWS * SW * 4 + 2 * (size_t)ROWS * TW * 4;
-    auto k = fields_tma_kernel<R, ABS, DTYPE>;
+    auto k = fields_tma_kernel<R, ABS, DTYPE, TH>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem)) != cudaSuccess) return e;
+    if (L.grid_per_sm > 0 && L.grid_per_sm < per_sm) per_sm = L.grid_per_sm;   // tuned persistent grid
     const int count = ntiles - L.tile_base;
     const int grid = count < sms * (per_sm > 0 ? per_sm : 1) ? count : sms * (per_sm > 0 ? per_sm : 1);
     k<<<grid, kThreads, smem, s>>>(L, ntiles);
@@ -403,9 +428,14 @@ cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
 
 template <bool ABS, int DTYPE>
 cudaError_t dispatch(const FieldsLaunch& L, int ntiles, int R, cudaStream_t s) {
-    if (R == 6) return launch_tma<6, ABS, DTYPE>(L, ntiles, s);
-    if (R == 9) return launch_tma<9, ABS, DTYPE>(L, ntiles, s);
-    return launch_tma<12, ABS, DTYPE>(L, ntiles, s);
+    if (L.tile_h == 32) {
+        if (R == 6) return launch_tma<6, ABS, DTYPE, 32>(L, ntiles, s);
+        if (R == 9) return launch_tma<9, ABS, DTYPE, 32>(L, ntiles, s);
+        return launch_tma<12, ABS, DTYPE, 32>(L, ntiles, s);
+    }
+    if (R == 6) return launch_tma<6, ABS, DTYPE, 64>(L, ntiles, s);
+    if (R == 9) return launch_tma<9, ABS, DTYPE, 64>(L, ntiles, s);
+    return launch_tma<12, ABS, DTYPE, 64>(L, ntiles, s);
 }
 
 }  // namespace
@@ -414,10 +444,10 @@ bool fields_tma_supported(int ndim, int Ru, int Rv) {
     return ndim == 2 && Ru == Rv && (Ru == 6 || Ru == 9 || Ru == 12);
 }
 
-int fields_tma_box(int dtype, int R, int* box_w, int* box_h) {
+int fields_tma_box(int dtype, int R, int tile_h, int* box_w, int* box_h) {
     const int ra = dtype == ITC_U8 ? 16 : ((R + 3) & ~3);
     *box_w = kTileW + 2 * ra;
-    *box_h = 64 + 2 * R;
+    *box_h = tile_h + 2 * R;
     return 0;
 }
 

@@ -60,6 +60,9 @@ struct ClassInfo {
     int ndim, dtype, absolute, tile_h;
     int nimg, ntiles;
     int tma;                    // every image of the class has a tensor map (TMA fields path)
+    int use_plain;              // tuned: take the plain-staged kernel even though TMA is possible
+    int grid_per_sm;            // tuned persistent CTAs per SM (0: as many as fit)
+    float tuned_ms;             // fields time of the class under the chosen configuration (0: untuned)
     int list_off;               // offset (ints) of this class's image list in the plan int area
     int prefix_off;             // offset (ints) of the class tile prefix (nimg + 1 ints)
     long long partial_base;     // first partial of the class
@@ -113,6 +116,8 @@ struct FieldsLaunch {
     int tile_h;
     int absolute;
     int tile_base;              // first tile of this launch within the class (image sub-ranges)
+    int test_stall;             // ITC_TEST_STALL_WAIT: CTA 0 waits for a phase that never completes
+    int grid_per_sm;            // persistent CTAs per SM (0: as many as fit)
 };
 
 struct RunLaunch {
@@ -158,7 +163,7 @@ cudaError_t launch_reduce_sxx(const double* partials, int n, double* out, cudaSt
 // TMA-staged 2-D fields (itc_fields_tma.cu): the radii it is compiled for, its box per radius
 // and data type, and its launch.
 bool fields_tma_supported(int ndim, int Ru, int Rv);
-int fields_tma_box(int dtype, int R, int* box_w, int* box_h);
+int fields_tma_box(int dtype, int R, int tile_h, int* box_w, int* box_h);
 cudaError_t launch_fields_tma(const FieldsLaunch& L, int ntiles, int R, int dtype, cudaStream_t s);
 // ndim: the lattice dimension of every image of the launch (2 or 3)
 cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s, int ndim);

@@ -29,13 +29,15 @@ ITC_F32 = 1
 ITC_CONTINUOUS = 1
 ITC_FIELDS_ABSOLUTE = 2
 ITC_STOP_ON_FIXED = 4
+ITC_TEST_STALL_WAIT = 256
 
 # every symbol include/itc.h declares
 EXPORTS = (
     "itc_field_pitch", "itc_fields_bytes", "itc_fields_workspace_bytes", "itc_status_string",
     "itc_fields", "itc_step", "itc_plan_bytes", "itc_plan", "itc_plan_pixels", "itc_plan_offsets",
     "itc_run", "itc_run_fields", "itc_run_iterate", "itc_run_fields_range", "itc_run_iterate_range",
-    "itc_run_pipelined", "itc_backward", "itc_fields_noalloc",
+    "itc_run_pipelined", "itc_backward", "itc_fields_noalloc", "itc_autotune", "itc_plan_classes",
+    "itc_plan_class", "itc_plan_configure",
 )
 
 
@@ -121,6 +123,16 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
         L.itc_run_iterate_range.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _SZ, _P]
         L.itc_run_pipelined.restype = ctypes.c_int
         L.itc_run_pipelined.argtypes = [_P, _P, _P, _P, _P, _SZ, _P, _P, ctypes.c_int]
+        L.itc_autotune.restype = ctypes.c_int
+        L.itc_autotune.argtypes = [_P, _P, _P, _SZ, ctypes.c_int, _P]
+        L.itc_plan_configure.restype = ctypes.c_int
+        L.itc_plan_configure.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
+        L.itc_plan_classes.restype = ctypes.c_int
+        L.itc_plan_classes.argtypes = [_P]
+        _I = ctypes.POINTER(ctypes.c_int)
+        _F = ctypes.POINTER(ctypes.c_float)
+        L.itc_plan_class.restype = ctypes.c_int
+        L.itc_plan_class.argtypes = [_P, ctypes.c_int, _I, _F, _I, _I, _I, _I, _F]
         L.itc_backward.restype = ctypes.c_int
         L.itc_backward.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]
         _lib = L
@@ -290,6 +302,31 @@ class Plan:
         _check(lib().itc_plan_offsets(self.host_ptr, int(b), ctypes.byref(f), ctypes.byref(w), ctypes.byref(g)),
                "itc_plan_offsets")
         return int(f.value), int(w.value), int(g.value)
+
+    def autotune(self, reps: int = 3, stream=None):
+        """itc_autotune: time the fields configurations per class and keep the fastest (updates both
+        plan copies; overwrites the workspace)."""
+        _check(lib().itc_autotune(self.host_ptr, self.dev.data_ptr(), self.ws.data_ptr(), self.ws.numel(), int(reps),
+                                  _stream(stream)), "itc_autotune")
+        return self.classes()
+
+    def configure(self, c: int, tile_h: int, ctas_per_sm: int = 0, staging: str = "tma", stream=None):
+        """itc_plan_configure: pin class c's fields configuration."""
+        _check(lib().itc_plan_configure(self.host_ptr, self.dev.data_ptr(), int(c), int(tile_h), int(ctas_per_sm),
+                                        1 if staging == "tma" else 0, _stream(stream)), "itc_plan_configure")
+
+    def classes(self):
+        """Configuration of every parameter class (itc_plan_class)."""
+        out = []
+        for c in range(lib().itc_plan_classes(self.host_ptr)):
+            nd, th, gp, st, ni = (ctypes.c_int() for _ in range(5))
+            sig, ms = (ctypes.c_float * 3)(), ctypes.c_float()
+            _check(lib().itc_plan_class(self.host_ptr, c, ctypes.byref(nd), sig, ctypes.byref(th), ctypes.byref(gp),
+                                        ctypes.byref(st), ctypes.byref(ni), ctypes.byref(ms)), "itc_plan_class")
+            out.append(dict(ndim=nd.value, sigma=[round(x, 4) for x in sig[:nd.value]], tile_h=th.value,
+                            ctas_per_sm=gp.value, staging="tma" if st.value else "plain", images=ni.value,
+                            tuned_ms=ms.value))
+        return out
 
     def fields_of(self, b: int):
         """View of image b's fields inside the workspace: [ndim+1, G, H, fpitch] float32."""

@@ -153,3 +153,33 @@ def test_product_path_has_no_cpu_fallback():
         if f.endswith(".py"):
             src = open(os.path.join(pkg, f)).read()
             assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_plan_class_queries_and_configuration_checks(L):
+    """Class queries are host-only; configuration and tuning reject bad arguments before any
+    device work.  Rows of 3 bytes past a multiple of 16 cannot use tensor tiles."""
+    rc, buf, ws = _plan(L, [(64, 64), (100, 70), (300, 513), (17, 9)], [8, 16, 128, 3],
+                        [_p(2.0), _p(3.0), _p(2.0), _p(4.0)])
+    assert rc == 0
+    hp = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.itc_plan_classes(hp) == 3
+    assert L.itc_plan_classes(None) == itc.ITC_ERR_INVALID_ARG
+    seen = []
+    for c in range(3):
+        nd, th, gp, st, ni = (ctypes.c_int(-9) for _ in range(5))
+        sig, ms = (ctypes.c_float * 3)(), ctypes.c_float(-1.0)
+        assert L.itc_plan_class(hp, c, ctypes.byref(nd), sig, ctypes.byref(th), ctypes.byref(gp), ctypes.byref(st),
+                                ctypes.byref(ni), ctypes.byref(ms)) == 0
+        assert nd.value == 2 and th.value == 64 and gp.value == 0 and st.value == 0 and ms.value == 0.0
+        seen.append((sig[0], ni.value))
+    assert sorted(seen) == [(2.0, 2), (3.0, 1), (4.0, 1)]
+    assert L.itc_plan_class(hp, 3, None, None, None, None, None, None, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_plan_class(hp, 0, None, None, None, None, None, None, None) == 0
+    dev = 0x100000
+    assert L.itc_plan_configure(hp, dev, 0, 64, 0, 1, None) == itc.ITC_ERR_UNSUPPORTED
+    assert L.itc_plan_configure(hp, dev, 0, 32, 0, 0, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_plan_configure(hp, dev, 5, 64, 0, 0, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_plan_configure(hp, dev, 0, 64, -1, 0, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_plan_configure(hp, dev, 0, 64, 0, 2, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_autotune(hp, dev, 0x4000, ws, 0, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_autotune(hp, dev, 0x4000, ws - 1, 3, None) == itc.ITC_ERR_WORKSPACE

@@ -135,3 +135,23 @@ def test_tma_tiles_equal_plain_tiles_bit_for_bit(sigma, dtype, absolute):
     ref = oracle.fields2d(h.astype(np.float64), sigma, 3.0, absolute)
     assert_fields_close([Fa[i, 0, :, :203].cpu().numpy().astype(np.float64) for i in range(3)], ref,
                         radii(sigma), absolute, "tma")
+
+
+def test_bounded_tile_wait_reports_instead_of_hanging():
+    """The TMA tile wait is bounded: with the test hook one CTA waits for a copy phase that never
+    completes, gives up after about a second, and the call reports S_XX = NaN; the GPU context
+    stays usable and the next call is correct."""
+    import torch
+    h = (np.random.default_rng(0).random((256, 256)) < 0.3).astype(np.uint8)
+    buf, (t,) = itc.pack_images([h], "cuda", align=16)   # aligned rows: the TMA path
+    img = itc.make_image(t)
+    p = itc.make_params(2.0, 3.0, flags=itc.ITC_TEST_STALL_WAIT)
+    out = torch.empty(itc.lib().itc_fields_bytes(__import__("ctypes").byref(img)) // 4, device="cuda")
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    sxx = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rc = itc.itc_fields(img, p, out.data_ptr(), sxx.data_ptr(), ws.data_ptr(), ws.numel(),
+                        torch.cuda.current_stream().cuda_stream)
+    assert rc == itc.ITC_OK
+    torch.cuda.synchronize()
+    assert np.isnan(sxx.item())
+    check(h, 2.0, what="after a stalled call")

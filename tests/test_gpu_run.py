@@ -235,6 +235,67 @@ def test_pipelined_and_range_runs_equal_plain_run():
         assert np.array_equal(W, outs[0][0]) and st == outs[0][1]
 
 
+def _fields_and_run(plan, W0s, iters_plan):
+    import torch
+    itc.run_fields(plan)
+    torch.cuda.synchronize()
+    F = [plan.fields_of(b).cpu().numpy().copy() for b in range(plan.B)]
+    W = plan.pack_W(W0s)
+    st = itc.new_stats(plan.B, W.device)
+    itc.run(plan, W, st)
+    torch.cuda.synchronize()
+    return F, W.cpu().numpy().copy(), itc.stats_to_numpy(st)
+
+
+def _c3_plan(n, iters):
+    images, Ms, sig = synth.c3_batch(n)
+    W0s = [synth.init_codebook(synth.rng_for(3, 40_000 + i), im.astype(np.float32), int(m))
+           for i, (im, m) in enumerate(zip(images, Ms))]
+    params = [itc.make_params(float(s), 3.0, iters) for s in sig]
+    buf, views = itc.pack_images(images, "cuda")   # rows padded to 16 bytes: tensor tiles possible
+    plan = itc.Plan(views, Ms, params)
+    plan._keep_buf = buf
+    return plan, W0s
+
+
+def test_every_fields_configuration_gives_the_same_result():
+    """Tile height, persistent grid and staging change only the schedule: the fields are
+    bit-for-bit identical, so are the codebooks after a run.  S_XX is a sum of per-tile
+    partials, each built from FP32 per-thread sums of at most 16 non-negative products h*A, so a
+    different tiling moves it by at most 16 FP32 roundings, relative (< 1e-6); D_cs moves by the
+    same amount through log S_XX."""
+    plan, W0s = _c3_plan(48, 12)
+    base = _fields_and_run(plan, W0s, 12)
+    configs = [(64, 0, "plain"), (64, 1, "tma"), (32, 0, "tma"), (32, 1, "tma"), (32, 2, "tma"), (64, 0, "tma")]
+    classes = plan.classes()
+    assert sum(info["staging"] == "tma" for info in classes) >= 2
+    for c, info in enumerate(classes):
+        if info["staging"] != "tma":
+            continue
+        for th, g, stg in configs:
+            plan.configure(c, th, g, stg)
+            got = plan.classes()[c]
+            assert (got["tile_h"], got["ctas_per_sm"], got["staging"]) == (th, g, stg)
+            F, W, st = _fields_and_run(plan, W0s, 12)
+            assert all(np.array_equal(a, b) for a, b in zip(F, base[0])), (c, th, g, stg)
+            assert np.array_equal(W, base[1]), (c, th, g, stg)
+            assert np.allclose(st["sxx"], base[2]["sxx"], rtol=1e-6, atol=0)
+            assert np.allclose(st["dcs"], base[2]["dcs"], rtol=0, atol=1e-6)
+
+
+def test_autotuned_plan_keeps_results():
+    plan, W0s = _c3_plan(64, 10)
+    base = _fields_and_run(plan, W0s, 10)
+    info = plan.autotune(reps=2)
+    assert len(info) >= 2
+    for c in info:
+        assert c["tuned_ms"] > 0 and c["tile_h"] in (32, 64) and c["staging"] in ("tma", "plain")
+    F, W, st = _fields_and_run(plan, W0s, 10)
+    assert all(np.array_equal(a, b) for a, b in zip(F, base[0]))
+    assert np.array_equal(W, base[1])
+    assert np.allclose(st["dcs"], base[2]["dcs"], rtol=0, atol=1e-6)
+
+
 @pytest.mark.parametrize("M", [700, 2048])
 def test_large_codebooks_against_oracle(M):
     """Many codebook vectors per image (up to the build's limit of 2048): each thread owns

@@ -54,6 +54,7 @@ def lib() -> ctypes.CDLL:
         L.orc_radius.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_sxx.restype = ctypes.c_double
         L.orc_dcs.restype = ctypes.c_double
+        L.orc_dcs_const.restype = ctypes.c_double
         L.orc_lattice_run.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -153,11 +154,32 @@ def _field_ptrs(F):
     return F, arr
 
 
-def lattice_step(A, F, sigma, W, step_scale=1.0, snap=True, absolute=False):
+def _vec(x, ndim):
+    return None if x is None else _f64(np.broadcast_to(np.asarray(x, float), (ndim,)))
+
+
+def widths(xi, omega):
+    """Kernel widths of Sec. 2.1 from the Parzen widths xi (data) and omega (codebook), per axis:
+    tau = sqrt(xi^2 + omega^2) (V(X;W)), rho = sqrt(2) omega (V(W)), s = sqrt(2) xi (V(X)), and
+    the step factor omega^2 / tau^2 at which Eq. (accupdate), evaluated exactly, moves w_k."""
+    xi, omega = np.asarray(xi, float), np.asarray(omega, float)
+    tau = np.sqrt(xi ** 2 + omega ** 2)
+    return tau, np.sqrt(2.0) * omega, np.sqrt(2.0) * xi, omega ** 2 / tau ** 2
+
+
+def dcs_const(sigma, rho=None, s=None, ndim=2):
+    """Normalisers of Eq. (1) left over when tau, rho, s differ: 1/2 sum log(tau^4/(rho^2 s^2))."""
+    sig = _vec(sigma, ndim)
+    return float(lib().orc_dcs_const(ndim, _d(sig), _d(_vec(rho, ndim)) if rho is not None else None,
+                                     _d(_vec(s, ndim)) if s is not None else None))
+
+
+def lattice_step(A, F, sigma, W, step_scale=1.0, snap=True, absolute=False, rho=None):
     """One lattice ITC iteration from oracle fields (Algorithm 1 steps 4-10).
 
-    ``A``/``F`` are 2-D (H x W) or 3-D (G x H x W) arrays; ``W`` is M x ndim.  Returns
-    ``(W_new, W_raw, stats)`` with stats = dict(c, sxw, sww, empty, moved).
+    ``A``/``F`` are 2-D (H x W) or 3-D (G x H x W) arrays; ``W`` is M x ndim; ``rho`` is the
+    width of the codebook pair sums (None = sigma).  Returns ``(W_new, W_raw, stats)`` with
+    stats = dict(c, sxw, sww, empty, moved).
     """
     A = _f64(A)
     ndim = len(F)
@@ -167,13 +189,16 @@ def lattice_step(A, F, sigma, W, step_scale=1.0, snap=True, absolute=False):
     W = _f64(W).reshape(-1, ndim)
     M = W.shape[0]
     Wo, Wr, st = np.zeros_like(W), np.zeros_like(W), np.zeros(5)
-    lib().orc_lattice_step(ndim, _i(shape), _d(A), Fp, int(absolute), _d(sig), M, _d(W),
-                           ctypes.c_double(step_scale), int(snap), _d(Wo), _d(Wr), _d(st))
+    rh = _vec(rho, ndim)
+    lib().orc_lattice_step(ndim, _i(shape), _d(A), Fp, int(absolute), _d(sig), _d(rh) if rh is not None else None,
+                           M, _d(W), ctypes.c_double(step_scale), int(snap), _d(Wo), _d(Wr), _d(st))
     return Wo, Wr, dict(c=st[0], sxw=st[1], sww=st[2], empty=int(st[3]), moved=int(st[4]))
 
 
-def lattice_run(A, F, sxx_value, sigma, W, iters, step_scale=1.0, snap=True, absolute=False, stop_on_fixed=False):
-    """Algorithm 1 loop; returns (W_final, dcs[0..t], tie[0..t-1], t)."""
+def lattice_run(A, F, sxx_value, sigma, W, iters, step_scale=1.0, snap=True, absolute=False, stop_on_fixed=False,
+                rho=None, dcs_const=0.0):
+    """Algorithm 1 loop; returns (W_final, dcs[0..t], tie[0..t-1], t).  ``sxx_value`` is S_XX at
+    the width of V(X); ``dcs_const`` the normalisers of Eq. (1) (see :func:`dcs_const`)."""
     A = _f64(A)
     ndim = len(F)
     shape = _i32([A.shape[0], A.shape[1]] if ndim == 2 else [A.shape[1], A.shape[2], A.shape[0]])
@@ -183,29 +208,35 @@ def lattice_run(A, F, sxx_value, sigma, W, iters, step_scale=1.0, snap=True, abs
     M = W.shape[0]
     dcs = np.zeros(iters + 1)
     tie = np.zeros(max(iters, 1))
+    rh = _vec(rho, ndim)
     t = lib().orc_lattice_run(ndim, _i(shape), _d(A), Fp, int(absolute), ctypes.c_double(sxx_value),
-                              _d(sig), M, _d(W), ctypes.c_double(step_scale), int(snap), int(iters),
-                              int(stop_on_fixed), _d(dcs), _d(tie))
+                              _d(sig), _d(rh) if rh is not None else None, ctypes.c_double(dcs_const), M, _d(W),
+                              ctypes.c_double(step_scale), int(snap), int(iters), int(stop_on_fixed), _d(dcs),
+                              _d(tie))
     return W, dcs[: t + 1], tie[:t], t
 
 
-def original_step(X, sigma, W, hx=None):
-    """Eq. (origupdate): one continuous, untruncated O(N M) update over the point list X (N x d)."""
+def original_step(X, sigma, W, hx=None, rho=None, kappa_from_widths=True):
+    """Eq. (origupdate): one continuous, untruncated O(N M) update over the point list X (N x d);
+    data sums at width sigma (tau), pair sums at rho (None = sigma).  ``kappa_from_widths``
+    gives the pair terms the factor tau^2/rho^2 that differentiating Eq. (1) yields; False is the
+    equation as printed (the two agree when tau = rho)."""
     X = _f64(X)
     N, ndim = X.shape
     W = _f64(W).reshape(-1, ndim)
     Wo = np.zeros_like(W)
     hk = _f64(hx) if hx is not None else None
     sig = _f64(np.broadcast_to(np.asarray(sigma, float), (ndim,)))
+    rh = _vec(rho, ndim)
     lib().orc_original_step(ndim, N, _d(X), _d(hk) if hk is not None else None, _d(sig),
-                            W.shape[0], _d(W), _d(Wo))
+                            _d(rh) if rh is not None else None, int(kappa_from_widths), W.shape[0], _d(W), _d(Wo))
     return Wo
 
 
-def original_run(X, sigma, W, iters, hx=None):
+def original_run(X, sigma, W, iters, hx=None, rho=None, kappa_from_widths=True):
     W = _f64(W)
     for _ in range(iters):
-        W = original_step(X, sigma, W, hx)
+        W = original_step(X, sigma, W, hx, rho, kappa_from_widths)
     return W
 
 
@@ -235,41 +266,58 @@ def _pts(shape, X, hx, sigma, trunc, R):
     return X, _f64(hx), sig, RR, _i32(shape)
 
 
-def dcs_sums(shape, X, hx, sigma, W, trunc=3.0, R=None):
-    """(S_XW, S_WW, S_XX) from their definitions; shape = lattice sizes per axis (u, v[, g])."""
+def _widths_args(ndim, rho, s, trunc, Rs):
+    """(rho, s, Rs) ctypes arguments; None stays NULL (= sigma, sigma, R)."""
+    rh, ss = _vec(rho, ndim), _vec(s, ndim)
+    RRs = None
+    if ss is not None:
+        RRs = _i32(Rs if Rs is not None else _radii(ss, trunc))
+    return ((rh, ss, RRs), (_d(rh) if rh is not None else None, _d(ss) if ss is not None else None,
+                            _i(RRs) if RRs is not None else None))
+
+
+def dcs_sums(shape, X, hx, sigma, W, trunc=3.0, R=None, rho=None, s=None, Rs=None):
+    """(S_XW, S_WW, S_XX) from their definitions; shape = lattice sizes per axis (u, v[, g]).
+    S_XW at width sigma (tau) over the box R, S_WW at rho, S_XX at s over the box Rs."""
     X, hx, sig, RR, shp = _pts(shape, X, hx, sigma, trunc, R)
+    keep, wa = _widths_args(X.shape[1], rho, s, trunc, Rs)
     W = _f64(W).reshape(-1, X.shape[1])
-    s = np.zeros(3)
-    lib().orc_dcs_sums(X.shape[1], _i(shp), X.shape[0], _d(X), _d(hx), _d(sig), _i(RR), W.shape[0], _d(W), _d(s))
-    return tuple(s)
+    out = np.zeros(3)
+    lib().orc_dcs_sums(X.shape[1], _i(shp), X.shape[0], _d(X), _d(hx), _d(sig), _i(RR), *wa, W.shape[0], _d(W),
+                       _d(out))
+    return tuple(out)
 
 
-def dcs(shape, X, hx, sigma, W, trunc=3.0, R=None) -> float:
-    """Cauchy-Schwarz divergence, Eq. (1): log S_WW + log S_XX - 2 log S_XW."""
+def dcs(shape, X, hx, sigma, W, trunc=3.0, R=None, rho=None, s=None, Rs=None) -> float:
+    """Cauchy-Schwarz divergence, Eq. (1): log S_WW + log S_XX - 2 log S_XW + K."""
     X, hx, sig, RR, shp = _pts(shape, X, hx, sigma, trunc, R)
+    keep, wa = _widths_args(X.shape[1], rho, s, trunc, Rs)
     W = _f64(W).reshape(-1, X.shape[1])
-    return lib().orc_dcs(X.shape[1], _i(shp), X.shape[0], _d(X), _d(hx), _d(sig), _i(RR), W.shape[0], _d(W))
+    return lib().orc_dcs(X.shape[1], _i(shp), X.shape[0], _d(X), _d(hx), _d(sig), _i(RR), *wa, W.shape[0], _d(W))
 
 
-def dcs_grad(shape, X, hx, sigma, W, trunc=3.0, R=None, with_h=True):
+def dcs_grad(shape, X, hx, sigma, W, trunc=3.0, R=None, with_h=True, rho=None, s=None, Rs=None):
     """(dD/dW [M x d], dD/dh [N] or None) from the analytic formulas."""
     X, hx, sig, RR, shp = _pts(shape, X, hx, sigma, trunc, R)
+    keep, wa = _widths_args(X.shape[1], rho, s, trunc, Rs)
     W = _f64(W).reshape(-1, X.shape[1])
     gW = np.zeros_like(W)
     gh = np.zeros(X.shape[0]) if with_h else None
-    lib().orc_dcs_grad(X.shape[1], _i(shp), X.shape[0], _d(X), _d(hx), _d(sig), _i(RR), W.shape[0], _d(W),
+    lib().orc_dcs_grad(X.shape[1], _i(shp), X.shape[0], _d(X), _d(hx), _d(sig), _i(RR), *wa, W.shape[0], _d(W),
                        _d(gW), _d(gh) if gh is not None else None)
     return gW, gh
 
 
-def dcs_grad2d_dense(h, sigma, W, trunc=3.0, R=None, A=None, with_h=True):
-    """Dense-image gradient of Eq. (1): (gW [M x 2], gh [H x W] or None, (S_XW, S_WW, S_XX))."""
+def dcs_grad2d_dense(h, sigma, W, trunc=3.0, R=None, A=None, with_h=True, rho=None, s=None):
+    """Dense-image gradient of Eq. (1): (gW [M x 2], gh [H x W] or None, (S_XW, S_WW, S_XX)).
+    ``A`` is the field of h at the width s of V(X) (computed here when None)."""
     h = _f64(h)
     H, Wd = h.shape
     su, sv = (float(sigma), float(sigma)) if np.isscalar(sigma) else map(float, sigma)
+    pu, pv = (su, sv) if rho is None else ((float(rho), float(rho)) if np.isscalar(rho) else map(float, rho))
     Ru, Rv = R if R is not None else _radii((su, sv), trunc)
     if A is None:
-        A = fields2d(h, (su, sv), R=(Ru, Rv))[0]
+        A = fields2d(h, (su, sv) if s is None else s, trunc)[0]
     A = _f64(A)
     s_xx = sxx(h, A)
     W = _f64(W).reshape(-1, 2)
@@ -277,13 +325,13 @@ def dcs_grad2d_dense(h, sigma, W, trunc=3.0, R=None, A=None, with_h=True):
     gh = np.zeros((H, Wd)) if with_h else None
     sums = np.zeros(3)
     lib().orc_dcs_grad2d_dense(_d(h), _d(A), H, Wd, ctypes.c_double(su), ctypes.c_double(sv), Ru, Rv,
-                               ctypes.c_double(s_xx), W.shape[0], _d(W), _d(gW),
-                               _d(gh) if gh is not None else None, _d(sums))
+                               ctypes.c_double(pu), ctypes.c_double(pv), ctypes.c_double(s_xx), W.shape[0],
+                               _d(W), _d(gW), _d(gh) if gh is not None else None, _d(sums))
     return gW, gh, tuple(sums)
 
 
-def dcs2d_dense(h, sigma, W, trunc=3.0, R=None, A=None) -> float:
-    """Eq. (1) for a dense 2-D weight image, from oracle fields (S_XX = sum h A) and the direct
+def dcs2d_dense(h, sigma, W, trunc=3.0, R=None, A=None, rho=None, s=None) -> float:
+    """Eq. (1) for a dense 2-D weight image, from oracle fields (S_XX = sum h A_s) and the direct
     window and pair sums at the real codebook W (the same sums as :func:`dcs_sums`)."""
-    _, _, (sxw, sww, s_xx) = dcs_grad2d_dense(h, sigma, W, trunc, R, A, with_h=False)
-    return float(np.log(sww) + np.log(s_xx) - 2.0 * np.log(sxw))
+    _, _, (sxw, sww, s_xx) = dcs_grad2d_dense(h, sigma, W, trunc, R, A, with_h=False, rho=rho, s=s)
+    return float(np.log(sww) + np.log(s_xx) - 2.0 * np.log(sxw) + dcs_const(sigma, rho, s, 2))

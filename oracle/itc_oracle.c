@@ -14,14 +14,14 @@
  *   Sec. 1 case (ii));  codebook W = {w_1..w_M}.
  *   Kernel g(d) = prod_i exp(-d_i^2 / (2 sigma_i^2)), unnormalised.
  *
- * Reading of the kernel widths (the paper has xi, omega, tau, rho, Sec. 2.1): sigma is
- * tau = rho, i.e. xi = omega = sigma/sqrt(2).  Then the three overlap integrals V(X;W), V(W) and
- * V(X) of Eq. (1) all use the same Gaussian of width sigma, every normalising constant cancels
- * in D_cs, and
- *     D_cs = log S_WW + log S_XX - 2 log S_XW
- *     S_XW = sum_k sum_x h(x) g(x - w_k)      (V(X;W), Gaussian product theorem)
- *     S_WW = sum_j sum_k g(w_j - w_k)         (V(W))
- *     S_XX = sum_x sum_y h(x) h(y) g(x - y)   (V(X)).
+ * Kernel widths (the paper has xi, omega, tau, rho, Sec. 2.1).  By the Gaussian product theorem
+ * the three overlap integrals of Eq. (1) are Gaussian sums of three widths:
+ *     V(X;W) ~ S_XW = sum_k sum_x h(x) g_tau(x - w_k),      tau^2 = xi^2 + omega^2
+ *     V(W)   ~ S_WW = sum_j sum_k g_rho(w_j - w_k),         rho^2 = 2 omega^2
+ *     V(X)   ~ S_XX = sum_x sum_y h(x) h(y) g_s(x - y),     s^2   = 2 xi^2
+ * and D_cs = log S_WW + log S_XX - 2 log S_XW + K with K = 1/2 sum_i log(tau_i^4 / (rho_i^2 s_i^2))
+ * collecting the normalisers (K = 0 when xi = omega, the default reading: one width sigma =
+ * tau = rho = s).  Functions take sigma (= tau) and optional rho and s (NULL = sigma).
  * Truncation (Sec. 3.1, finite filter masks): data sums run over the box |x_i - r_i| <= R_i
  * around the lattice site r they are centred on, R_i = ceil(trunc * sigma_i); the codebook
  * interaction sums S_WW, s_k, E_k are not truncated.  Sites outside the lattice hold no data.
@@ -328,9 +328,14 @@ static size_t site_index(int ndim, const int *shape, const double *r)
 }
 
 void orc_lattice_step(int ndim, const int *shape, const double *A, const double *const *F,
-                      int absolute, const double *sigma, int M, const double *W_in,
+                      int absolute, const double *sigma, const double *rho, int M, const double *W_in,
                       double step_scale, int snap, double *W_out, double *W_raw, double *stats)
 {
+    if (!rho) rho = sigma;
+    /* the stationarity condition of Eq. (1) in w_k: D_k / tau^2 = c E_k / rho^2 per axis, so the
+       pair term carries kappa = tau^2 / rho^2 (1 when tau = rho) */
+    double kappa[3];
+    for (int i = 0; i < ndim; ++i) kappa[i] = (sigma[i] * sigma[i]) / (rho[i] * rho[i]);
     double *a = (double *)malloc(M * sizeof(double));
     double *D = (double *)malloc((size_t)M * ndim * sizeof(double));
     double *s = (double *)malloc(M * sizeof(double));
@@ -349,7 +354,7 @@ void orc_lattice_step(int ndim, const int *shape, const double *A, const double 
         for (int j = 0; j < M; ++j) {
             double gk = 1.0;
             for (int i = 0; i < ndim; ++i)
-                gk *= gauss1(W_in[j * ndim + i] - W_in[k * ndim + i], sigma[i]);
+                gk *= gauss1(W_in[j * ndim + i] - W_in[k * ndim + i], rho[i]);
             s[k] += gk;
             for (int i = 0; i < ndim; ++i)
                 E[k * ndim + i] += gk * (W_in[j * ndim + i] - W_in[k * ndim + i]);
@@ -364,7 +369,7 @@ void orc_lattice_step(int ndim, const int *shape, const double *A, const double 
         for (int i = 0; i < ndim; ++i) {
             double w = W_in[k * ndim + i], nw;
             if (a[k] > 0) {
-                double raw = w + step_scale * (D[k * ndim + i] - c * E[k * ndim + i]) / a[k];
+                double raw = w + step_scale * (D[k * ndim + i] - kappa[i] * c * E[k * ndim + i]) / a[k];
                 W_raw[k * ndim + i] = raw;
                 if (snap) nw = lattice_round(raw, shape[i]);
                 else nw = raw < 0 ? 0 : (raw > shape[i] - 1 ? shape[i] - 1 : raw);
@@ -395,8 +400,8 @@ void orc_lattice_step(int ndim, const int *shape, const double *A, const double 
  * returned W.  tie[t] = distance of the closest unrounded coordinate of iteration t to a
  * half-integer (snap mode).  Returns the number of iterations run. */
 int orc_lattice_run(int ndim, const int *shape, const double *A, const double *const *F,
-                    int absolute, double sxx, const double *sigma, int M, double *W,
-                    double step_scale, int snap, int iters, int stop_on_fixed,
+                    int absolute, double sxx, const double *sigma, const double *rho, double dcs_const,
+                    int M, double *W, double step_scale, int snap, int iters, int stop_on_fixed,
                     double *dcs, double *tie)
 {
     double *Wn = (double *)malloc((size_t)M * ndim * sizeof(double));
@@ -404,8 +409,8 @@ int orc_lattice_run(int ndim, const int *shape, const double *A, const double *c
     double st[5];
     int t = 0;
     for (; t < iters; ++t) {
-        orc_lattice_step(ndim, shape, A, F, absolute, sigma, M, W, step_scale, snap, Wn, raw, st);
-        if (dcs) dcs[t] = log(st[2]) + log(sxx) - 2.0 * log(st[1]);
+        orc_lattice_step(ndim, shape, A, F, absolute, sigma, rho, M, W, step_scale, snap, Wn, raw, st);
+        if (dcs) dcs[t] = log(st[2]) + log(sxx) - 2.0 * log(st[1]) + dcs_const;
         if (tie) {
             double m = 1e300;
             for (int i = 0; i < M * ndim; ++i) {
@@ -419,8 +424,8 @@ int orc_lattice_run(int ndim, const int *shape, const double *A, const double *c
         if (stop_on_fixed && st[4] == 0) { ++t; break; }
     }
     if (dcs) {
-        orc_lattice_step(ndim, shape, A, F, absolute, sigma, M, W, step_scale, snap, Wn, raw, st);
-        dcs[t] = log(st[2]) + log(sxx) - 2.0 * log(st[1]);
+        orc_lattice_step(ndim, shape, A, F, absolute, sigma, rho, M, W, step_scale, snap, Wn, raw, st);
+        dcs[t] = log(st[2]) + log(sxx) - 2.0 * log(st[1]) + dcs_const;
     }
     free(Wn);
     free(raw);
@@ -433,12 +438,18 @@ int orc_lattice_run(int ndim, const int *shape, const double *A, const double *c
  * (NULL = 1), evaluated as the three terms of Eq. (origupdate):
  *   w_k' = sum_i g(x_i - w_k) x_i / den_k - c sum_j g(w_j - w_k) w_j / den_k
  *          + c sum_j g(w_j - w_k) w_k / den_k,   den_k = sum_i g(x_i - w_k)
- * with c = (N/M) V(X;W)/V(W) = S_XW / S_WW once the Gaussian normalisers cancel (sigma = tau =
- * rho).  Cost O(N M) exponentials per iteration (Sec. 2.2).
+ * with the data sums over g_tau (sigma) and the codebook sums over g_rho (rho; NULL = sigma).
+ * Written out with normalised Gaussians, c = (N/M) V(X;W)/V(W) times the ratio of the
+ * normalisers of the two sums is S_XW / S_WW.  As printed, Eq. (origupdate) has no further
+ * factor (kappa_from_widths = 0); differentiating Eq. (1) gives the pair terms an extra
+ * tau^2/rho^2 per axis (kappa_from_widths = 1).  The two agree when tau = rho.
+ * Cost O(N M) exponentials per iteration (Sec. 2.2).
  */
 void orc_original_step(int ndim, int N, const double *X, const double *hx, const double *sigma,
-                       int M, const double *W_in, double *W_out)
+                       const double *rho, int kappa_from_widths, int M, const double *W_in,
+                       double *W_out)
 {
+    if (!rho) rho = sigma;
     double *den = (double *)malloc(M * sizeof(double));
     double *num = (double *)malloc((size_t)M * ndim * sizeof(double));
     double *s = (double *)malloc(M * sizeof(double));
@@ -457,7 +468,7 @@ void orc_original_step(int ndim, int N, const double *X, const double *hx, const
         for (int i = 0; i < ndim; ++i) mw[k * ndim + i] = 0;
         for (int j = 0; j < M; ++j) {
             double gk = 1.0;
-            for (int i = 0; i < ndim; ++i) gk *= gauss1(W_in[j * ndim + i] - W_in[k * ndim + i], sigma[i]);
+            for (int i = 0; i < ndim; ++i) gk *= gauss1(W_in[j * ndim + i] - W_in[k * ndim + i], rho[i]);
             s[k] += gk;
             for (int i = 0; i < ndim; ++i) mw[k * ndim + i] += gk * W_in[j * ndim + i];
         }
@@ -466,9 +477,11 @@ void orc_original_step(int ndim, int N, const double *X, const double *hx, const
     }
     double c = sxw / sww;
     for (int k = 0; k < M; ++k)
-        for (int i = 0; i < ndim; ++i)
-            W_out[k * ndim + i] = num[k * ndim + i] / den[k] - c * mw[k * ndim + i] / den[k] +
-                                  c * s[k] / den[k] * W_in[k * ndim + i];
+        for (int i = 0; i < ndim; ++i) {
+            const double ck = kappa_from_widths ? c * (sigma[i] * sigma[i]) / (rho[i] * rho[i]) : c;
+            W_out[k * ndim + i] = num[k * ndim + i] / den[k] - ck * mw[k * ndim + i] / den[k] +
+                                  ck * s[k] / den[k] * W_in[k * ndim + i];
+        }
     free(den);
     free(num);
     free(s);
@@ -490,10 +503,16 @@ static int in_box(int ndim, const double *x, const double *c, const int *R)
     return 1;
 }
 
-/* sums[0..2] = S_XW, S_WW, S_XX, evaluated directly from their definitions. */
+/* sums[0..2] = S_XW, S_WW, S_XX, evaluated directly from their definitions: S_XW with g_sigma
+ * over the box R, S_WW with g_rho (untruncated), S_XX with g_s over the box Rs (rho, s, Rs may
+ * be NULL: sigma, sigma, R). */
 void orc_dcs_sums(int ndim, const int *shape, int N, const double *X, const double *hx,
-                  const double *sigma, const int *R, int M, const double *W, double *sums)
+                  const double *sigma, const int *R, const double *rho, const double *ss,
+                  const int *Rs, int M, const double *W, double *sums)
 {
+    if (!rho) rho = sigma;
+    if (!ss) ss = sigma;
+    if (!Rs) Rs = R;
     double sxw = 0, sww = 0, sxx = 0;
     for (int k = 0; k < M; ++k) {
         double r[3];
@@ -506,16 +525,16 @@ void orc_dcs_sums(int ndim, const int *shape, int N, const double *X, const doub
         }
         for (int j = 0; j < M; ++j) {
             double gk = 1.0;
-            for (int i = 0; i < ndim; ++i) gk *= gauss1(W[j * ndim + i] - W[k * ndim + i], sigma[i]);
+            for (int i = 0; i < ndim; ++i) gk *= gauss1(W[j * ndim + i] - W[k * ndim + i], rho[i]);
             sww += gk;
         }
     }
     for (int p = 0; p < N; ++p)
         for (int q = 0; q < N; ++q) {
-            if (!in_box(ndim, X + (size_t)p * ndim, X + (size_t)q * ndim, R)) continue;
+            if (!in_box(ndim, X + (size_t)p * ndim, X + (size_t)q * ndim, Rs)) continue;
             double gk = hx[p] * hx[q];
             for (int i = 0; i < ndim; ++i)
-                gk *= gauss1(X[(size_t)p * ndim + i] - X[(size_t)q * ndim + i], sigma[i]);
+                gk *= gauss1(X[(size_t)p * ndim + i] - X[(size_t)q * ndim + i], ss[i]);
             sxx += gk;
         }
     sums[0] = sxw;
@@ -523,29 +542,46 @@ void orc_dcs_sums(int ndim, const int *shape, int N, const double *X, const doub
     sums[2] = sxx;
 }
 
-/* D_cs = 2H(X;W) - H(W) - H(X) = log S_WW + log S_XX - 2 log S_XW, Eq. (1). */
+/* The normalisers of Eq. (1): K = log(n_rho n_s / n_tau^2) for the normalised Gaussians
+ * n_t = prod_i (2 pi t_i^2)^(-1/2), i.e. 1/2 sum_i log(tau_i^4 / (rho_i^2 s_i^2)). */
+double orc_dcs_const(int ndim, const double *sigma, const double *rho, const double *ss)
+{
+    if (!rho) rho = sigma;
+    if (!ss) ss = sigma;
+    double k = 0;
+    for (int i = 0; i < ndim; ++i)
+        k += 0.5 * log(pow(sigma[i], 4) / (rho[i] * rho[i] * ss[i] * ss[i]));
+    return k;
+}
+
+/* D_cs = 2H(X;W) - H(W) - H(X) = log S_WW + log S_XX - 2 log S_XW + K, Eq. (1). */
 double orc_dcs(int ndim, const int *shape, int N, const double *X, const double *hx,
-               const double *sigma, const int *R, int M, const double *W)
+               const double *sigma, const int *R, const double *rho, const double *ss, const int *Rs,
+               int M, const double *W)
 {
     double s[3];
-    orc_dcs_sums(ndim, shape, N, X, hx, sigma, R, M, W, s);
-    return log(s[1]) + log(s[2]) - 2.0 * log(s[0]);
+    orc_dcs_sums(ndim, shape, N, X, hx, sigma, R, rho, ss, Rs, M, W, s);
+    return log(s[1]) + log(s[2]) - 2.0 * log(s[0]) + orc_dcs_const(ndim, sigma, rho, ss);
 }
 
 /*
  * Analytic gradient of orc_dcs (Eq. (1) differentiated; dq/dw_k of Sec. 3.1 with the sign and
  * factor of d/dw exp(-|x-w|^2/(2 s^2)) = exp(.) (x - w)/s^2):
- *   dD/dw_{k,i} = (2/sigma_i^2) (E_{k,i}/S_WW - D_{k,i}/S_XW),
- *        D_k = sum_{x in box(r_k)} h g(x - w_k)(x - w_k),  E_k = sum_j g(w_j - w_k)(w_j - w_k)
- *   dD/dh(x)    = 2 A(x)/S_XX - (2/S_XW) sum_k g(x - w_k) [x in box(r_k)],
- *        A(x) = sum_{y in box(x)} h(y) g(x - y).
- * gW is M x ndim; gh has one entry per point of X.
+ *   dD/dw_{k,i} = (2/rho_i^2) E_{k,i}/S_WW - (2/tau_i^2) D_{k,i}/S_XW,
+ *        D_k = sum_{x in box(r_k)} h g_tau(x - w_k)(x - w_k),  E_k = sum_j g_rho(w_j - w_k)(w_j - w_k)
+ *   dD/dh(x)    = 2 A_s(x)/S_XX - (2/S_XW) sum_k g_tau(x - w_k) [x in box(r_k)],
+ *        A_s(x) = sum_{y in box_s(x)} h(y) g_s(x - y).
+ * (tau = sigma; rho, s, Rs NULL = sigma, sigma, R.)  gW is M x ndim; gh has one entry per point.
  */
 void orc_dcs_grad(int ndim, const int *shape, int N, const double *X, const double *hx,
-                  const double *sigma, const int *R, int M, const double *W, double *gW, double *gh)
+                  const double *sigma, const int *R, const double *rho, const double *ss,
+                  const int *Rs, int M, const double *W, double *gW, double *gh)
 {
+    if (!rho) rho = sigma;
+    if (!ss) ss = sigma;
+    if (!Rs) Rs = R;
     double sums[3];
-    orc_dcs_sums(ndim, shape, N, X, hx, sigma, R, M, W, sums);
+    orc_dcs_sums(ndim, shape, N, X, hx, sigma, R, rho, ss, Rs, M, W, sums);
     double sxw = sums[0], sww = sums[1], sxx = sums[2];
     for (int k = 0; k < M; ++k) {
         double r[3], D[3] = {0, 0, 0}, E[3] = {0, 0, 0};
@@ -558,20 +594,20 @@ void orc_dcs_grad(int ndim, const int *shape, int N, const double *X, const doub
         }
         for (int j = 0; j < M; ++j) {
             double gk = 1.0;
-            for (int i = 0; i < ndim; ++i) gk *= gauss1(W[j * ndim + i] - W[k * ndim + i], sigma[i]);
+            for (int i = 0; i < ndim; ++i) gk *= gauss1(W[j * ndim + i] - W[k * ndim + i], rho[i]);
             for (int i = 0; i < ndim; ++i) E[i] += gk * (W[j * ndim + i] - W[k * ndim + i]);
         }
         for (int i = 0; i < ndim; ++i)
-            gW[k * ndim + i] = 2.0 / (sigma[i] * sigma[i]) * (E[i] / sww - D[i] / sxw);
+            gW[k * ndim + i] = 2.0 / (rho[i] * rho[i]) * E[i] / sww - 2.0 / (sigma[i] * sigma[i]) * D[i] / sxw;
     }
     if (!gh) return;
     for (int p = 0; p < N; ++p) {
         const double *x = X + (size_t)p * ndim;
         double a = 0, st = 0;
         for (int q = 0; q < N; ++q) {
-            if (!in_box(ndim, x, X + (size_t)q * ndim, R)) continue;
+            if (!in_box(ndim, x, X + (size_t)q * ndim, Rs)) continue;
             double gk = hx[q];
-            for (int i = 0; i < ndim; ++i) gk *= gauss1(x[i] - X[(size_t)q * ndim + i], sigma[i]);
+            for (int i = 0; i < ndim; ++i) gk *= gauss1(x[i] - X[(size_t)q * ndim + i], ss[i]);
             a += gk;
         }
         for (int k = 0; k < M; ++k) {
@@ -593,9 +629,11 @@ void orc_dcs_grad(int ndim, const int *shape, int N, const double *X, const doub
  * window sums at w_k are taken directly from h.
  */
 void orc_dcs_grad2d_dense(const double *h, const double *A, int H, int W, double su, double sv,
-                          int Ru, int Rv, double sxx, int M, const double *Wc, double *gW,
-                          double *gh, double *sums_out)
+                          int Ru, int Rv, double pu, double pv, double sxx, int M, const double *Wc,
+                          double *gW, double *gh, double *sums_out)
 {
+    /* (su, sv) = tau, (pu, pv) = rho of the pair sums; A is the field of h at the width of
+       S_XX, so that sxx = sum h A */
     double sxw = 0, sww = 0;
     double *D = (double *)malloc((size_t)M * 2 * sizeof(double));
     double *E = (double *)malloc((size_t)M * 2 * sizeof(double));
@@ -618,7 +656,7 @@ void orc_dcs_grad2d_dense(const double *h, const double *A, int H, int W, double
         D[2 * k + 1] = dv;
         double eu = 0, ev = 0;
         for (int j = 0; j < M; ++j) {
-            double gk = gauss1(Wc[2 * j] - wu, su) * gauss1(Wc[2 * j + 1] - wv, sv);
+            double gk = gauss1(Wc[2 * j] - wu, pu) * gauss1(Wc[2 * j + 1] - wv, pv);
             sww += gk;
             eu += gk * (Wc[2 * j] - wu);
             ev += gk * (Wc[2 * j + 1] - wv);
@@ -627,8 +665,8 @@ void orc_dcs_grad2d_dense(const double *h, const double *A, int H, int W, double
         E[2 * k + 1] = ev;
     }
     for (int k = 0; k < M; ++k) {
-        gW[2 * k] = 2.0 / (su * su) * (E[2 * k] / sww - D[2 * k] / sxw);
-        gW[2 * k + 1] = 2.0 / (sv * sv) * (E[2 * k + 1] / sww - D[2 * k + 1] / sxw);
+        gW[2 * k] = 2.0 / (pu * pu) * E[2 * k] / sww - 2.0 / (su * su) * D[2 * k] / sxw;
+        gW[2 * k + 1] = 2.0 / (pv * pv) * E[2 * k + 1] / sww - 2.0 / (sv * sv) * D[2 * k + 1] / sxw;
     }
     if (gh) {
         for (int u = 0; u < H; ++u)

@@ -96,6 +96,27 @@ def make_workload(name, rank, n=None):
     raise ValueError(name)
 
 
+def algorithmic_field_fmas(images, params, ndims):
+    """FMAs the fields pass must do: five 1-D passes of 2R+1 taps per pixel in 2-D (T, T_v; A,
+    F_u, F_v); in 3-D the g pass is read off the gray value, then T, T_v, T_g along v and A, F_u,
+    F_v, F_g along u: seven passes per voxel of the lattice (R from the in-plane sigma)."""
+    import math
+    tot = 0
+    for im, p, nd in zip(images, params, ndims):
+        s = p["sigma"] if np.isscalar(p["sigma"]) else p["sigma"][0]
+        taps = 2 * math.ceil(3.0 * s) + 1
+        if nd == 2:
+            tot += 5 * taps * im.size
+        else:
+            tot += 7 * taps * im.size * 256
+    return tot
+
+
+# FP32 FMA lanes per SM per clock (4 SM sub-partitions x 32 lanes); the ALU roofline uses it with
+# the SM clock sampled during the timed region.
+FMA_LANES_PER_SM = 128
+
+
 def algorithmic_field_bytes(images, ndims, Gs):
     """Bytes the fields pass must move: read the input once, write its fields once.
     2-D: input bytes + 3 FP32 planes per pixel; 3-D: input bytes + 4 FP32 planes per voxel."""
@@ -186,6 +207,22 @@ def cpu_baseline(name, seconds):
 
 
 # ----------------------------------------------------------------------------------- our arm
+def alu_roofline(images, pk, ndims, fields_ms, clocks, dev):
+    """The fields pass against the FP32 FMA rate of the SMs at the clock seen under load."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 0.0
+    fmas = algorithmic_field_fmas(images, pk, ndims)
+    peak = 2.0 * FMA_LANES_PER_SM * sms * mhz * 1e6 / 1e12
+    ach = 2.0 * fmas / (fields_ms / 1000.0) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak if peak else None,
+            "algorithmic_fma_per_launch": fmas,
+            "peak_source": f"{FMA_LANES_PER_SM} FP32 FMA lanes/SM x {sms} SMs x {mhz:.0f} MHz (median SM clock "
+                           "sampled in the timed region), 2 flop/FMA",
+            "note": "secondary: 5 x (2R+1) FMA per pixel (2-D), the ideal count without halo recompute; "
+                    "tiles and windows that hold no data are skipped, so this may exceed what executes"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1310_7114_gb300 import build, itc
@@ -393,6 +430,7 @@ def run_ours(args, rank, world, local_rank):
                                      "(profiles/fields_tma_kernel_c3_1024.md)",
                      "kernel": "fields pass (fields_tma_kernel, persistent, one launch per sigma class)",
                      "algorithmic_bytes_per_launch": fbytes, "peak_source": f"{peak_src} hbm_gbs"},
+        "roofline_alu": alu_roofline(images, pk, ndims, f_avg, clk.summary(), dev),
         "e2e": {"value": world * B / (e2e_ms / 1000.0), "unit": "images/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                 "path": "itc_run_pipelined + itc_backward through the C ABI; inputs from pinned host memory; "

@@ -88,12 +88,22 @@ typedef struct {
 
 /* Method parameters (host struct, passed by pointer, read during the call). */
 typedef struct {
-    float sigma[3];      /* kernel width per axis (u, v, g), lattice units, > 0 */
+    float sigma[3];      /* kernel width per axis (u, v, g), lattice units, > 0: the width tau of
+                            the data-codebook overlap V(X;W) (tau^2 = xi^2 + omega^2, Sec. 2.1);
+                            the fields are convolutions with it */
     float trunc;         /* mask half width in sigmas: R_i = ceil(trunc * sigma_i); paper: small
                             masks (Sec. 3.1); 3 is the usual choice */
     int iters;           /* fixed-point iterations (Algorithm 1 loop), >= 0 */
-    float step_scale;    /* 1: Eq. (origupdate); 0.5: Eq. (accupdate) evaluated exactly */
+    float step_scale;    /* 1: the fixed-point form of Eq. (origupdate); Eq. (accupdate)
+                            evaluated exactly moves by omega^2 / tau^2 of that step (0.5 when
+                            xi = omega) */
     int flags;           /* ITC_CONTINUOUS | ITC_FIELDS_ABSOLUTE | ITC_STOP_ON_FIXED */
+    float sigma_pair[3]; /* width rho of the codebook overlap V(W) (rho^2 = 2 omega^2); 0 = sigma.
+                            The pair terms of the update carry tau^2 / rho^2 per axis, the factor
+                            that differentiating Eq. (1) gives (Eq. (origupdate) as printed omits
+                            it; the two agree when tau = rho) */
+    float sigma_self[3]; /* width s of the data overlap V(X) (s^2 = 2 xi^2); 0 = sigma.  A width
+                            other than sigma costs one more fields pass (A only) per call */
 } itc_params;
 
 /* Per-image results, written by the device. */
@@ -106,6 +116,24 @@ typedef struct {
     int iters_done;      /* updates applied */
     int status;          /* ITC_OK, ITC_WARN_EMPTY_SUPPORT or ITC_ERR_NONFINITE */
 } itc_stats;
+
+/* --------------------------------------------------------------- parameters from xi, omega */
+
+/*
+ * itc_params_parzen -- method parameters from the Parzen widths of Eq. (dens1) (xi, data) and
+ * Eq. (dens2) (omega, codebook), per axis (ndim values each), by the Gaussian product theorem of
+ * Sec. 2.1: sigma = tau = sqrt(xi^2 + omega^2), sigma_pair = rho = sqrt(2) omega,
+ * sigma_self = sqrt(2) xi; step_scale = 1 (form 0, the fixed point of Eq. (origupdate)) or
+ * omega^2 / tau^2 (form 1, Eq. (accupdate) evaluated exactly; it must then be the same on every
+ * axis).  D_cs then includes the normalising constant 1/2 sum_i log(tau_i^4 / (rho_i^2 s_i^2)).
+ * When mass > 0 and M > 0 the widths are instead the paper's schedule of Sec. 4,
+ * omega = sqrt(mass / M) / 2 and xi = omega / 2 on every axis (mass = number of foreground
+ * pixels, or the total weight), and xi, omega are ignored (may be NULL).
+ * Errors: ITC_ERR_INVALID_ARG (non-positive width, ndim not 2 or 3, form 1 with axis-dependent
+ * omega^2 / tau^2).  Host-only.
+ */
+int itc_params_parzen(int ndim, const float* xi, const float* omega, double mass, int M,
+                      float trunc, int iters, int form, int flags, itc_params* out);
 
 /* ------------------------------------------------------------------------------ queries */
 
@@ -287,7 +315,8 @@ int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int
  * with the fixed tile height of the lattice dimension (64 in 2-D, 32 in 3-D; pass it);
  * grid_per_sm = persistent CTAs per SM (0 = as many as fit, else 1..64).  Updates the host
  * plan and copies it to plan_dev (synchronously on `stream`).  Errors: ITC_ERR_INVALID_ARG,
- * ITC_ERR_UNSUPPORTED (tensor tiles for a class whose images cannot use them), ITC_ERR_CUDA.
+ * ITC_ERR_UNSUPPORTED (tensor tiles for a class whose images cannot use them, or a
+ * self-overlap class), ITC_ERR_CUDA.
  */
 int itc_plan_configure(void* plan_host, void* plan_dev, int c, int tile_h, int grid_per_sm,
                        int staging, void* stream);
@@ -298,8 +327,10 @@ int itc_plan_classes(const void* plan_host);
 /*
  * itc_plan_class -- the configuration of class c (host-only): lattice dimension, sigma, output
  * rows per fields tile, persistent CTAs per SM (0 = as many as fit), staging (1 = tensor tiles,
- * 0 = plain loads), number of images and the tuned fields time in ms (0 if not tuned).  Any
- * output pointer may be NULL.  Errors: ITC_ERR_INVALID_ARG.
+ * 0 = plain loads, 2 = the extra pass that computes the field of h at the width of V(X) for
+ * images whose sigma_self differs from sigma: plain loads, A only), number of images and the
+ * tuned fields time in ms (0 if not tuned).  Any output pointer may be NULL.
+ * Errors: ITC_ERR_INVALID_ARG.
  */
 int itc_plan_class(const void* plan_host, int c, int* ndim, float* sigma, int* tile_h,
                    int* grid_per_sm, int* staging, int* images, float* tuned_ms);

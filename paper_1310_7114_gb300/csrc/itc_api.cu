@@ -39,6 +39,17 @@ int check_image(const itc_image* img) {
     return ITC_OK;
 }
 
+// Widths of the codebook overlap (rho) and the data overlap (s); 0 in the struct means sigma.
+float pair_width(const itc_params* p, int i) { return p->sigma_pair[i] > 0.f ? p->sigma_pair[i] : p->sigma[i]; }
+float self_width(const itc_params* p, int i) { return p->sigma_self[i] > 0.f ? p->sigma_self[i] : p->sigma[i]; }
+
+// True when V(X) needs its own fields pass (s != sigma on some axis).
+bool has_self_pass(const itc_params* p, int ndim) {
+    for (int i = 0; i < ndim; ++i)
+        if (self_width(p, i) != p->sigma[i]) return true;
+    return false;
+}
+
 int check_params(const itc_params* p, int ndim) {
     if (!p) return ITC_ERR_INVALID_ARG;
     if (!finite_pos(p->trunc)) return ITC_ERR_INVALID_ARG;
@@ -47,11 +58,20 @@ int check_params(const itc_params* p, int ndim) {
     if (p->iters < 0 || !isfinite(p->step_scale)) return ITC_ERR_INVALID_ARG;
     if (p->flags & ~(ITC_CONTINUOUS | ITC_FIELDS_ABSOLUTE | ITC_STOP_ON_FIXED | ITC_TEST_STALL_WAIT))
         return ITC_ERR_INVALID_ARG;
-    const double ru = ceil((double)p->trunc * p->sigma[0]), rv = ceil((double)p->trunc * p->sigma[1]);
-    if (ru > ITC_MAX_RADIUS_UV || rv > ITC_MAX_RADIUS_UV) return ITC_ERR_UNSUPPORTED;
-    if (ndim == 3 && ceil((double)p->trunc * p->sigma[2]) > ITC_MAX_RADIUS_G) return ITC_ERR_UNSUPPORTED;
-    // 3-D tiles stage four input channels; past R = 24 they exceed the 227 KB of shared memory
-    if (ndim == 3 && (ru > ITC_MAX_RADIUS_UV_3D || rv > ITC_MAX_RADIUS_UV_3D)) return ITC_ERR_UNSUPPORTED;
+    for (int i = 0; i < ndim; ++i) {
+        // 0 selects sigma; anything else must be a positive finite width
+        if (p->sigma_pair[i] != 0.f && !finite_pos(p->sigma_pair[i])) return ITC_ERR_INVALID_ARG;
+        if (p->sigma_self[i] != 0.f && !finite_pos(p->sigma_self[i])) return ITC_ERR_INVALID_ARG;
+    }
+    float ws[3];
+    for (int pass = 0; pass < 2; ++pass) {   // the fields widths, then the self-overlap widths
+        for (int i = 0; i < 3; ++i) ws[i] = pass == 0 ? p->sigma[i] : self_width(p, i);
+        const double ru = ceil((double)p->trunc * ws[0]), rv = ceil((double)p->trunc * ws[1]);
+        if (ru > ITC_MAX_RADIUS_UV || rv > ITC_MAX_RADIUS_UV) return ITC_ERR_UNSUPPORTED;
+        if (ndim == 3 && ceil((double)p->trunc * ws[2]) > ITC_MAX_RADIUS_G) return ITC_ERR_UNSUPPORTED;
+        // 3-D tiles stage four input channels; past R = 24 they exceed the 227 KB of shared memory
+        if (ndim == 3 && (ru > ITC_MAX_RADIUS_UV_3D || rv > ITC_MAX_RADIUS_UV_3D)) return ITC_ERR_UNSUPPORTED;
+    }
     return ITC_OK;
 }
 
@@ -64,10 +84,10 @@ void fill_taps(float sigma, int R, float* g, float* dg) {
     }
 }
 
-void make_taps(const itc_params* p, int ndim, Taps* t) {
+void make_taps(const itc_params* p, int ndim, Taps* t, bool self = false) {
     memset(t, 0, sizeof(*t));
     for (int i = 0; i < 3; ++i) {
-        const float s = (i < ndim) ? p->sigma[i] : 1.f;
+        const float s = (i < ndim) ? (self ? self_width(p, i) : p->sigma[i]) : 1.f;
         t->sigma[i] = s;
         t->inv2s2[i] = (i < ndim) ? (float)(1.0 / (2.0 * (double)s * s)) : 0.f;
         t->R[i] = (i < ndim) ? radius_of(s, p->trunc) : 0;
@@ -101,12 +121,25 @@ void fill_desc(const itc_image* img, const itc_params* p, int M, ImageDesc* d) {
     d->plane_floats = (long long)d->G * img->H * d->fpitch;
     d->bwd_tiles_u = (img->H + kBwdTileH - 1) / kBwdTileH;
     d->bwd_tiles_v = (img->W + kBwdTileW - 1) / kBwdTileW;
+    double k = 0;
     for (int i = 0; i < 3; ++i) {
-        const float s = i < img->ndim ? p->sigma[i] : 1.f;
+        const bool on = i < img->ndim;
+        const float s = on ? p->sigma[i] : 1.f;
+        const double r = on ? (double)pair_width(p, i) : 1.0, ss = on ? (double)self_width(p, i) : 1.0;
         d->sigma[i] = s;
-        d->inv2s2[i] = i < img->ndim ? (float)(1.0 / (2.0 * (double)s * s)) : 0.f;
-        d->R[i] = i < img->ndim ? radius_of(s, p->trunc) : 0;
+        d->inv2s2[i] = on ? (float)(1.0 / (2.0 * (double)s * s)) : 0.f;
+        d->R[i] = on ? radius_of(s, p->trunc) : 0;
+        d->rho[i] = (float)r;
+        d->pinv2s2[i] = on ? (float)(1.0 / (2.0 * r * r)) : 0.f;
+        d->kappa[i] = on ? (float)(((double)s * s) / (r * r)) : 0.f;
+        if (on) k += 0.5 * log(pow((double)s, 4) / (r * r * ss * ss));
     }
+    d->dcs_const = k;
+    d->self_tiles_u = d->tiles_u;
+    d->self_off = -1;
+    d->self_cls = -1;
+    d->sxx_off = 0;
+    d->sxx_tiles = (int)((long long)d->tiles_u * d->tiles_v * d->tiles_g);
 }
 
 long long tiles_of(const ImageDesc& d) { return (long long)d.tiles_u * d.tiles_v * d.tiles_g; }
@@ -118,7 +151,9 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? ITC_OK : ITC_ERR_CUDA
 size_t plan_layout(int B, size_t* desc_off, size_t* ints_off, size_t* tmap_off = nullptr) {
     const size_t h = align_up(sizeof(PlanHeader), 256);
     const size_t d = align_up((size_t)B * sizeof(ImageDesc), 256);
-    const size_t n = align_up((size_t)(3 * (size_t)B + kMaxClasses + 2) * sizeof(int), 256);
+    // per class an image list and a tile prefix (an image is in at most two classes: its
+    // fields class and its self-overlap class), then the backward image order
+    const size_t n = align_up((size_t)(5 * (size_t)B + kMaxClasses + 2) * sizeof(int), 256);
     const size_t m = align_up((size_t)B * sizeof(CUtensorMap), 256);
     if (desc_off) *desc_off = h;
     if (ints_off) *ints_off = h + d;
@@ -194,9 +229,21 @@ int relayout(PlanHeader* h, ImageDesc* descs, int* ints, CUtensorMap* tmaps) {
         for (int i = 0; i < ci.nimg; ++i) {
             ImageDesc& d = descs[ints[ci.list_off + i]];
             ints[ci.prefix_off + i] = (int)t;
-            d.tile_begin = (int)t;
-            d.partial_off = pbase + t;
-            t += tiles_of(d);
+            if (ci.self) {
+                // the self-overlap pass: its own tiles and partials, which S_XX then sums
+                const long long nt = (long long)d.self_tiles_u * d.tiles_v * d.tiles_g;
+                d.sxx_off = pbase + t;
+                d.sxx_tiles = (int)nt;
+                t += nt;
+            } else {
+                d.tile_begin = (int)t;
+                d.partial_off = pbase + t;
+                if (d.self_cls < 0) {
+                    d.sxx_off = d.partial_off;
+                    d.sxx_tiles = (int)tiles_of(d);
+                }
+                t += tiles_of(d);
+            }
             if (t > 0x7fffffffLL) return ITC_ERR_UNSUPPORTED;
         }
         ints[ci.prefix_off + ci.nimg] = (int)t;
@@ -293,6 +340,15 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
                      encode_input_map(img, L.taps.R[0], &L.tmap_one);
     rc = cuda_status(launch_fields_any(L, tma, 0, (int)nt, L.taps.R[0], L.taps.R[1], img->ndim, img->dtype, s));
     if (rc) return rc;
+    if (sxx && has_self_pass(p, img->ndim)) {
+        // V(X) at its own width: the same tiles again (plain staging), S_XX partials only
+        make_taps(p, img->ndim, &L.taps, true);
+        L.mode = 2;
+        L.absolute = 0;
+        L.test_stall = 0;
+        rc = cuda_status(launch_fields_any(L, false, 0, (int)nt, L.taps.R[0], L.taps.R[1], img->ndim, img->dtype, s));
+        if (rc) return rc;
+    }
     if (sxx) rc = cuda_status(launch_reduce_sxx(L.partials, (int)nt, sxx, s));
     return rc;
 }
@@ -350,30 +406,44 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     CUtensorMap* tmaps = reinterpret_cast<CUtensorMap*>(buf.data() + tmap_off);
 
     // parameter classes: (ndim, dtype, sigma, trunc)
-    struct Key { int ndim, dtype; float s0, s1, s2, trunc; };
+    struct Key { int ndim, dtype; float s0, s1, s2, trunc; int self; };
     std::vector<Key> keys;
-    std::vector<int> cls_of(B);
+    std::vector<int> cls_of(B), self_of(B, -1);
+    // the class of (image b, pass): fields classes by (ndim, dtype, sigma, trunc); images whose
+    // V(X) width differs from sigma also join a self-overlap class keyed by that width
+    auto class_of = [&](int b, const itc_params* pb, bool self) -> int {
+        const int nd = imgs[b].ndim;
+        float w[3];
+        for (int i = 0; i < 3; ++i) w[i] = i < nd ? (self ? self_width(pb, i) : pb->sigma[i]) : 0.f;
+        Key k{nd, imgs[b].dtype, w[0], w[1], w[2], pb->trunc, self ? 1 : 0};
+        for (size_t i = 0; i < keys.size(); ++i)
+            if (memcmp(&keys[i], &k, sizeof(Key)) == 0) return (int)i;
+        if ((int)keys.size() == kMaxClasses) return -1;
+        keys.push_back(k);
+        const int c = (int)keys.size() - 1;
+        ClassInfo& ci = h->cls[c];
+        make_taps(pb, nd, &ci.taps, self);
+        ci.ndim = nd;
+        ci.dtype = imgs[b].dtype;
+        ci.absolute = 0;
+        ci.self = self ? 1 : 0;
+        ci.tile_h = tile_h_of(nd);
+        ci.tma = !self && fields_tma_supported(ci.ndim, ci.taps.R[0], ci.taps.R[1]) ? 1 : 0;
+        return c;
+    };
     for (int b = 0; b < B; ++b) {
         const itc_params* pb = p_stride ? p + b : p;
-        Key k{imgs[b].ndim, imgs[b].dtype, pb->sigma[0], pb->sigma[1], imgs[b].ndim == 3 ? pb->sigma[2] : 0.f, pb->trunc};
-        int c = -1;
-        for (size_t i = 0; i < keys.size(); ++i)
-            if (memcmp(&keys[i], &k, sizeof(Key)) == 0) { c = (int)i; break; }
-        if (c < 0) {
-            if ((int)keys.size() == kMaxClasses) return ITC_ERR_UNSUPPORTED;
-            keys.push_back(k);
-            c = (int)keys.size() - 1;
-            ClassInfo& ci = h->cls[c];
-            make_taps(pb, imgs[b].ndim, &ci.taps);
-            ci.ndim = imgs[b].ndim;
-            ci.dtype = imgs[b].dtype;
-            ci.absolute = 0;
-            ci.tile_h = tile_h_of(imgs[b].ndim);
-            ci.tma = fields_tma_supported(ci.ndim, ci.taps.R[0], ci.taps.R[1]) ? 1 : 0;
-        }
+        const int c = class_of(b, pb, false);
+        if (c < 0) return ITC_ERR_UNSUPPORTED;
         cls_of[b] = c;
         fill_desc(imgs + b, pb, M[b], descs + b);
         descs[b].cls = c;
+        if (has_self_pass(pb, imgs[b].ndim)) {
+            const int sc = class_of(b, pb, true);
+            if (sc < 0) return ITC_ERR_UNSUPPORTED;
+            self_of[b] = sc;
+            descs[b].self_cls = sc;
+        }
     }
     h->ncls = (int)keys.size();
 
@@ -396,6 +466,13 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         h->max_dim[2] = d.G > h->max_dim[2] ? d.G : h->max_dim[2];
         h->ndim_mask |= 1 << d.ndim;
     }
+    // A_s planes of the images with a self-overlap pass
+    for (int b = 0; b < B; ++b) {
+        ImageDesc& d = descs[b];
+        if (d.self_cls < 0) continue;
+        d.self_off = foff;
+        foff += (long long)align_up((size_t)d.plane_floats, 64);
+    }
     h->fields_floats = foff;
     h->total_pixels = ghoff;
     h->max_M = (int)maxM;
@@ -407,7 +484,7 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         ci.list_off = io;
         int n = 0;
         for (int b = 0; b < B; ++b)
-            if (cls_of[b] == c) ints[io + n++] = b;
+            if ((ci.self ? self_of[b] : cls_of[b]) == c) ints[io + n++] = b;
         ci.nimg = n;
         io += n;
         ci.prefix_off = io;
@@ -500,8 +577,9 @@ int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, in
         L.absolute = 0;
         L.tmaps = reinterpret_cast<const CUtensorMap*>(pd + h->tmap_off);
         L.grid_per_sm = ci.grid_per_sm;
-        const int rc = cuda_status(launch_fields_any(L, ci.tma != 0 && !ci.use_plain, t0, t1, ci.taps.R[0],
-                                                     ci.taps.R[1], ci.ndim, ci.dtype, s));
+        L.mode = ci.self ? 1 : 0;
+        const int rc = cuda_status(launch_fields_any(L, ci.tma != 0 && !ci.use_plain && !ci.self, t0, t1,
+                                                     ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
         if (rc) return rc;
     }
     return ITC_OK;
@@ -541,6 +619,7 @@ int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int
         L.tile_h = ci.tile_h;
         L.tmaps = reinterpret_cast<const CUtensorMap*>(pd + h->tmap_off);
         L.grid_per_sm = ci.grid_per_sm;
+        L.mode = ci.self ? 1 : 0;
         const bool tma = ci.tma && !ci.use_plain;
         for (int i = 0; i <= reps; ++i) {   // the first launch warms caches and is not timed
             if (i == 1 && cudaEventRecord(e0, s) != cudaSuccess) return ITC_ERR_CUDA;
@@ -555,7 +634,7 @@ int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int
     };
     for (int c = 0; c < h->ncls && !rc; ++c) {
         ClassInfo& ci = h->cls[c];
-        if (ci.ndim != 2) continue;   // 3-D tiles have one configuration
+        if (ci.ndim != 2 || ci.self) continue;   // 3-D and self-overlap tiles have one configuration
         struct Cand { int plain, tile_h, grid; };
         Cand cands[5];
         int nc = 0;
@@ -598,7 +677,7 @@ int itc_plan_class(const void* plan_host, int c, int* ndim, float* sigma, int* t
     if (sigma) for (int i = 0; i < 3; ++i) sigma[i] = ci.taps.sigma[i];
     if (tile_h) *tile_h = ci.tile_h;
     if (grid_per_sm) *grid_per_sm = ci.grid_per_sm;
-    if (staging) *staging = (ci.tma && !ci.use_plain) ? 1 : 0;
+    if (staging) *staging = ci.self ? 2 : ((ci.tma && !ci.use_plain) ? 1 : 0);
     if (images) *images = ci.nimg;
     if (tuned_ms) *tuned_ms = ci.tuned_ms;
     return ITC_OK;
@@ -610,6 +689,7 @@ int itc_plan_configure(void* plan_host, void* plan_dev, int c, int tile_h, int g
     if (!h || !plan_dev || !aligned(plan_dev, 16) || c < 0 || c >= h->ncls) return ITC_ERR_INVALID_ARG;
     if (grid_per_sm < 0 || grid_per_sm > 64 || (staging != 0 && staging != 1)) return ITC_ERR_INVALID_ARG;
     ClassInfo& ci = h->cls[c];
+    if (ci.self) return ITC_ERR_UNSUPPORTED;   // the self-overlap pass has one configuration
     if (staging == 1 && !ci.tma) return ITC_ERR_UNSUPPORTED;
     if (staging == 1 ? (tile_h != 32 && tile_h != 64) : tile_h != tile_h_of(ci.ndim)) return ITC_ERR_INVALID_ARG;
     ci.use_plain = staging ? 0 : 1;
@@ -624,6 +704,45 @@ int itc_plan_configure(void* plan_host, void* plan_dev, int c, int tile_h, int g
             cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return ITC_ERR_CUDA;
+    return ITC_OK;
+}
+
+int itc_params_parzen(int ndim, const float* xi, const float* omega, double mass, int M, float trunc,
+                      int iters, int form, int flags, itc_params* out) {
+    if (!out || (ndim != 2 && ndim != 3) || (form != 0 && form != 1)) return ITC_ERR_INVALID_ARG;
+    double x[3], o[3];
+    const bool schedule = mass > 0.0 && M > 0;
+    for (int i = 0; i < ndim; ++i) {
+        if (schedule) {
+            // Sec. 4: omega = sqrt(N / M) / 2, xi = omega / 2
+            o[i] = sqrt(mass / M) / 2.0;
+            x[i] = o[i] / 2.0;
+        } else {
+            if (!xi || !omega) return ITC_ERR_INVALID_ARG;
+            x[i] = xi[i];
+            o[i] = omega[i];
+        }
+        if (!(x[i] > 0.0) || !(o[i] > 0.0) || !isfinite(x[i]) || !isfinite(o[i])) return ITC_ERR_INVALID_ARG;
+    }
+    itc_params p;
+    memset(&p, 0, sizeof(p));
+    double step = 1.0;
+    for (int i = 0; i < ndim; ++i) {
+        const double t2 = x[i] * x[i] + o[i] * o[i];
+        p.sigma[i] = (float)sqrt(t2);
+        p.sigma_pair[i] = (float)(sqrt(2.0) * o[i]);
+        p.sigma_self[i] = (float)(sqrt(2.0) * x[i]);
+        const double si = o[i] * o[i] / t2;
+        if (form == 1) {
+            if (i > 0 && fabs(si - step) > 1e-12 * step) return ITC_ERR_INVALID_ARG;
+            step = si;
+        }
+    }
+    p.trunc = trunc;
+    p.iters = iters;
+    p.step_scale = (float)step;
+    p.flags = flags;
+    *out = p;
     return ITC_OK;
 }
 

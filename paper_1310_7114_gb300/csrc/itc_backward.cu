@@ -1,8 +1,10 @@
 // itc_backward.cu -- gradient of the Cauchy-Schwarz divergence, Eq. (1), with respect to the
 // codebook and to the per-pixel weights of weighted ITC (Sec. 5).
 //
-//   dD/dw_{k,i} = (2 / sigma_i^2) (E_{k,i} / S_WW - D_{k,i} / S_XW)
-//   dD/dh(x)    = 2 A(x) / S_XX - (2 / S_XW) sum_k g(x - w_k) [x in box(round(w_k))]
+//   dD/dw_{k,i} = (2 / rho_i^2) E_{k,i} / S_WW - (2 / tau_i^2) D_{k,i} / S_XW
+//   dD/dh(x)    = 2 A_s(x) / S_XX - (2 / S_XW) sum_k g_tau(x - w_k) [x in box(round(w_k))]
+// (tau = sigma: the data kernel and its fields; rho: the codebook pair kernel; A_s: the field of h
+// at the width s of V(X); rho = s = tau unless set apart, and then A_s = A.)
 //
 // Kernel 1 (one CTA per image): window sums a_k, D_k around round(w_k) read directly from the
 // image (kernel evaluated at the real w_k, one warp per k), the M x M sums s_k, E_k (one warp
@@ -53,9 +55,9 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
     __shared__ double red[4];
 
     if (tid < 32) {
-        const long long nt = (long long)D.tiles_u * D.tiles_v * D.tiles_g;
+        const long long nt = D.sxx_tiles;
         double v = 0;
-        for (long long i = tid; i < nt; i += 32) v += L.partials[D.partial_off + i];
+        for (long long i = tid; i < nt; i += 32) v += L.partials[D.sxx_off + i];
         v = warp_sum_d(v);
         if (tid == 0) red[3] = v;
     }
@@ -125,8 +127,9 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
     }
     // codebook interaction sums: one thread per k, every j in order
     {
-        const float q0 = (float)(1.4426950408889634 * (double)c0), q1 = (float)(1.4426950408889634 * (double)c1);
-        const float q2 = (float)(1.4426950408889634 * (double)c2);
+        const float q0 = (float)(1.4426950408889634 * (double)D.pinv2s2[0]);
+        const float q1 = (float)(1.4426950408889634 * (double)D.pinv2s2[1]);
+        const float q2 = (float)(1.4426950408889634 * (double)D.pinv2s2[2]);
         for (int k = tid; k < M; k += blockDim.x) {
             const float wk0 = sw[k * 3], wk1 = sw[k * 3 + 1], wk2 = sw[k * 3 + 2];
             float s_ = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
@@ -169,8 +172,10 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
         float* gW = L.grad_W + D.w_off;
         for (int k = tid; k < M; k += blockDim.x)
             for (int i = 0; i < nd; ++i) {
-                const double s2 = (double)D.sigma[i] * (double)D.sigma[i];
-                gW[k * nd + i] = (float)(gD * 2.0 / s2 * ((double)sE[k * 3 + i] / sww - (double)sD[k * 3 + i] / sxw));
+                const double t2 = (double)D.sigma[i] * (double)D.sigma[i];
+                const double r2 = (double)D.rho[i] * (double)D.rho[i];
+                gW[k * nd + i] = (float)(gD * 2.0 * ((double)sE[k * 3 + i] / (r2 * sww) -
+                                                     (double)sD[k * 3 + i] / (t2 * sxw)));
             }
     }
     if (tid == 0) {
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
             r.sww = sww;
             r.sxx = sxx;
             r.c = sxw / sww;
-            r.dcs = sxw > 0 ? log(sww) + log(sxx) - 2.0 * log(sxw) : INFINITY;
+            r.dcs = sxw > 0 ? log(sww) + log(sxx) - 2.0 * log(sxw) + D.dcs_const : INFINITY;
             r.empty = (int)red[2];
             r.moved = 0;
             r.iters_done = 0;
@@ -211,7 +216,8 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
     const int ntiles = D.bwd_tiles_u * D.bwd_tiles_v;
     const int Ru = D.R[0], Rv = D.R[1], Rg = D.R[2];
     const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
-    const float* A = L.fields + D.field_off;
+    // the S_XX term uses the field of h at the width of V(X): A itself unless set apart
+    const float* A = L.fields + (D.self_off >= 0 ? D.self_off : D.field_off);
     float* gh = L.grad_h + D.gh_off;
     const float s1 = (float)L.scal[img * 4 + 0], s2 = (float)L.scal[img * 4 + 1];
 

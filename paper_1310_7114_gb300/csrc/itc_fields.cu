@@ -32,6 +32,22 @@ __device__ __forceinline__ double block_sum_double(double v, double* red) {
     return t;  // valid in thread 0
 }
 
+__device__ __forceinline__ double block_sum_tile(float v, double* red) {
+    // S_XX share of one tile (deterministic): FP32 xor-shuffles within each warp (the FP64 rate
+    // of the part is a small fraction of its FP32 rate), then the warp sums in FP64 by warp 0.
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = (double)v;
+    __syncthreads();
+    double t = 0;
+    if (wid == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
 __device__ __forceinline__ int find_image(const int* __restrict__ prefix, int n, int b) {
     // largest p with prefix[p] <= b
     int lo = 0, hi = n - 1;
@@ -71,12 +87,16 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
         dp = &L.one;
     }
     const int H = dp->H, W = dp->W, pitch = dp->pitch, fpitch = dp->fpitch, G = dp->G;
-    const int tiles_v = dp->tiles_v, tiles_u = dp->tiles_u;
+    // mode 0: every plane of the fields; 1: A only, into the A_s plane (self-overlap pass);
+    // 2: the S_XX partials only
+    const int mode = L.mode;
+    const int nstore = mode == 0 ? NC : (mode == 1 ? 1 : 0);
+    const int tiles_v = dp->tiles_v, tiles_u = mode ? dp->self_tiles_u : dp->tiles_u;
     const int tv = b % tiles_v;
     const int tu = (b / tiles_v) % tiles_u;
     const int tg = b / (tiles_v * tiles_u);
     const int u0 = tu * TH, v0 = tv * TW;
-    float* const fbase = L.fields + dp->field_off;
+    float* const fbase = L.fields + (mode == 1 ? dp->self_off : dp->field_off);
     const long long plane = dp->plane_floats;
 
     extern __shared__ __align__(16) float smem[];
@@ -127,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
     const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
 
     const int nslices = (NDIM == 3) ? min(kGSlices, G - tg * kGSlices) : 1;
-    double part = 0.0;
+    float part = 0.f;
 
     for (int sl = 0; sl < nslices; ++sl) {
         const int yg = tg * kGSlices + sl;
@@ -156,7 +176,8 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
                     if (u >= H) break;
                     float* o = fbase + slice_off + (long long)u * fpitch + v0 + c0;
 #pragma unroll
-                    for (int f = 0; f < NC; ++f) st4(o + f * plane, 0.f, 0.f, 0.f, 0.f);
+                    for (int f = 0; f < NC; ++f)
+                        if (f < nstore) st4(o + f * plane, 0.f, 0.f, 0.f, 0.f);
                 }
             }
             continue;
@@ -308,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
                     float* o = fbase + slice_off + (long long)u * fpitch + v0 + c0;
 #pragma unroll
                     for (int f = 0; f < NC; ++f)
-                        st4(o + f * plane, acc[f][kk][0], acc[f][kk][1], acc[f][kk][2], acc[f][kk][3]);
+                        if (f < nstore) st4(o + f * plane, acc[f][kk][0], acc[f][kk][1], acc[f][kk][2], acc[f][kk][3]);
                     const int si = (k0 + kk + Ru) * SW + c0 + Rv;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -321,13 +342,14 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
                     }
                 }
             }
-            part += (double)ps;
+            part += ps;
         }
         __syncthreads();   // sT / s_in reuse by the next slice
     }
 
-    const double tot = block_sum_double(part, red);
-    if (tid == 0) L.partials[dp->partial_off + b] = tot;   // b = tile index within the image
+    const double tot = block_sum_tile(part, red);
+    // b = tile index within the image
+    if (tid == 0) L.partials[(mode ? dp->sxx_off : dp->partial_off) + b] = tot;
 }
 
 template <int RU, int RV, int NDIM, bool ABS, int DTYPE, int TH>

@@ -2,7 +2,7 @@
 //
 // Same arithmetic as fields_kernel in itc_fields.cu (the results are bit for bit the same: every
 // output accumulates the same products in the same order), reorganised for throughput:
-//   * persistent CTAs walk the tile list with a fixed stride;
+//   * persistent CTAs each walk a contiguous run of the tile list, image lookups loaded ahead;
 //   * the input tile plus its halo arrives by one cp.async.bulk.tensor (TMA) per tile into one
 //     of two staging buffers (one for 4-byte inputs), so copies run ahead of the tile being
 //     computed;
@@ -55,15 +55,10 @@ __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d
     *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
 }
 
-// The image and tile-local index of tile t of this launch, found by the whole calling warp:
-// a 32-ary search over the class tile prefix (largest p with prefix[p] <= t), three dependent
-// loads for 4096 images instead of twelve for a binary search.
-__device__ __forceinline__ void locate_warp(const FieldsLaunch& L, int t, int& img, int& local) {
-    if (!L.descs) {
-        img = 0;
-        local = t;
-        return;
-    }
+// The class-list position p of the image holding tile t of this launch, found by the whole
+// calling warp: a 32-ary search over the class tile prefix (largest p with prefix[p] <= t),
+// three dependent loads for 4096 images instead of twelve for a binary search.
+__device__ __forceinline__ int locate_pos(const FieldsLaunch& L, int t) {
     const int lane = threadIdx.x & 31;
     const int* prefix = L.tile_prefix;
     int lo = 0, hi = L.nimg - 1;   // prefix[lo] <= t always holds (prefix[0] = 0)
@@ -80,10 +75,63 @@ __device__ __forceinline__ void locate_warp(const FieldsLaunch& L, int t, int& i
     const int idx = lo + lane;
     const bool ok = idx <= hi && __ldg(prefix + idx) <= t;
     const unsigned m = __ballot_sync(0xffffffffu, ok);
-    const int p = lo + 31 - __clz(m);
-    img = __ldg(L.img_list + p);
-    local = t - __ldg(prefix + p);
+    return lo + 31 - __clz(m);
 }
+
+// The image and tile-local index of tile t (whole warp).
+__device__ __forceinline__ void locate_warp(const FieldsLaunch& L, int t, int& img, int& local) {
+    if (!L.descs) {
+        img = 0;
+        local = t;
+        return;
+    }
+    const int p = locate_pos(L, t);
+    img = __ldg(L.img_list + p);
+    local = t - __ldg(L.tile_prefix + p);
+}
+
+// Walks the tiles of one CTA's contiguous run in order (warp 0, every lane the same values).
+// The image changes only at image boundaries; the next image's entry, first tile and tiles per
+// row are loaded one boundary ahead and the list entry of the image after it two ahead, so no
+// load issued at a boundary depends on another and no tile waits on a lookup.
+struct TileCursor {
+    int t, p, img, local, next, tv;   // tile, list position, image, tile in image, first tile of
+                                      // the next image, tiles per row of the image
+    int n_img, n_next, n_tv;          // the same for position p + 1
+    int nn_img;                       // image at position p + 2
+    __device__ void start(const FieldsLaunch& L, int t0) {
+        t = t0;
+        if (!L.descs) {
+            p = 0; img = 0; local = t0; next = 0x7fffffff; tv = L.one.tiles_v;
+            return;
+        }
+        p = locate_pos(L, t0);
+        img = __ldg(L.img_list + p);
+        local = t0 - __ldg(L.tile_prefix + p);
+        next = __ldg(L.tile_prefix + p + 1);
+        tv = L.descs[img].tiles_v;
+        if (p + 1 < L.nimg) {
+            n_img = __ldg(L.img_list + p + 1);
+            n_next = __ldg(L.tile_prefix + p + 2);
+            n_tv = L.descs[n_img].tiles_v;
+        }
+        if (p + 2 < L.nimg) nn_img = __ldg(L.img_list + p + 2);
+    }
+    __device__ void advance(const FieldsLaunch& L) {
+        ++t;
+        ++local;
+        if (t == next && L.descs && p + 1 < L.nimg) {
+            ++p;
+            img = n_img; next = n_next; tv = n_tv; local = 0;
+            if (p + 1 < L.nimg) {
+                n_img = nn_img;
+                n_next = __ldg(L.tile_prefix + p + 2);
+                n_tv = L.descs[nn_img].tiles_v;
+            }
+            if (p + 2 < L.nimg) nn_img = __ldg(L.img_list + p + 2);
+        }
+    }
+};
 
 // Bounded wait for a staged tile: gives up after about one second (2^31 SM clocks); false means
 // the copy never landed.
@@ -131,32 +179,39 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
     }
     __syncthreads();
 
+    // This CTA's tiles: the contiguous run [t_lo, t_hi) of the launch's tiles [tile_base, ntiles),
+    // split evenly over the grid, so that neighbouring tiles share their image lookups.
+    const long long count = ntiles - L.tile_base;
+    const int t_lo = L.tile_base + (int)(count * blockIdx.x / gridDim.x);
+    const int t_hi = L.tile_base + (int)(count * (blockIdx.x + 1) / gridDim.x);
+
     // tile copies run NST tiles ahead: the n-th tile of this CTA lands in stage n % NST
-    // called by all of warp 0: resolve the tile, remember it for its stage, lane 0 starts the copy
+    // called by all of warp 0: remember the cursor's tile for its stage, lane 0 starts the copy
     uint32_t inflight = 0;   // (thread 0) bit b: a copy into stage b has been started, not yet waited for
-    auto issue = [&](int t, int buf, bool copy) {
-        int local, img;
-        locate_warp(L, t, img, local);
+    TileCursor cur = {};
+    auto issue = [&](int buf, bool copy) {
         if (tid == 0) {
-            const ImageDesc* dp = L.descs ? L.descs + img : &L.one;
-            const int tv = local % dp->tiles_v, tu = local / dp->tiles_v;
-            const CUtensorMap* map = L.descs ? L.tmaps + img : &L.tmap_one;
-            s_img[buf] = img;
-            s_local[buf] = local;
+            const int tv = cur.local % cur.tv, tu = cur.local / cur.tv;
+            const CUtensorMap* map = L.descs ? L.tmaps + cur.img : &L.tmap_one;
+            s_img[buf] = cur.img;
+            s_local[buf] = cur.local;
             if (copy) {
                 mbar_expect_tx(&bar[buf], BOX_BYTES);
                 tma_load_2d(stage0 + buf * STAGE_BYTES, map, tv * TW - RA, tu * TH - R, &bar[buf]);
                 inflight |= 1u << buf;
             }
         }
+        cur.advance(L);
     };
 
-    int t = L.tile_base + blockIdx.x;   // tiles [tile_base, ntiles) of the class
-    if (tid < 32)
+    int t = t_lo;
+    if (tid < 32 && t_lo < t_hi) {
+        cur.start(L, t_lo);
         for (int b = 0; b < NST; ++b)
-            if (t + b * (int)gridDim.x < ntiles)
+            if (t + b < t_hi)
                 // the test hook starts no copy for the first tile of CTA 0: its wait cannot end
-                issue(t + b * gridDim.x, b, !(L.test_stall && blockIdx.x == 0 && b == 0));
+                issue(b, !(L.test_stall && blockIdx.x == 0 && b == 0));
+    }
     uint32_t phase = 0;   // bit b: parity of the next completion of bar[b]
     int n = 0;            // tiles of this CTA so far
     const int kb = tid >> 4, cg = tid & 15;
@@ -175,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
         }
     };
 
-    for (; t < ntiles; t += gridDim.x) {
+    for (; t < t_hi; ++t) {
         const int buf = NST == 2 ? (n & 1) : 0;
         const unsigned char* stage = stage0 + buf * STAGE_BYTES;
         if (tid == 0) {
@@ -188,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
             // every tile this CTA still owns gets a NaN S_XX share, so each affected image
             // reports a non-finite status; then the copies still in flight land (bounded waits)
             if (tid < 32) {
-                for (int tt = t; tt < ntiles; tt += gridDim.x) {
+                for (int tt = t; tt < t_hi; ++tt) {
                     int im, lc;
                     locate_warp(L, tt, im, lc);
                     const ImageDesc* d2 = L.descs ? L.descs + im : &L.one;
@@ -244,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
             if (tid < 32) colbits[tid >> 2][tid & 3] = 0u;
         }
         const int any = __syncthreads_or(nonzero);   // the stage is free from here on
-        if (tid < 32 && t + NST * (int)gridDim.x < ntiles) issue(t + NST * gridDim.x, buf, true);
+        if (tid < 32 && t + NST < t_hi) issue(buf, true);
 
         const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
         if (!any) {
@@ -334,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
                 }
             }
         }
-        double part = 0.0;
+        float part = 0.f;
         if (col_active && t_any) {
             float2 aA[K][2], aU[K][2], aV[K][2];
 #pragma unroll
@@ -391,10 +446,10 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
                         if (v0 + c0 + j < W) ps = fmaf(hrow[j], a4[j], ps);
                 }
             }
-            part = (double)ps;
+            part = ps;
         }
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if ((tid & 31) == 0) red[tid >> 5] = part;
+        if ((tid & 31) == 0) red[tid >> 5] = (double)part;   // FP32 within a warp, FP64 across warps
         if (tid == 0) pending = dp->partial_off + local;
     }
     __syncthreads();

@@ -53,6 +53,15 @@ struct ImageDesc {
     float sigma[3];
     float inv2s2[3];            // 1 / (2 sigma_i^2)
     int R[3];
+    float rho[3];               // width of the codebook pair sums (rho = sigma unless set)
+    float pinv2s2[3];           // 1 / (2 rho_i^2)
+    float kappa[3];             // tau_i^2 / rho_i^2: factor of the pair term in the update
+    double dcs_const;           // normalisers of Eq. (1): 1/2 sum log(tau^4 / (rho^2 s^2))
+    long long sxx_off;          // first S_XX partial summed for S_XX (partial_off unless a
+    int sxx_tiles;              //   separate self-overlap pass holds them), and their count
+    int self_tiles_u;           // tile rows of the self-overlap pass (plain tiles)
+    long long self_off;         // offset of the A_s plane (field of h at width s), -1: s = sigma
+    int self_cls;               // class of the self-overlap pass, -1: none
 };
 
 struct ClassInfo {
@@ -63,6 +72,7 @@ struct ClassInfo {
     int use_plain;              // tuned: take the plain-staged kernel even though TMA is possible
     int grid_per_sm;            // tuned persistent CTAs per SM (0: as many as fit)
     float tuned_ms;             // fields time of the class under the chosen configuration (0: untuned)
+    int self;                   // self-overlap class: A at width s only, plain tiles
     int list_off;               // offset (ints) of this class's image list in the plan int area
     int prefix_off;             // offset (ints) of the class tile prefix (nimg + 1 ints)
     long long partial_base;     // first partial of the class
@@ -118,6 +128,8 @@ struct FieldsLaunch {
     int tile_base;              // first tile of this launch within the class (image sub-ranges)
     int test_stall;             // ITC_TEST_STALL_WAIT: CTA 0 waits for a phase that never completes
     int grid_per_sm;            // persistent CTAs per SM (0: as many as fit)
+    int mode;                   // 0: every field plane; 1: A only, into the A_s plane, S_XX
+                                // partials at sxx_off (self-overlap pass); 2: S_XX partials only
 };
 
 struct RunLaunch {

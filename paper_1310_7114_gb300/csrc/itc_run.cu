@@ -5,13 +5,14 @@
 // iteration:
 //   gather   a_k = A(r_k), D_k = F(r_k) (- r_k a_k if absolute) + (r_k - w_k) a_k,
 //            r_k = round(w_k) clamped to the lattice                  (Eq. (accupdate) data terms)
-//   pairs    s_k = sum_j g(w_j - w_k),  E_k = sum_j g(w_j - w_k)(w_j - w_k)   (Eq. (origupdate))
+//   pairs    s_k = sum_j g_rho(w_j - w_k),  E_k = sum_j g_rho(w_j - w_k)(w_j - w_k)   (Eq. (origupdate))
 //            one thread per k loops over every j in order (positions are broadcast from shared
 //            memory), so the per-k sums need no reduction; g = exp2f(-sum_i d_i^2 c_i) with
 //            log2(e) folded into c_i.
 //   sums     S_XW = sum_k a_k, S_WW = sum_k s_k (FP32 shuffle trees, then the warps in order),
 //            c = S_XW / S_WW, D_cs of Eq. (1) in double at the reported W
-//   update   w_k' = w_k + step_scale (D_k - c E_k) / a_k, rounded to the lattice unless
+//   update   w_k' = w_k + step_scale (D_k - kappa c E_k) / a_k, kappa_i = tau_i^2 / rho_i^2 (the
+//            factor differentiating Eq. (1) gives the pair term; 1 when tau = rho), rounded unless
 //            ITC_CONTINUOUS (on the lattice w_k is an integer, so w_k + round(delta) is exact in
 //            FP32); a_k = 0 keeps w_k.  Jacobi: every k reads the old W.
 #include <math.h>
@@ -68,13 +69,14 @@ __device__ __forceinline__ void block_sums(float a, float s, int e, float* red, 
     __syncthreads();   // red is reused by the next call
 }
 
-__device__ void write_stats(itc_stats* st, const Sums& s, double sxx, int moved, int iters_done) {
+__device__ void write_stats(itc_stats* st, const Sums& s, double sxx, int moved, int iters_done,
+                            double dcs_const) {
     itc_stats r;
     r.sxw = s.sxw;
     r.sww = s.sww;
     r.sxx = sxx;
     r.c = (double)s.sxw / (double)s.sww;
-    r.dcs = s.sxw > 0 ? log((double)s.sww) + log(sxx) - 2.0 * log((double)s.sxw) : INFINITY;
+    r.dcs = s.sxw > 0 ? log((double)s.sww) + log(sxx) - 2.0 * log((double)s.sxw) + dcs_const : INFINITY;
     r.empty = s.empty;
     r.moved = moved;
     r.iters_done = iters_done;
@@ -104,10 +106,13 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
     D.plane = Dg.plane_floats;
     D.H = Dg.H; D.W = Dg.W; D.G = Dg.G; D.fpitch = Dg.fpitch; D.M = Dg.M; D.iters = Dg.iters;
     D.flags = Dg.flags; D.step = Dg.step_scale;
-    // g(d) = exp(-sum_i d_i^2 / (2 sigma_i^2)) = 2^(-sum_i d_i^2 c_i), c_i = log2(e) / (2 sigma_i^2)
-    const float c0 = (float)(1.4426950408889634 * (double)Dg.inv2s2[0]);
-    const float c1 = (float)(1.4426950408889634 * (double)Dg.inv2s2[1]);
-    const float c2 = ND == 3 ? (float)(1.4426950408889634 * (double)Dg.inv2s2[2]) : 0.f;
+    // pair kernel g_rho(d) = exp(-sum_i d_i^2 / (2 rho_i^2)) = 2^(-sum_i d_i^2 c_i),
+    // c_i = log2(e) / (2 rho_i^2); rho = sigma unless the codebook width is set apart
+    const float c0 = (float)(1.4426950408889634 * (double)Dg.pinv2s2[0]);
+    const float c1 = (float)(1.4426950408889634 * (double)Dg.pinv2s2[1]);
+    const float c2 = ND == 3 ? (float)(1.4426950408889634 * (double)Dg.pinv2s2[2]) : 0.f;
+    const float kap[3] = {Dg.kappa[0], Dg.kappa[1], ND == 3 ? Dg.kappa[2] : 0.f};
+    const double dcs_const = Dg.dcs_const;
     const long long w_off = Dg.w_off;
     const int M = D.M, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -118,8 +123,8 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
     if (L.sxx_single) {
         if (tid == 0) s_sxx = *L.sxx_single;
     } else if (tid < 32) {
-        const long long nt = (long long)Dg.tiles_u * Dg.tiles_v * Dg.tiles_g;
-        const long long po = Dg.partial_off;
+        const long long nt = Dg.sxx_tiles;
+        const long long po = Dg.sxx_off;
         double v = 0;
         for (long long i = tid; i < nt; i += 32) v += L.partials[po + i];
         v = warp_sum_d(v);
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
             pe += !(ak > 0.f);
         }
         block_sums(pa, ps, pe, red, &s);
-        if (!L.final_eval && t == 0 && L.stats && tid == 0) write_stats(L.stats + img, s, sxx, 0, 0);
+        if (!L.final_eval && t == 0 && L.stats && tid == 0) write_stats(L.stats + img, s, sxx, 0, 0, dcs_const);
         if (t == D.iters || stop) break;
         // update (Jacobi: every k above read the old W; the barriers in block_sums separate them)
         const float c = s.sxw / s.sww;
@@ -228,7 +233,8 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
 #pragma unroll
             for (int i = 0; i < ND; ++i) {
                 const int ni = i == 0 ? D.H : (i == 1 ? D.W : D.G);
-                const float delta = D.step * (Dm[q][i] - c * Ek[q][i]) / a[q];
+                // tau^2 / rho^2 on the pair term: 1 (exact) when tau = rho
+                const float delta = D.step * (Dm[q][i] - (c * kap[i]) * Ek[q][i]) / a[q];
                 float nv;
                 if (snap) {
                     // w is integral: round(w + delta) = w + round(delta), exact in FP32
@@ -248,7 +254,7 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
         ++done;
         if (stop_fixed && moved == 0) stop = true;
     }
-    if (L.final_eval && L.stats && tid == 0) write_stats(L.stats + img, s, sxx, moved, done);
+    if (L.final_eval && L.stats && tid == 0) write_stats(L.stats + img, s, sxx, moved, done, dcs_const);
     if (!L.final_eval && L.stats && tid == 0) {
         L.stats[img].moved = moved;
         L.stats[img].iters_done = done;

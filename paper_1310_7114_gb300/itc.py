@@ -37,7 +37,7 @@ EXPORTS = (
     "itc_fields", "itc_step", "itc_plan_bytes", "itc_plan", "itc_plan_pixels", "itc_plan_offsets",
     "itc_run", "itc_run_fields", "itc_run_iterate", "itc_run_fields_range", "itc_run_iterate_range",
     "itc_run_pipelined", "itc_backward", "itc_fields_noalloc", "itc_autotune", "itc_plan_classes",
-    "itc_plan_class", "itc_plan_configure",
+    "itc_plan_class", "itc_plan_configure", "itc_params_parzen",
 )
 
 
@@ -49,7 +49,8 @@ class ItcImage(ctypes.Structure):
 
 class ItcParams(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float * 3), ("trunc", ctypes.c_float), ("iters", ctypes.c_int),
-                ("step_scale", ctypes.c_float), ("flags", ctypes.c_int)]
+                ("step_scale", ctypes.c_float), ("flags", ctypes.c_int), ("sigma_pair", ctypes.c_float * 3),
+                ("sigma_self", ctypes.c_float * 3)]
 
 
 class ItcStats(ctypes.Structure):
@@ -125,6 +126,9 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
         L.itc_run_pipelined.argtypes = [_P, _P, _P, _P, _P, _SZ, _P, _P, ctypes.c_int]
         L.itc_autotune.restype = ctypes.c_int
         L.itc_autotune.argtypes = [_P, _P, _P, _SZ, ctypes.c_int, _P]
+        L.itc_params_parzen.restype = ctypes.c_int
+        L.itc_params_parzen.argtypes = [ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_float,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
         L.itc_plan_configure.restype = ctypes.c_int
         L.itc_plan_configure.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
         L.itc_plan_classes.restype = ctypes.c_int
@@ -165,9 +169,33 @@ def _stream(stream=None) -> int:
     return s.cuda_stream
 
 
-def make_params(sigma, trunc: float = 3.0, iters: int = 0, step_scale: float = 1.0, flags: int = 0) -> ItcParams:
-    s = [float(sigma)] * 3 if np.isscalar(sigma) else [float(x) for x in sigma] + [1.0] * (3 - len(sigma))
-    return ItcParams((ctypes.c_float * 3)(*s), float(trunc), int(iters), float(step_scale), int(flags))
+def _width3(x, fill):
+    if x is None:
+        return [0.0] * 3
+    return [float(x)] * 3 if np.isscalar(x) else [float(v) for v in x] + [fill] * (3 - len(x))
+
+
+def make_params(sigma, trunc: float = 3.0, iters: int = 0, step_scale: float = 1.0, flags: int = 0,
+                sigma_pair=None, sigma_self=None) -> ItcParams:
+    """itc_params; ``sigma_pair`` (rho) and ``sigma_self`` (s) default to sigma (stored as 0)."""
+    s = _width3(sigma, 1.0)
+    return ItcParams((ctypes.c_float * 3)(*s), float(trunc), int(iters), float(step_scale), int(flags),
+                     (ctypes.c_float * 3)(*_width3(sigma_pair, 0.0)), (ctypes.c_float * 3)(*_width3(sigma_self, 0.0)))
+
+
+def params_parzen(ndim: int, xi=None, omega=None, mass: float = 0.0, M: int = 0, trunc: float = 3.0,
+                  iters: int = 0, form: int = 0, flags: int = 0) -> ItcParams:
+    """itc_params_parzen: parameters from the Parzen widths (xi, omega) or, with mass and M, from
+    the schedule omega = sqrt(mass/M)/2, xi = omega/2."""
+    def arr(x):
+        if x is None:
+            return None
+        v = [float(x)] * ndim if np.isscalar(x) else [float(t) for t in x]
+        return (ctypes.c_float * 3)(*(v + [0.0] * (3 - len(v))))
+    out = ItcParams()
+    _check(lib().itc_params_parzen(int(ndim), arr(xi), arr(omega), ctypes.c_double(mass), int(M), ctypes.c_float(trunc),
+                                   int(iters), int(form), int(flags), ctypes.byref(out)), "itc_params_parzen")
+    return out
 
 
 def make_image(data, ndim: int = 2, G: int = 1, weight=None) -> ItcImage:
@@ -216,11 +244,12 @@ def stats_to_numpy(t) -> np.ndarray:
 
 
 def fields(data, sigma, trunc: float = 3.0, absolute: bool = False, ndim: int = 2, G: int = 1, weight=None,
-           stream=None):
-    """Fields of one image; returns (fields [nf, G, H, fpitch] float32, S_XX float64 tensor [1])."""
+           stream=None, sigma_self=None):
+    """Fields of one image; returns (fields [nf, G, H, fpitch] float32, S_XX float64 tensor [1]).
+    S_XX is taken at ``sigma_self`` (the width of V(X)) when given."""
     torch = _torch()
     img = make_image(data, ndim, G, weight)
-    p = make_params(sigma, trunc, flags=ITC_FIELDS_ABSOLUTE if absolute else 0)
+    p = make_params(sigma, trunc, flags=ITC_FIELDS_ABSOLUTE if absolute else 0, sigma_self=sigma_self)
     nbytes = lib().itc_fields_bytes(ctypes.byref(img))
     if nbytes == 0:
         raise ItcError(ITC_ERR_INVALID_ARG, "itc_fields_bytes")
@@ -236,11 +265,11 @@ def fields(data, sigma, trunc: float = 3.0, absolute: bool = False, ndim: int = 
 
 
 def step(data, fields_t, sxx, W, sigma, trunc: float = 3.0, step_scale: float = 1.0, flags: int = 0,
-         ndim: int = 2, G: int = 1, weight=None, stream=None):
+         ndim: int = 2, G: int = 1, weight=None, stream=None, sigma_pair=None, sigma_self=None):
     """One update (itc_step); returns (W_out float32 [M, d], W_lattice int32 [M, d], stats record)."""
     torch = _torch()
     img = make_image(data, ndim, G, weight)
-    p = make_params(sigma, trunc, 1, step_scale, flags)
+    p = make_params(sigma, trunc, 1, step_scale, flags, sigma_pair=sigma_pair, sigma_self=sigma_self)
     W = W.contiguous()
     M = W.shape[0]
     Wo = torch.empty_like(W)
@@ -324,7 +353,7 @@ class Plan:
             _check(lib().itc_plan_class(self.host_ptr, c, ctypes.byref(nd), sig, ctypes.byref(th), ctypes.byref(gp),
                                         ctypes.byref(st), ctypes.byref(ni), ctypes.byref(ms)), "itc_plan_class")
             out.append(dict(ndim=nd.value, sigma=[round(x, 4) for x in sig[:nd.value]], tile_h=th.value,
-                            ctas_per_sm=gp.value, staging="tma" if st.value else "plain", images=ni.value,
+                            ctas_per_sm=gp.value, staging={0: "plain", 1: "tma", 2: "self"}[st.value], images=ni.value,
                             tuned_ms=ms.value))
         return out
 

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_struct_sizes_match_the_header():
     assert ctypes.sizeof(itc.ItcImage) == 40
-    assert ctypes.sizeof(itc.ItcParams) == 28
+    assert ctypes.sizeof(itc.ItcParams) == 52
     assert ctypes.sizeof(itc.ItcStats) == 56
 
 
@@ -183,3 +183,46 @@ def test_plan_class_queries_and_configuration_checks(L):
     assert L.itc_plan_configure(hp, dev, 0, 64, 0, 2, None) == itc.ITC_ERR_INVALID_ARG
     assert L.itc_autotune(hp, dev, 0x4000, ws, 0, None) == itc.ITC_ERR_INVALID_ARG
     assert L.itc_autotune(hp, dev, 0x4000, ws - 1, 3, None) == itc.ITC_ERR_WORKSPACE
+
+
+def test_params_from_parzen_widths(L):
+    """itc_params_parzen: tau = sqrt(xi^2 + omega^2), rho = sqrt(2) omega, s = sqrt(2) xi, the
+    accupdate step omega^2/tau^2, and the schedule omega = sqrt(N/M)/2, xi = omega/2."""
+    p = itc.params_parzen(2, xi=1.0, omega=2.0, iters=7)
+    assert np.allclose(list(p.sigma)[:2], [5 ** 0.5] * 2) and np.allclose(list(p.sigma_pair)[:2], [8 ** 0.5] * 2)
+    assert np.allclose(list(p.sigma_self)[:2], [2 ** 0.5] * 2) and p.step_scale == 1.0 and p.iters == 7
+    p = itc.params_parzen(3, xi=(1.0, 1.0, 2.0), omega=(2.0, 2.0, 4.0), form=1)
+    assert abs(p.step_scale - 0.8) < 1e-7
+    p = itc.params_parzen(2, mass=400.0, M=4)
+    assert np.allclose(list(p.sigma_pair)[:2], [2 ** 0.5 * 5.0] * 2) and np.allclose(list(p.sigma_self)[:2], [2 ** 0.5 * 2.5] * 2)
+    out = itc.ItcParams()
+    xi = (ctypes.c_float * 3)(1.0, 1.0, 0.0)
+    om = (ctypes.c_float * 3)(2.0, 1.0, 0.0)
+    assert L.itc_params_parzen(2, xi, om, 0.0, 0, 3.0, 0, 1, 0, ctypes.byref(out)) == itc.ITC_ERR_INVALID_ARG
+    neg = (ctypes.c_float * 3)(-1.0, 1.0, 0.0)
+    assert L.itc_params_parzen(2, neg, om, 0.0, 0, 3.0, 0, 0, 0, ctypes.byref(out)) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_params_parzen(4, xi, om, 0.0, 0, 3.0, 0, 0, 0, ctypes.byref(out)) == itc.ITC_ERR_INVALID_ARG
+
+
+def test_width_parameters_are_checked_and_classed(L):
+    img = itc.ItcImage(2, 64, 64, 1, 64, itc.ITC_U8, 0x1000, None)
+    fields = ctypes.c_void_p(0x2000)
+    for kw, code in ((dict(sigma_pair=-1.0), itc.ITC_ERR_INVALID_ARG), (dict(sigma_self=float("nan")), itc.ITC_ERR_INVALID_ARG),
+                     (dict(sigma_self=11.0), itc.ITC_ERR_UNSUPPORTED)):
+        p = itc.make_params(2.0, 3.0, **kw)
+        assert L.itc_fields(ctypes.byref(img), ctypes.byref(p), fields, None, 0x4000, 1 << 20, None) == code, kw
+    # images whose V(X) width differs join a self-overlap class (staging 2); the workspace grows
+    # by one A plane per such image
+    ps = [itc.make_params(2.0), itc.make_params(2.0, sigma_self=1.5), itc.make_params(2.0, sigma_pair=3.0)]
+    rc, buf, ws = _plan(L, [(64, 64), (64, 64), (64, 64)], [4, 4, 4], ps)
+    assert rc == 0
+    hp = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.itc_plan_classes(hp) == 2
+    st = ctypes.c_int()
+    sig = (ctypes.c_float * 3)()
+    n = ctypes.c_int()
+    assert L.itc_plan_class(hp, 1, None, sig, None, None, ctypes.byref(st), ctypes.byref(n), None) == 0
+    assert st.value == 2 and n.value == 1 and abs(sig[0] - 1.5) < 1e-7
+    rc2, _, ws2 = _plan(L, [(64, 64)] * 3, [4, 4, 4], [itc.make_params(2.0)] * 3)
+    assert ws - ws2 >= 64 * 64 * 4
+    assert L.itc_plan_configure(hp, 0x100000, 1, 64, 0, 0, None) == itc.ITC_ERR_UNSUPPORTED

@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         os.makedirs(os.path.dirname(_SO), exist_ok=True)
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -148,6 +148,38 @@ def sxx(h, A) -> float:
 
 
 # ------------------------------------------------------------------------- fixed-point step
+def segment_q(tau, ndim=2):
+    """q_i = 1/tau_i^2 rounded once to float (tau taken as the float of the parameters)."""
+    t = np.asarray(np.broadcast_to(np.asarray(tau, np.float32), (ndim,)), np.float64)
+    return (1.0 / (t * t)).astype(np.float32)
+
+
+def segment2d(h, tau, W):
+    """Segmentation reading (Figs. 3, 6): label of the codebook vector whose lattice site gives the
+    smallest single-precision sum_i d_i^2 / tau_i^2 (lowest index on ties); -1 where h = 0."""
+    h = _f64(h)
+    H, Wd = h.shape
+    q = np.ascontiguousarray(segment_q(tau, 2))
+    Wc = _f64(W).reshape(-1, 2)
+    lab = np.zeros((H, Wd), np.int32)
+    lib().orc_segment2d(_d(h), H, Wd, q.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), Wc.shape[0], _d(Wc),
+                        lab.ctypes.data_as(_I))
+    return lab
+
+
+def segment3d(gray, tau, W, G=256, hw=None):
+    """Segmentation of a gray image's [u, v, g] lattice: one label per pixel (its voxel)."""
+    gray = _i32(gray)
+    H, Wd = gray.shape
+    q = np.ascontiguousarray(segment_q(tau, 3))
+    Wc = _f64(W).reshape(-1, 3)
+    hwp = _f64(hw) if hw is not None else None
+    lab = np.zeros((H, Wd), np.int32)
+    lib().orc_segment3d(_i(gray), _d(hwp) if hwp is not None else None, H, Wd, G,
+                        q.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), Wc.shape[0], _d(Wc), lab.ctypes.data_as(_I))
+    return lab
+
+
 def _field_ptrs(F):
     F = [_f64(f) for f in F]
     arr = (_D * len(F))(*[_d(f) for f in F])

@@ -689,3 +689,68 @@ void orc_dcs_grad2d_dense(const double *h, const double *A, int H, int W, double
     free(D);
     free(E);
 }
+
+/* ------------------------------------------------------------- segmentation (Figs. 3 and 6) */
+/*
+ * The segments of Figs. 3 and 6 assign every pixel of the shape to one codebook vector; the
+ * paper does not state the rule.  Reading: the codebook vector of largest kernel value
+ * g_tau(x - r_k) at the pixel, i.e. the smallest
+ *     D_k(x) = sum_i d_i^2 q_i,   d_i = x_i - r_{k,i},  r_k = lattice_round(w_k),  q_i = 1/tau_i^2,
+ * evaluated in single precision exactly as written: each d_i^2 q_i rounded to float, the terms
+ * added in axis order (u, v[, g]) with one rounding each (no fused multiply-add), lowest k on
+ * ties.  q (float, ndim values) is given by the caller.  Sites without data (h = 0) get -1.
+ * labels has one entry per pixel (H x W, row major); in 3-D the pixel (u, v) is the voxel
+ * (u, v, gray(u, v)) with weight hw(u, v).
+ */
+static int nearest_codebook(int ndim, const int *x, const float *q, int M, const int *r)
+{
+    int best = -1;
+    float bd = 0.f;
+    for (int k = 0; k < M; ++k) {
+        float d = 0.f;
+        for (int i = 0; i < ndim; ++i) {
+            const int di = x[i] - r[k * ndim + i];
+            const float t = (float)(di * di) * q[i];
+            d = (i == 0) ? t : d + t;
+        }
+        if (best < 0 || d < bd) {
+            best = k;
+            bd = d;
+        }
+    }
+    return best;
+}
+
+static int *codebook_sites(int ndim, const int *shape, int M, const double *Wc)
+{
+    int *r = (int *)malloc((size_t)M * ndim * sizeof(int));
+    for (int k = 0; k < M; ++k)
+        for (int i = 0; i < ndim; ++i) r[k * ndim + i] = (int)lattice_round(Wc[k * ndim + i], shape[i]);
+    return r;
+}
+
+void orc_segment2d(const double *h, int H, int W, const float *q, int M, const double *Wc, int *labels)
+{
+    const int shape[2] = {H, W};
+    int *r = codebook_sites(2, shape, M, Wc);
+    for (int u = 0; u < H; ++u)
+        for (int v = 0; v < W; ++v) {
+            const int x[2] = {u, v};
+            labels[(size_t)u * W + v] = h[(size_t)u * W + v] != 0.0 ? nearest_codebook(2, x, q, M, r) : -1;
+        }
+    free(r);
+}
+
+void orc_segment3d(const int *gray, const double *hw, int H, int W, int G, const float *q, int M,
+                   const double *Wc, int *labels)
+{
+    const int shape[3] = {H, W, G};
+    int *r = codebook_sites(3, shape, M, Wc);
+    for (int u = 0; u < H; ++u)
+        for (int v = 0; v < W; ++v) {
+            const size_t o = (size_t)u * W + v;
+            const int x[3] = {u, v, gray[o]};
+            labels[o] = (hw ? hw[o] : 1.0) != 0.0 ? nearest_codebook(3, x, q, M, r) : -1;
+        }
+    free(r);
+}

@@ -180,6 +180,16 @@ def segment3d(gray, tau, W, G=256, hw=None):
     return lab
 
 
+def chamfer34(X):
+    """Sec. 5 weighting: 3-4 chamfer distance of every foreground pixel to the nearest background
+    pixel (outside of the image = background), by the two raster passes; H x W int32."""
+    X = np.ascontiguousarray(np.asarray(X) != 0, dtype=np.uint8)
+    H, W = X.shape
+    T = np.zeros((H, W), np.int32)
+    lib().orc_chamfer34(X.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), H, W, T.ctypes.data_as(_I))
+    return T
+
+
 def _field_ptrs(F):
     F = [_f64(f) for f in F]
     arr = (_D * len(F))(*[_d(f) for f in F])

@@ -754,3 +754,47 @@ void orc_segment3d(const int *gray, const double *hw, int H, int W, int G, const
         }
     free(r);
 }
+
+/* -------------------------------------------- chamfer distance transform (Sec. 5 weighting) */
+/*
+ * Sec. 5 weights the pixels of a binary shape by a distance transform T(X) (Borgefors' chamfer
+ * transform), so that interior pixels count more.  Reading: the 3-4 chamfer distance of every
+ * foreground pixel to the nearest background pixel, with the outside of the image counted as
+ * background (a one-pixel background frame); background pixels get 0.  Unit steps cost 3 along
+ * an axis and 4 along a diagonal.  Computed here by the two raster passes of the 3 x 3 mask:
+ * forward (rows top to bottom, columns left to right) over the upper-left half of the mask,
+ * then backward (bottom to top, right to left) over the lower-right half.  X: H x W bytes
+ * (nonzero = foreground); T: H x W ints.
+ */
+static int chamfer_at(const int *T, int H, int W, int u, int v)
+{
+    return (u < 0 || u >= H || v < 0 || v >= W) ? 0 : T[(size_t)u * W + v];   /* frame: 0 */
+}
+
+static int min2(int a, int b) { return a < b ? a : b; }
+
+void orc_chamfer34(const unsigned char *X, int H, int W, int *T)
+{
+    for (int u = 0; u < H; ++u)
+        for (int v = 0; v < W; ++v) {
+            if (!X[(size_t)u * W + v]) {
+                T[(size_t)u * W + v] = 0;
+                continue;
+            }
+            int d = chamfer_at(T, H, W, u - 1, v - 1) + 4;
+            d = min2(d, chamfer_at(T, H, W, u - 1, v) + 3);
+            d = min2(d, chamfer_at(T, H, W, u - 1, v + 1) + 4);
+            d = min2(d, chamfer_at(T, H, W, u, v - 1) + 3);
+            T[(size_t)u * W + v] = d;
+        }
+    for (int u = H - 1; u >= 0; --u)
+        for (int v = W - 1; v >= 0; --v) {
+            int d = T[(size_t)u * W + v];
+            if (d == 0) continue;
+            d = min2(d, chamfer_at(T, H, W, u + 1, v + 1) + 4);
+            d = min2(d, chamfer_at(T, H, W, u + 1, v) + 3);
+            d = min2(d, chamfer_at(T, H, W, u + 1, v - 1) + 4);
+            d = min2(d, chamfer_at(T, H, W, u, v + 1) + 3);
+            T[(size_t)u * W + v] = d;
+        }
+}

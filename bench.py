@@ -207,6 +207,33 @@ def cpu_baseline(name, seconds):
 
 
 # ----------------------------------------------------------------------------------- our arm
+def segment_report(images, seg_ms, world, B, peaks, peak_src):
+    """itc_segment over the batch: images/s and its bytes (input once, one int16 label per pixel)
+    against the HBM copy bandwidth."""
+    nbytes = sum(im.size * (im.itemsize + 2) for im in images)
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    ach = nbytes / (seg_ms / 1000.0) / 1e9
+    return {"value": world * B / (seg_ms / 1000.0), "unit": "images/s", "ms": seg_ms,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "algorithmic_bytes_per_launch": nbytes, "peak_source": f"{peak_src} hbm_gbs"},
+            "note": "labels by the final codebook after the timed steps; timed on its own, not part of the step"}
+
+
+def chamfer_report(images, ms, world, B, peaks, peak_src):
+    """itc_chamfer over the batch: images/s and its bytes (input once, one float weight per pixel)
+    against the HBM copy bandwidth."""
+    if ms is None:
+        return None
+    nbytes = sum(im.size * 5 for im in images)
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    ach = nbytes / (ms / 1000.0) / 1e9
+    return {"value": world * B / (ms / 1000.0), "unit": "images/s", "ms": ms,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "algorithmic_bytes_per_launch": nbytes, "peak_source": f"{peak_src} hbm_gbs"},
+            "note": "Sec. 5 weights T(X) of every binary image; one warp per image walks its rows twice; "
+                    "timed on its own, not part of the step"}
+
+
 def alu_roofline(images, pk, ndims, fields_ms, clocks, dev):
     """The fields pass against the FP32 FMA rate of the SMs at the clock seen under load."""
     import torch
@@ -365,6 +392,36 @@ def run_ours(args, rank, world, local_rank):
     d2h = 2 * W.numel() * 4 + stats.numel()
 
     # the same work launched image by image (one plan per image), on a prefix of the batch
+    # segmentation of every image by its final codebook (outside the step), its own timing
+    labels = torch.empty(plan.pixels, dtype=torch.int16, device=dev)
+    for _ in range(args.warmup):
+        itc.segment(plan, W, labels)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(args.steps):
+        itc.segment(plan, W, labels)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seg_ms = s0.elapsed_time(s1) / args.steps
+
+    # Sec. 5 chamfer weights of every binary image (outside the step), its own timing
+    cham = None
+    if all(im.dtype == np.uint8 for im in images) and all(n == 2 for n in ndims) and max(im.shape[1] for im in images) <= 1024:
+        cbuf = torch.zeros(max(int(itc.lib().itc_plan_padded_offset(plan.host_ptr, B)), 4), dtype=torch.float32,
+                           device=dev)
+        for _ in range(args.warmup):
+            itc.chamfer(plan, cbuf, views=False)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            itc.chamfer(plan, cbuf, views=False)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cham = c0.elapsed_time(c1) / args.steps
+        del cbuf
+
     per_image = None
     if not args.no_per_image and rank == 0:
         n_pi = min(B, args.per_image_n)
@@ -421,6 +478,8 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world} (independent images per GPU, no collective)",
                    "fields_tuning": [{k: c[k] for k in ("sigma", "images", "tile_h", "ctas_per_sm", "staging",
                                                         "tuned_ms")} for c in tuning]},
+        "segment": segment_report(images, seg_ms, world, B, peaks, peak_src),
+        "chamfer": chamfer_report(images, cham, world, B, peaks, peak_src),
         "phases_ms": {"fields": f_avg, "iterate": statistics.mean(i_ms), "backward": statistics.mean(b_ms),
                       "note": "phases run in sequence in a separate timed loop; the headline step overlaps "
                               f"fields and iterations over {args.chunks} image ranges on two streams"},

@@ -336,6 +336,41 @@ int itc_plan_class(const void* plan_host, int c, int* ndim, float* sigma, int* t
                    int* grid_per_sm, int* staging, int* images, float* tuned_ms);
 
 /*
+ * itc_plan_padded_offset -- offset (in elements) of image b in the plan's padded per-pixel
+ * layout: every image as H rows of itc_field_pitch(W) elements (16-byte aligned rows), images
+ * one after another.  b = B gives the total.  Host-only; negative on error.
+ */
+long long itc_plan_padded_offset(const void* plan_host, int b);
+
+/*
+ * itc_chamfer -- the pixel weights T(X) of weighted ITC, Sec. 5: for every binary image of a
+ * plan (all images must be 2-D ITC_U8; nonzero = foreground) the 3-4 chamfer distance transform
+ * (Borgefors) of the foreground, i.e. the length of the shortest 8-connected path to the nearest
+ * background pixel with axial steps costing 3 and diagonal steps 4; the outside of the image
+ * counts as background (reading); background pixels get 0.  Values are exact integers stored as
+ * floats.  out: device, the padded per-pixel layout (itc_plan_padded_offset; the padding columns
+ * are not written), 16-byte aligned, caller-owned; a plan over these weights (ITC_F32 images of
+ * pitch itc_field_pitch(W)) gives the chamfer-weighted clustering P = T(X) * G of Sec. 5.
+ * Errors: ITC_ERR_INVALID_ARG, ITC_ERR_UNSUPPORTED (an image wider than 1024), ITC_ERR_CUDA.
+ */
+int itc_chamfer(const void* plan_host, const void* plan_dev, float* out, void* stream);
+
+/*
+ * itc_segment -- the segments of Figs. 3 and 6 for every image of a plan: each pixel with data
+ * (h != 0; in 3-D the voxel (u, v, gray(u, v))) gets the index k of the codebook vector whose
+ * lattice site r_k = round(w_k) (clamped to the lattice) gives the largest kernel value
+ * g_tau(x - r_k), i.e. the smallest sum_i (x_i - r_{k,i})^2 / tau_i^2 (tau = the plan's sigma).
+ * The paper does not state the rule; this is the reading, evaluated in single precision term
+ * by term (q_i = 1/tau_i^2 rounded once to float, each product and sum rounded, axis order, no
+ * fused multiply-add), lowest k on ties.  Pixels without data get -1.
+ * W: the plan's codebook layout (device, as for itc_run).  labels: device, one int16 per pixel,
+ * image b at the pixel offset of itc_plan_offsets, rows of W entries (caller-owned).
+ * Errors: ITC_ERR_INVALID_ARG, ITC_ERR_CUDA.
+ */
+int itc_segment(const void* plan_host, const void* plan_dev, const float* W, short* labels,
+                void* stream);
+
+/*
  * itc_backward -- gradient of Eq. (1) for every image of a plan, scaled by an upstream gradient:
  *   dD/dw_{k,i} = (2 / sigma_i^2) (E_{k,i} / S_WW - D_{k,i} / S_XW)
  *   dD/dh(x)    = 2 A(x) / S_XX - (2 / S_XW) sum_k g(x - w_k) [x in the box of round(w_k)]

@@ -448,10 +448,12 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     h->ncls = (int)keys.size();
 
     // fields, codebook and pixel offsets
-    long long foff = 0, woff = 0, ghoff = 0, maxM = 0;
+    long long foff = 0, woff = 0, ghoff = 0, maxM = 0, padoff = 0;
     int bwd = 0;
     for (int b = 0; b < B; ++b) {
         ImageDesc& d = descs[b];
+        d.pad_off = padoff;
+        padoff += (long long)d.H * d.fpitch;
         d.field_off = foff;
         foff += (long long)align_up((size_t)(d.ndim + 1) * d.plane_floats, 64);
         d.w_off = woff;
@@ -475,6 +477,7 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     }
     h->fields_floats = foff;
     h->total_pixels = ghoff;
+    h->pad_floats = padoff;
     h->max_M = (int)maxM;
 
     // per class: image list (ascending image index) and the place of its tile prefix
@@ -744,6 +747,46 @@ int itc_params_parzen(int ndim, const float* xi, const float* omega, double mass
     p.flags = flags;
     *out = p;
     return ITC_OK;
+}
+
+long long itc_plan_padded_offset(const void* plan_host, int b) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || b < 0 || b > h->B) return ITC_ERR_INVALID_ARG;
+    if (b == h->B) return h->pad_floats;
+    const ImageDesc* descs = reinterpret_cast<const ImageDesc*>(reinterpret_cast<const unsigned char*>(plan_host) +
+                                                                h->desc_off);
+    return descs[b].pad_off;
+}
+
+int itc_chamfer(const void* plan_host, const void* plan_dev, float* out, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !aligned(plan_dev, 16) || !out || !aligned(out, 16)) return ITC_ERR_INVALID_ARG;
+    const ImageDesc* descs = reinterpret_cast<const ImageDesc*>(reinterpret_cast<const unsigned char*>(plan_host) +
+                                                                h->desc_off);
+    for (int b = 0; b < h->B; ++b) {
+        if (descs[b].ndim != 2 || descs[b].dtype != ITC_U8) return ITC_ERR_INVALID_ARG;
+        if (descs[b].W > kChamferMaxW) return ITC_ERR_UNSUPPORTED;
+    }
+    const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
+    ChamferLaunch L;
+    L.descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
+    L.out = out;
+    L.order = reinterpret_cast<const int*>(pd + h->ints_off) + h->bwd_order_off;
+    L.B = h->B;
+    return cuda_status(launch_chamfer(L, h->max_dim[1], reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int itc_segment(const void* plan_host, const void* plan_dev, const float* W, short* labels, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !aligned(plan_dev, 16) || !W || !labels) return ITC_ERR_INVALID_ARG;
+    if (!aligned(W, 4) || !aligned(labels, 2)) return ITC_ERR_INVALID_ARG;
+    const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
+    SegmentLaunch L;
+    L.descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
+    L.W = W;
+    L.labels = labels;
+    L.order = reinterpret_cast<const int*>(pd + h->ints_off) + h->bwd_order_off;
+    return cuda_status(launch_segment(L, h->B, h->max_M, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int itc_plan_classes(const void* plan_host) {

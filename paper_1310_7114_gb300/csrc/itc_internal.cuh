@@ -62,6 +62,8 @@ struct ImageDesc {
     int self_tiles_u;           // tile rows of the self-overlap pass (plain tiles)
     long long self_off;         // offset of the A_s plane (field of h at width s), -1: s = sigma
     int self_cls;               // class of the self-overlap pass, -1: none
+    long long pad_off;          // offset (floats) of the image in the padded per-pixel layout
+                                // (H rows of fpitch floats; chamfer weights)
 };
 
 struct ClassInfo {
@@ -98,6 +100,7 @@ struct PlanHeader {
     long long bwd_tiles;        // backward pixel tiles over all images
     int bwd_order_off;          // offset (ints) of the backward image order (B ints, most tiles first)
     long long tmap_off;         // bytes from plan start to CUtensorMap[B] (input tiles)
+    long long pad_floats;       // sum H*fpitch (padded per-pixel layout)
     ClassInfo cls[kMaxClasses];
 };
 
@@ -161,6 +164,22 @@ struct BackwardLaunch {
     int B;
 };
 
+constexpr int kChamferMaxW = 1024;   // chamfer rows: 32 lanes x 32 segments of registers
+
+struct ChamferLaunch {
+    const ImageDesc* descs;
+    float* out;                 // padded per-pixel layout (pad_off, rows of fpitch floats)
+    const int* order;           // image of each warp (B ints, most pixels first)
+    int B;
+};
+
+struct SegmentLaunch {
+    const ImageDesc* descs;
+    const float* W;
+    short* labels;              // per image H x W at gh_off
+    const int* order;           // image of each CTA (B ints, most pixels first)
+};
+
 constexpr int kBwdTileH = 64;   // backward pixel tile: 64 rows x 64 columns
 constexpr int kBwdTileW = 64;
 constexpr int kGSlices = 8;     // 3-D fields: gray slices per CTA
@@ -179,6 +198,8 @@ int fields_tma_box(int dtype, int R, int tile_h, int* box_w, int* box_h);
 cudaError_t launch_fields_tma(const FieldsLaunch& L, int ntiles, int R, int dtype, cudaStream_t s);
 // ndim: the lattice dimension of every image of the launch (2 or 3)
 cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s, int ndim);
+cudaError_t launch_chamfer(const ChamferLaunch& L, int max_W, cudaStream_t s);
+cudaError_t launch_segment(const SegmentLaunch& L, int B, int max_M, cudaStream_t s);
 cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles,
                             cudaStream_t s);
 }  // namespace itc

@@ -37,7 +37,8 @@ EXPORTS = (
     "itc_fields", "itc_step", "itc_plan_bytes", "itc_plan", "itc_plan_pixels", "itc_plan_offsets",
     "itc_run", "itc_run_fields", "itc_run_iterate", "itc_run_fields_range", "itc_run_iterate_range",
     "itc_run_pipelined", "itc_backward", "itc_fields_noalloc", "itc_autotune", "itc_plan_classes",
-    "itc_plan_class", "itc_plan_configure", "itc_params_parzen",
+    "itc_plan_class", "itc_plan_configure", "itc_params_parzen", "itc_segment",
+    "itc_plan_padded_offset", "itc_chamfer",
 )
 
 
@@ -126,6 +127,12 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
         L.itc_run_pipelined.argtypes = [_P, _P, _P, _P, _P, _SZ, _P, _P, ctypes.c_int]
         L.itc_autotune.restype = ctypes.c_int
         L.itc_autotune.argtypes = [_P, _P, _P, _SZ, ctypes.c_int, _P]
+        L.itc_plan_padded_offset.restype = ctypes.c_longlong
+        L.itc_plan_padded_offset.argtypes = [_P, ctypes.c_int]
+        L.itc_chamfer.restype = ctypes.c_int
+        L.itc_chamfer.argtypes = [_P, _P, _P, _P]
+        L.itc_segment.restype = ctypes.c_int
+        L.itc_segment.argtypes = [_P, _P, _P, _P, _P]
         L.itc_params_parzen.restype = ctypes.c_int
         L.itc_params_parzen.argtypes = [ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_float,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
@@ -386,6 +393,35 @@ def run(plan: Plan, W, stats=None, stream=None):
     _check(itc_run(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), _ptr(stats), plan.ws.data_ptr(),
                    plan.ws.numel(), _stream(stream)), "itc_run")
     return W
+
+
+def chamfer(plan: Plan, out=None, stream=None, views: bool = True):
+    """itc_chamfer: the Sec. 5 weights of every binary image of the plan; returns (buffer, list of
+    [H, W] float32 views with rows of field_pitch(W) floats, ready to be the images of a weighted
+    plan; None with views=False)."""
+    torch = _torch()
+    if out is None:
+        total = int(lib().itc_plan_padded_offset(plan.host_ptr, plan.B))
+        out = torch.zeros(max(total, 4), dtype=torch.float32, device=plan.dev.device)
+    _check(lib().itc_chamfer(plan.host_ptr, plan.dev.data_ptr(), out.data_ptr(), _stream(stream)), "itc_chamfer")
+    if not views:
+        return out, None
+    views = []
+    for b, (H, W) in enumerate(plan.shapes):
+        o = int(lib().itc_plan_padded_offset(plan.host_ptr, b))
+        fp = field_pitch(W)
+        views.append(out[o:o + H * fp].view(H, fp)[:, :W])
+    return out, views
+
+
+def segment(plan: Plan, W, labels=None, stream=None):
+    """itc_segment: int16 label per pixel (plan.pixels, image b at its pixel offset), -1 without data."""
+    torch = _torch()
+    if labels is None:
+        labels = torch.empty(plan.pixels, dtype=torch.int16, device=W.device)
+    _check(lib().itc_segment(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), labels.data_ptr(), _stream(stream)),
+           "itc_segment")
+    return labels
 
 
 def run_fields(plan: Plan, stream=None):

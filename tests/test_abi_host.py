@@ -226,3 +226,34 @@ def test_width_parameters_are_checked_and_classed(L):
     rc2, _, ws2 = _plan(L, [(64, 64)] * 3, [4, 4, 4], [itc.make_params(2.0)] * 3)
     assert ws - ws2 >= 64 * 64 * 4
     assert L.itc_plan_configure(hp, 0x100000, 1, 64, 0, 0, None) == itc.ITC_ERR_UNSUPPORTED
+
+
+def test_segment_rejects_invalid_arguments(L):
+    rc, buf, ws = _plan(L, [(64, 64)], [8], _p())
+    hp = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.itc_segment(hp, None, 0x1000, 0x2000, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_segment(hp, 0x100000, None, 0x2000, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_segment(hp, 0x100000, 0x1000, 0x2001, None) == itc.ITC_ERR_INVALID_ARG
+    bogus = ctypes.create_string_buffer(len(buf.raw))
+    assert L.itc_segment(ctypes.cast(bogus, ctypes.c_void_p), 0x100000, 0x1000, 0x2000, None) == itc.ITC_ERR_INVALID_ARG
+
+
+def test_chamfer_checks_and_padded_layout(L):
+    rc, buf, ws = _plan(L, [(10, 20), (7, 5)], [2, 2], _p())
+    hp = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.itc_plan_padded_offset(hp, 0) == 0
+    assert L.itc_plan_padded_offset(hp, 1) == 10 * 20
+    assert L.itc_plan_padded_offset(hp, 2) == 10 * 20 + 7 * 8
+    assert L.itc_plan_padded_offset(hp, 3) < 0
+    assert L.itc_chamfer(hp, 0x100000, 0x2008, None) == itc.ITC_ERR_INVALID_ARG    # unaligned output
+    assert L.itc_chamfer(hp, None, 0x2000, None) == itc.ITC_ERR_INVALID_ARG
+    rc, buf, ws = _plan(L, [(16, 1100)], [2], _p())
+    assert L.itc_chamfer(ctypes.cast(buf, ctypes.c_void_p), 0x100000, 0x2000, None) == itc.ITC_ERR_UNSUPPORTED
+    imgs = (itc.ItcImage * 1)(itc.ItcImage(2, 16, 16, 1, 16, itc.ITC_F32, 0x10000, None))
+    M = (ctypes.c_int * 1)(2)
+    ps = (itc.ItcParams * 1)(_p())
+    nb = L.itc_plan_bytes(1)
+    b2 = ctypes.create_string_buffer(nb)
+    wsz = ctypes.c_size_t(0)
+    assert L.itc_plan(1, imgs, M, ps, 0, ctypes.cast(b2, ctypes.c_void_p), nb, ctypes.byref(wsz)) == 0
+    assert L.itc_chamfer(ctypes.cast(b2, ctypes.c_void_p), 0x100000, 0x2000, None) == itc.ITC_ERR_INVALID_ARG

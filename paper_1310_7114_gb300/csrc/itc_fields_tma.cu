@@ -4,8 +4,11 @@
 // output accumulates the same products in the same order), reorganised for throughput:
 //   * persistent CTAs each walk a contiguous run of the tile list, image lookups loaded ahead;
 //   * the input tile plus its halo arrives by one cp.async.bulk.tensor (TMA) per tile into one
-//     of two staging buffers (one for 4-byte inputs), so copies run ahead of the tile being
+//     of three staging buffers (two for 4-byte inputs), so copies run ahead of the tile being
 //     computed;
+//   * the row pass reads its input windows straight from the staged box (bytes are turned into
+//     floats in registers), so a tile needs two barriers and no float copy of its input, and three
+//     CTAs fit on an SM for byte inputs;
 //   * both passes use packed FP32 FMAs (fma.rn.f32x2) over pairs of neighbouring columns.
 // Used for 2-D images whose rows start on 16-byte boundaries (the tensor map needs it) and for
 // the compiled radii 6, 9 and 12; everything else goes through fields_kernel.
@@ -142,41 +145,51 @@ __device__ __forceinline__ bool wait_stage(uint64_t* bar, uint32_t parity) {
     return true;
 }
 
+// Compile-time shape of one tile (rows TH + 2R of the staged box, stages in flight).
+template <int R, int DTYPE, int TH>
+struct TmaTile {
+    static constexpr int TW = kTileW, K = TH / 16;
+    static constexpr int ROWS = TH + 2 * R;
+    static constexpr int ES = DTYPE == ITC_U8 ? 1 : 4;
+    static constexpr int RA = DTYPE == ITC_U8 ? 16 : ((R + 3) & ~3);   // box starts 16-byte aligned
+    static constexpr int BW = TW + 2 * RA;                              // box width in elements
+    static constexpr int BOX_BYTES = BW * ROWS * ES;
+    static constexpr int STAGE_BYTES = (BOX_BYTES + 127) & ~127;
+    static constexpr int NST = STAGE_BYTES <= 12288 ? 3 : 2;           // staging buffers
+    static constexpr size_t SMEM = 128 + (size_t)NST * STAGE_BYTES + 2 * (size_t)ROWS * TW * 4;
+    static constexpr int MIN_CTAS = (DTYPE == ITC_U8 && TH == 64) ? 3 : 2;
+};
+
 template <int R, bool ABS, int DTYPE, int TH>
-__global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_constant__ FieldsLaunch L, int ntiles) {
-    constexpr int TW = kTileW, K = TH / 16;
-    constexpr int ROWS = TH + 2 * R;
-    constexpr int SW = ((TW + 2 * R + 3) & ~3) + 4;
-    constexpr int ES = DTYPE == ITC_U8 ? 1 : 4;
-    constexpr int RA = DTYPE == ITC_U8 ? 16 : ((R + 3) & ~3);   // box starts 16-byte aligned
-    constexpr int BW = TW + 2 * RA;                              // box width in elements
-    constexpr int BOX_BYTES = BW * ROWS * ES;
-    constexpr int STAGE_BYTES = (BOX_BYTES + 127) & ~127;
-    constexpr int NST = STAGE_BYTES <= 16384 ? 2 : 1;           // staging buffers (copies in flight)
-    constexpr int NWIN = ((8 + 2 * R) + 3) & ~3;                 // window of 8 row-pass outputs
+__global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
+    fields_tma_kernel(const __grid_constant__ FieldsLaunch L, int ntiles) {
+    using TT = TmaTile<R, DTYPE, TH>;
+    constexpr int TW = TT::TW, K = TT::K, ROWS = TT::ROWS, RA = TT::RA, BW = TT::BW;
+    constexpr int BOX_BYTES = TT::BOX_BYTES, STAGE_BYTES = TT::STAGE_BYTES, NST = TT::NST;
+    constexpr int NWIN = 8 + 2 * R;                  // inputs of 8 neighbouring row-pass outputs
+    constexpr int OFF = (RA - R) & 3;                // the window's first input within its 4-group
+    constexpr int NQ = (OFF + NWIN + 3) / 4;         // 4-element groups covering the window
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the TMA destination must be 128-byte aligned: round the base up (128 spare bytes reserved)
     unsigned char* stage0 = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // NST stages
-    float* s_in = reinterpret_cast<float*>(stage0 + NST * STAGE_BYTES);  // ROWS x SW
-    float* sT = s_in + ROWS * SW;                                     // T then T_v: ROWS x TW each
-    __shared__ __align__(8) uint64_t bar[2];
+    float* sT = reinterpret_cast<float*>(stage0 + NST * STAGE_BYTES);   // T then T_v: ROWS x TW each
+    __shared__ __align__(8) uint64_t bar[NST];
     __shared__ double red[32];
     __shared__ int s_abort;
-    // Zero tracking: rowmask[r] bit q = staged row r has a nonzero in its 4-column group q;
-    // colbits[b] = bits over staged rows whose T (8-column block b) is not known to be zero.
-    __shared__ uint32_t rowmask[ROWS];
-    __shared__ uint32_t colbits[TW / 8][4];
-    __shared__ int s_img[2], s_local[2];   // image and local tile of the copy in each stage
+    // colbits[p][b] (tile parity p): bits over staged rows whose T in 8-column block b is not
+    // known to be zero; the buffer of the next tile is cleared while this one is read
+    __shared__ uint32_t colbits[2][TW / 8][4];
+    __shared__ int s_img[NST], s_local[NST];   // image and local tile of the copy in each stage
     const Taps& tp = L.taps;
     const int tid = threadIdx.x;
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < NST; ++b) mbar_init(&bar[b], 1);
         mbar_init_fence();
         s_abort = 0;
     }
+    if (tid < 64) colbits[tid >> 5][(tid >> 2) & 7][tid & 3] = 0u;
     __syncthreads();
 
     // This CTA's tiles: the contiguous run [t_lo, t_hi) of the launch's tiles [tile_base, ntiles),
@@ -185,7 +198,8 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
     const int t_lo = L.tile_base + (int)(count * blockIdx.x / gridDim.x);
     const int t_hi = L.tile_base + (int)(count * (blockIdx.x + 1) / gridDim.x);
 
-    // tile copies run NST tiles ahead: the n-th tile of this CTA lands in stage n % NST
+    // tile copies run up to NST - 1 tiles ahead: the n-th tile of this CTA lands in stage n % NST,
+    // whose previous tile (n - NST) has finished both passes by the time the copy is started
     // called by all of warp 0: remember the cursor's tile for its stage, lane 0 starts the copy
     uint32_t inflight = 0;   // (thread 0) bit b: a copy into stage b has been started, not yet waited for
     TileCursor cur = {};
@@ -229,9 +243,18 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
             pending = -1;
         }
     };
+    // element i of a staged 4-group q: bytes -> float exactly (2^23 + b as a float, minus 2^23)
+    auto elem = [&](const uint32_t (&w)[NQ > 0 ? NQ * (DTYPE == ITC_U8) + 1 : 1], const float4 (&f)[NQ], int i) -> float {
+        if constexpr (DTYPE == ITC_U8)
+            return __int_as_float((int)__byte_perm(w[i >> 2], 0x4B000000u, 0x7540u | (unsigned)(i & 3))) - 8388608.f;
+        else {
+            const float4 g = f[i >> 2];
+            return (i & 3) == 0 ? g.x : ((i & 3) == 1 ? g.y : ((i & 3) == 2 ? g.z : g.w));
+        }
+    };
 
     for (; t < t_hi; ++t) {
-        const int buf = NST == 2 ? (n & 1) : 0;
+        const int buf = n % NST;
         const unsigned char* stage = stage0 + buf * STAGE_BYTES;
         if (tid == 0) {
             if (wait_stage(&bar[buf], (phase >> buf) & 1u)) inflight &= ~(1u << buf);
@@ -257,7 +280,11 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
             return;
         }
         phase ^= 1u << buf;
+        // the stage of the previous tile is free: start the copy NST - 1 tiles ahead into it
+        if (tid < 32 && n > 0 && t + NST - 1 < t_hi) issue((n - 1) % NST, true);
         ++n;
+        const int par = n & 1;
+        if (tid < 32) colbits[par ^ 1][tid >> 2][tid & 3] = 0u;   // for the next tile
         const int img = s_img[buf], local = s_local[buf];
         const ImageDesc* dp = L.descs ? L.descs + img : &L.one;
         const int H = dp->H, W = dp->W, fpitch = dp->fpitch;
@@ -265,84 +292,42 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
         float* const fbase = L.fields + dp->field_off;
         const long long plane = dp->plane_floats;
 
-        // staged box -> float input tile, columns shifted so that s_in column 0 is v0 - R; one
-        // warp per staged row, one 4-column group per lane, a ballot gives the row's zero mask
-        int nonzero = 0;
-        {
-            constexpr int NG = SW / 4;
-            static_assert(NG <= 32, "one lane per 4-column group");
-            const int wid = tid >> 5, lane = tid & 31;
-            for (int r = wid; r < ROWS; r += kThreads / 32) {
-                int nz = 0;
-                if (lane < NG) {
-                    const int c = lane * 4;
-                    float x[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int cc = c + j;
-                        float v = 0.f;
-                        if (cc < TW + 2 * R) {
-                            const int sc = r * BW + cc + (RA - R);
-                            // byte -> float exactly: 2^23 + b as a float, minus 2^23
-                            if (DTYPE == ITC_U8) v = __int_as_float(0x4B000000 | (int)stage[sc]) - 8388608.f;
-                            else v = reinterpret_cast<const float*>(stage)[sc];
-                        }
-                        x[j] = v;
-                        nz |= (v != 0.f);
-                    }
-                    st4(s_in + r * SW + c, x[0], x[1], x[2], x[3]);
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, nz);
-                if (lane == 0) rowmask[r] = m;
-                nonzero |= nz;
-            }
-            if (tid < 32) colbits[tid >> 2][tid & 3] = 0u;
-        }
-        const int any = __syncthreads_or(nonzero);   // the stage is free from here on
-        if (tid < 32 && t + NST < t_hi) issue(buf, true);
-
-        const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
-        if (!any) {
-            if (col_active) {
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    const int u = u0 + k0 + kk;
-                    if (u >= H) break;
-                    float* o = fbase + (long long)u * fpitch + v0 + c0;
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) st4(o + f * plane, 0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            if (tid == 0) L.partials[dp->partial_off + local] = 0.0;
-            continue;
-        }
-
-        // ---- pass along v: 8 outputs per item, pairs of neighbouring columns per packed FMA
+        // ---- pass along v, read straight from the staged box: 8 outputs per item, pairs of
+        // neighbouring columns per packed FMA; windows without data store zeros
         for (int item = tid; item < ROWS * 8; item += kThreads) {
             const int r = item >> 3, c = (item & 7) * 8;
             const int gu = u0 - R + r;
             if (v0 + c >= W) continue;
             float* oT = sT + r * TW + c;
             float* oV = oT + ROWS * TW;
-            if (gu < 0 || gu >= H) {
-                st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + 4, 0.f, 0.f, 0.f, 0.f);
-                st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + 4, 0.f, 0.f, 0.f, 0.f);
-                continue;
-            }
-            constexpr uint32_t WMASK = (1u << (NWIN / 4)) - 1u;
-            if (((rowmask[r] >> (c >> 2)) & WMASK) == 0u) {   // every input of the window is zero
-                st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + 4, 0.f, 0.f, 0.f, 0.f);
-                st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + 4, 0.f, 0.f, 0.f, 0.f);
-                continue;
-            }
-            atomicOr(&colbits[item & 7][r >> 5], 1u << (r & 31));
-            float x[NWIN];
-            const float* src = s_in + r * SW + c;
+            // the window's 4-groups: box columns c - R + RA - OFF ... (a multiple of 4)
+            const int g0 = (c - R + RA - OFF) >> 2;
+            uint32_t w[NQ * (DTYPE == ITC_U8) + 1];
+            float4 f[NQ];
+            bool nz = false;
+            if (gu >= 0 && gu < H) {
+                if constexpr (DTYPE == ITC_U8) {
+                    const uint32_t* row = reinterpret_cast<const uint32_t*>(stage + r * BW);
 #pragma unroll
-            for (int q = 0; q < NWIN / 4; ++q) {
-                const float4 f = *reinterpret_cast<const float4*>(src + 4 * q);
-                x[4 * q] = f.x; x[4 * q + 1] = f.y; x[4 * q + 2] = f.z; x[4 * q + 3] = f.w;
+                    for (int q = 0; q < NQ; ++q) { w[q] = row[g0 + q]; nz |= w[q] != 0u; }
+                } else {
+                    const float4* row = reinterpret_cast<const float4*>(stage + (size_t)r * BW * 4);
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        f[q] = row[g0 + q];
+                        nz |= (f[q].x != 0.f) | (f[q].y != 0.f) | (f[q].z != 0.f) | (f[q].w != 0.f);
+                    }
+                }
             }
+            if (!nz) {
+                st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + 4, 0.f, 0.f, 0.f, 0.f);
+                st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + 4, 0.f, 0.f, 0.f, 0.f);
+                continue;
+            }
+            atomicOr(&colbits[par][item & 7][r >> 5], 1u << (r & 31));
+            float x[NWIN];
+#pragma unroll
+            for (int i = 0; i < NWIN; ++i) x[i] = elem(w, f, OFF + i);
             float xv[ABS ? NWIN : 1];
             if constexpr (ABS) {
                 const float vb = (float)(v0 - R + c);
@@ -371,9 +356,10 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
 
         // ---- pass along u: K rows x 4 columns per thread, column pairs per packed FMA
         // T rows k0 .. k0 + K + 2R - 1 of this thread's 8-column block all zero -> outputs are zero
+        const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
         bool t_any = false;
         if (col_active) {
-            const uint32_t* cb = colbits[cg >> 1];
+            const uint32_t* cb = colbits[par][cg >> 1];
             const int rlo = k0, w0 = rlo >> 5;
             const unsigned long long both = ((unsigned long long)cb[w0 + 1] << 32) | cb[w0];
             const unsigned long long need = (K + 2 * R >= 64) ? ~0ull : ((1ull << (K + 2 * R)) - 1ull);
@@ -385,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
                     if (u >= H) break;
                     float* o = fbase + (long long)u * fpitch + v0 + c0;
 #pragma unroll
-                    for (int f = 0; f < 3; ++f) st4(o + f * plane, 0.f, 0.f, 0.f, 0.f);
+                    for (int ff = 0; ff < 3; ++ff) st4(o + ff * plane, 0.f, 0.f, 0.f, 0.f);
                 }
             }
         }
@@ -439,11 +425,23 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
                     st4(o, aA[kk][0].x, aA[kk][0].y, aA[kk][1].x, aA[kk][1].y);
                     st4(o + plane, aU[kk][0].x, aU[kk][0].y, aU[kk][1].x, aU[kk][1].y);
                     st4(o + 2 * plane, aV[kk][0].x, aV[kk][0].y, aV[kk][1].x, aV[kk][1].y);
-                    const float* hrow = s_in + (k0 + kk + R) * SW + c0 + R;
+                    // h at the four outputs, from the staged box (row k0 + kk + R, columns RA + c0 ..)
+                    float h4[4];
+                    if constexpr (DTYPE == ITC_U8) {
+                        const uint32_t hw =
+                            *reinterpret_cast<const uint32_t*>(stage + (k0 + kk + R) * BW + RA + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            h4[j] = __int_as_float((int)__byte_perm(hw, 0x4B000000u, 0x7540u | (unsigned)j)) - 8388608.f;
+                    } else {
+                        const float4 hf =
+                            *reinterpret_cast<const float4*>(stage + ((size_t)(k0 + kk + R) * BW + RA + c0) * 4);
+                        h4[0] = hf.x; h4[1] = hf.y; h4[2] = hf.z; h4[3] = hf.w;
+                    }
                     const float a4[4] = {aA[kk][0].x, aA[kk][0].y, aA[kk][1].x, aA[kk][1].y};
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
-                        if (v0 + c0 + j < W) ps = fmaf(hrow[j], a4[j], ps);
+                        if (v0 + c0 + j < W) ps = fmaf(h4[j], a4[j], ps);
                 }
             }
             part = ps;
@@ -458,15 +456,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_tma_kernel(const __grid_co
 
 template <int R, bool ABS, int DTYPE, int TH>
 cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
-    constexpr int TW = kTileW;
-    constexpr int ROWS = TH + 2 * R;
-    constexpr int SW = ((TW + 2 * R + 3) & ~3) + 4;
-    constexpr int ES = DTYPE == ITC_U8 ? 1 : 4;
-    constexpr int RA = DTYPE == ITC_U8 ? 16 : ((R + 3) & ~3);
-    constexpr int BOX_BYTES = (TW + 2 * RA) * ROWS * ES;
-    constexpr int STAGE_BYTES = (BOX_BYTES + 127) & ~127;
-    constexpr int NST = STAGE_BYTES <= 16384 ? 2 : 1;
-    const size_t smem = 128 + NST * (size_t)STAGE_BYTES + (size_t)ROWS * SW * 4 + 2 * (size_t)ROWS * TW * 4;
+    const size_t smem = TmaTile<R, DTYPE, TH>::SMEM;
     auto k = fields_tma_kernel<R, ABS, DTYPE, TH>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -180,6 +180,31 @@ def segment3d(gray, tau, W, G=256, hw=None):
     return lab
 
 
+def deriche_kernel(x):
+    """The damped-sinusoid fit k(x) of exp(-x^2/2), x >= 0 (Deriche)."""
+    lib().orc_deriche_kernel.restype = ctypes.c_double
+    return np.array([lib().orc_deriche_kernel(ctypes.c_double(float(t))) for t in np.ravel(x)])
+
+
+def deriche_filter(x, sigma):
+    """(sum_m x[m] g(m-n), sum_m x[m] g(m-n)(m-n)) by Deriche's recursion, zero outside the signal."""
+    x = _f64(x).ravel()
+    y, yd = np.zeros_like(x), np.zeros_like(x)
+    lib().orc_deriche_filter(_d(x), x.size, ctypes.c_double(sigma), _d(y), _d(yd))
+    return y, yd
+
+
+def fields2d_recursive(h, sigma, absolute=False):
+    """(A, F_u, F_v) by the recursive Gaussian (large-sigma fields, Sec. 3.1)."""
+    h = _f64(h)
+    H, W = h.shape
+    su, sv = (float(sigma), float(sigma)) if np.isscalar(sigma) else map(float, sigma)
+    A, Fu, Fv = np.zeros_like(h), np.zeros_like(h), np.zeros_like(h)
+    lib().orc_fields2d_recursive(_d(h), H, W, ctypes.c_double(su), ctypes.c_double(sv), int(absolute),
+                                 _d(A), _d(Fu), _d(Fv))
+    return A, Fu, Fv
+
+
 def chamfer34(X):
     """Sec. 5 weighting: 3-4 chamfer distance of every foreground pixel to the nearest background
     pixel (outside of the image = background), by the two raster passes; H x W int32."""

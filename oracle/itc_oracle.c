@@ -798,3 +798,109 @@ void orc_chamfer34(const unsigned char *X, int H, int W, int *T)
             T[(size_t)u * W + v] = d;
         }
 }
+
+/* --------------------------------------------- recursive Gaussian fields (large sigma, Sec. 3.1) */
+/*
+ * For large widths Sec. 3.1 points to recursive filters (it cites Deriche 1992).  Deriche's
+ * recursive Gaussian fits the kernel by two damped sinusoids,
+ *     exp(-x^2/2) ~ k(x) = sum_t (alpha_t cos(omega_t x) + beta_t sin(omega_t x)) exp(-b_t x),  x >= 0,
+ * (the published fit: alpha = 1.680, -0.6803; beta = 3.735, -0.2598; omega = 0.6318, 1.997;
+ * b = 1.783, 1.723), and the convolution with the sampled kernel g(d) ~ k(|d| / sigma) is then
+ * exact by recursion: with z_t = exp((-b_t + i omega_t) / sigma) and c_t = alpha_t - i beta_t,
+ * k(j / sigma) = Re sum_t c_t z_t^j, so for a signal x[0..n)
+ *     y[n]  = sum_m x[m] g(m - n)            = Re sum_t c_t (s0_t[n] + r0_t[n])
+ *     yd[n] = sum_m x[m] g(m - n) (m - n)    = Re sum_t c_t (r1_t[n] - s1_t[n])
+ * with the first-order complex recursions (zero outside the signal: zero start states)
+ *     s0[n] = x[n] + z s0[n-1],           s1[n] = z (s1[n-1] + s0[n-1])        (causal, j >= 0)
+ *     r0[n] = z (x[n+1] + r0[n+1]),       r1[n] = z (r1[n+1] + r0[n+1]) + z x[n+1]   (anticausal, j >= 1)
+ * where s1 = sum_j j z^j x[n-j] and r1 = sum_{j>=1} j z^j x[n+j].  The kernel is untruncated; the
+ * approximation is only the fit.  Written with explicit complex arithmetic in double.
+ */
+static const double kDericheAlpha[2] = {1.680, -0.6803};
+static const double kDericheBeta[2] = {3.735, -0.2598};
+static const double kDericheOmega[2] = {0.6318, 1.997};
+static const double kDericheB[2] = {1.783, 1.723};
+
+/* the fitted kernel k(x), x >= 0 */
+double orc_deriche_kernel(double x)
+{
+    double k = 0;
+    for (int t = 0; t < 2; ++t)
+        k += (kDericheAlpha[t] * cos(kDericheOmega[t] * x) + kDericheBeta[t] * sin(kDericheOmega[t] * x)) *
+             exp(-kDericheB[t] * x);
+    return k;
+}
+
+/* y = sum_m x[m] g(m - n), yd = sum_m x[m] g(m - n)(m - n) (either may be NULL) */
+void orc_deriche_filter(const double *x, int n, double sigma, double *y, double *yd)
+{
+    for (int i = 0; i < n; ++i) {
+        if (y) y[i] = 0;
+        if (yd) yd[i] = 0;
+    }
+    for (int t = 0; t < 2; ++t) {
+        const double mag = exp(-kDericheB[t] / sigma), ang = kDericheOmega[t] / sigma;
+        const double zr = mag * cos(ang), zi = mag * sin(ang);
+        const double cr = kDericheAlpha[t], ci = -kDericheBeta[t];
+        /* causal */
+        double s0r = 0, s0i = 0, s1r = 0, s1i = 0;
+        for (int i = 0; i < n; ++i) {
+            /* s1[i] = z (s1[i-1] + s0[i-1]) uses the previous s0 */
+            const double ar = s1r + s0r, ai = s1i + s0i;
+            s1r = zr * ar - zi * ai;
+            s1i = zr * ai + zi * ar;
+            const double pr = zr * s0r - zi * s0i, pi = zr * s0i + zi * s0r;
+            s0r = x[i] + pr;
+            s0i = pi;
+            if (y) y[i] += cr * s0r - ci * s0i;
+            if (yd) yd[i] -= cr * s1r - ci * s1i;
+        }
+        /* anticausal */
+        double r0r = 0, r0i = 0, r1r = 0, r1i = 0;
+        for (int i = n - 1; i >= 0; --i) {
+            const double xn = i + 1 < n ? x[i + 1] : 0.0;
+            /* r1[i] = z (r1[i+1] + r0[i+1] + x[i+1]),  r0[i] = z (r0[i+1] + x[i+1]) */
+            const double ar = r1r + r0r + xn, ai = r1i + r0i;
+            const double br = r0r + xn, bi = r0i;
+            r1r = zr * ar - zi * ai;
+            r1i = zr * ai + zi * ar;
+            r0r = zr * br - zi * bi;
+            r0i = zr * bi + zi * br;
+            if (y) y[i] += cr * r0r - ci * r0i;
+            if (yd) yd[i] += cr * r1r - ci * r1i;
+        }
+    }
+}
+
+/*
+ * 2-D fields by recursion along v, then along u (separable):  T = g_v * h, T_v = (d g)_v * h, then
+ * A = g_u * T, F_u = (d g)_u * T, F_v = g_u * T_v (centred moments, as for the mask fields);
+ * absolute: F_i + y_i A.
+ */
+void orc_fields2d_recursive(const double *h, int H, int W, double su, double sv, int absolute,
+                            double *A, double *Fu, double *Fv)
+{
+    double *T = (double *)malloc((size_t)H * W * sizeof(double));
+    double *Tv = (double *)malloc((size_t)H * W * sizeof(double));
+    const int L = H > W ? H : W;
+    double *in = (double *)malloc((size_t)L * sizeof(double));
+    double *o0 = (double *)malloc((size_t)L * sizeof(double));
+    double *o1 = (double *)malloc((size_t)L * sizeof(double));
+    for (int u = 0; u < H; ++u) orc_deriche_filter(h + (size_t)u * W, W, sv, T + (size_t)u * W, Tv + (size_t)u * W);
+    for (int v = 0; v < W; ++v) {
+        for (int u = 0; u < H; ++u) in[u] = T[(size_t)u * W + v];
+        orc_deriche_filter(in, H, su, o0, o1);
+        for (int u = 0; u < H; ++u) {
+            A[(size_t)u * W + v] = o0[u];
+            Fu[(size_t)u * W + v] = o1[u] + (absolute ? u * o0[u] : 0.0);
+        }
+        for (int u = 0; u < H; ++u) in[u] = Tv[(size_t)u * W + v];
+        orc_deriche_filter(in, H, su, o0, NULL);
+        for (int u = 0; u < H; ++u) Fv[(size_t)u * W + v] = o0[u] + (absolute ? v * A[(size_t)u * W + v] : 0.0);
+    }
+    free(T);
+    free(Tv);
+    free(in);
+    free(o0);
+    free(o1);
+}

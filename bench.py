@@ -36,7 +36,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per pixel of the fields pass, from one ncu capture of the C3 workload
 # with 1024 images (profiles/fields_tma_kernel_c3_1024.md), valid only for the kernel source it was
 # taken on (sha256 prefix below); scaled to a launch by its pixel count.
-FIELDS_TRAFFIC = {"workload": "c3", "bytes_per_pixel": 954.7e6 / 86358723, "source_sha256": "ba422d6171b21d3b",
+FIELDS_TRAFFIC = {"workload": "c3", "bytes_per_pixel": 1008.5e6 / 86358723, "source_sha256": "71a6ebf2c1b65b7a",
                   "source": "paper_1310_7114_gb300/csrc/itc_fields_tma.cu"}
 
 

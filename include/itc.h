@@ -63,6 +63,11 @@ extern "C" {
 #define ITC_FIELDS_ABSOLUTE 2  /* itc_fields writes u.X, v.X (, g.X) convolutions, not centred */
 #define ITC_STOP_ON_FIXED 4    /* stop when an iteration moves no codebook (theta = 0 test of
                                   Algorithm 1) */
+#define ITC_RECURSIVE 8        /* 2-D plans only: fields by recursive filtering instead of masks
+                                  (Sec. 3.1, for large widths): Deriche's fit of the Gaussian by
+                                  two damped sinusoids, untruncated, cost independent of sigma;
+                                  no radius limit.  itc_fields rejects it (ITC_ERR_UNSUPPORTED);
+                                  itc_backward rejects plans that use it */
 #define ITC_TEST_STALL_WAIT 256 /* test hook (itc_fields, tensor-tile path only): the first tile
                                   copy of the first CTA is never started, so that CTA's bounded
                                   wait (about one second) runs out; the call then reports
@@ -328,7 +333,8 @@ int itc_plan_classes(const void* plan_host);
  * itc_plan_class -- the configuration of class c (host-only): lattice dimension, sigma, output
  * rows per fields tile, persistent CTAs per SM (0 = as many as fit), staging (1 = tensor tiles,
  * 0 = plain loads, 2 = the extra pass that computes the field of h at the width of V(X) for
- * images whose sigma_self differs from sigma: plain loads, A only), number of images and the
+ * images whose sigma_self differs from sigma: plain loads, A only, 3 = recursive filtering,
+ * ITC_RECURSIVE), number of images and the
  * tuned fields time in ms (0 if not tuned).  Any output pointer may be NULL.
  * Errors: ITC_ERR_INVALID_ARG.
  */

@@ -56,13 +56,15 @@ int check_params(const itc_params* p, int ndim) {
     for (int i = 0; i < ndim; ++i)
         if (!finite_pos(p->sigma[i])) return ITC_ERR_INVALID_ARG;
     if (p->iters < 0 || !isfinite(p->step_scale)) return ITC_ERR_INVALID_ARG;
-    if (p->flags & ~(ITC_CONTINUOUS | ITC_FIELDS_ABSOLUTE | ITC_STOP_ON_FIXED | ITC_TEST_STALL_WAIT))
+    if (p->flags & ~(ITC_CONTINUOUS | ITC_FIELDS_ABSOLUTE | ITC_STOP_ON_FIXED | ITC_RECURSIVE | ITC_TEST_STALL_WAIT))
         return ITC_ERR_INVALID_ARG;
+    if ((p->flags & ITC_RECURSIVE) && ndim != 2) return ITC_ERR_UNSUPPORTED;
     for (int i = 0; i < ndim; ++i) {
         // 0 selects sigma; anything else must be a positive finite width
         if (p->sigma_pair[i] != 0.f && !finite_pos(p->sigma_pair[i])) return ITC_ERR_INVALID_ARG;
         if (p->sigma_self[i] != 0.f && !finite_pos(p->sigma_self[i])) return ITC_ERR_INVALID_ARG;
     }
+    if (p->flags & ITC_RECURSIVE) return ITC_OK;   // no masks: no radius limit
     float ws[3];
     for (int pass = 0; pass < 2; ++pass) {   // the fields widths, then the self-overlap widths
         for (int i = 0; i < 3; ++i) ws[i] = pass == 0 ? p->sigma[i] : self_width(p, i);
@@ -84,14 +86,33 @@ void fill_taps(float sigma, int R, float* g, float* dg) {
     }
 }
 
+// Deriche's damped-sinusoid fit of exp(-x^2/2) (weights alpha, beta; frequencies omega; decays b)
+constexpr double kRecAlpha[2] = {1.680, -0.6803}, kRecBeta[2] = {3.735, -0.2598};
+constexpr double kRecOmega[2] = {0.6318, 1.997}, kRecDecay[2] = {1.783, 1.723};
+
+void make_rec_coef(const float* sigma, RecCoef* rc) {
+    for (int a = 0; a < 2; ++a)
+        for (int t = 0; t < 2; ++t) {
+            const double mag = exp(-kRecDecay[t] / (double)sigma[a]), ang = kRecOmega[t] / (double)sigma[a];
+            rc->zr[a][t] = (float)(mag * cos(ang));
+            rc->zi[a][t] = (float)(mag * sin(ang));
+        }
+    for (int t = 0; t < 2; ++t) {
+        rc->cr[t] = (float)kRecAlpha[t];
+        rc->ci[t] = (float)(-kRecBeta[t]);
+    }
+}
+
 void make_taps(const itc_params* p, int ndim, Taps* t, bool self = false) {
     memset(t, 0, sizeof(*t));
+    const bool rec = (p->flags & ITC_RECURSIVE) != 0;
     for (int i = 0; i < 3; ++i) {
         const float s = (i < ndim) ? (self ? self_width(p, i) : p->sigma[i]) : 1.f;
         t->sigma[i] = s;
         t->inv2s2[i] = (i < ndim) ? (float)(1.0 / (2.0 * (double)s * s)) : 0.f;
-        t->R[i] = (i < ndim) ? radius_of(s, p->trunc) : 0;
+        t->R[i] = (i < ndim && !rec) ? radius_of(s, p->trunc) : 0;
     }
+    if (rec) return;   // no masks
     fill_taps(t->sigma[0], t->R[0], t->gu, t->dgu);
     fill_taps(t->sigma[1], t->R[1], t->gv, t->dgv);
     if (ndim == 3) fill_taps(t->sigma[2], t->R[2], t->gg, t->dgg);
@@ -117,6 +138,10 @@ void fill_desc(const itc_image* img, const itc_params* p, int M, ImageDesc* d) {
     const int th = tile_h_of(img->ndim);
     d->tiles_u = (img->H + th - 1) / th;
     d->tiles_v = (img->W + kTileW - 1) / kTileW;
+    if (p->flags & ITC_RECURSIVE) {   // one S_XX partial per 32 columns
+        d->tiles_u = 1;
+        d->tiles_v = (img->W + 31) / 32;
+    }
     d->tiles_g = img->ndim == 3 ? (d->G + kGSlices - 1) / kGSlices : 1;
     d->plane_floats = (long long)d->G * img->H * d->fpitch;
     d->bwd_tiles_u = (img->H + kBwdTileH - 1) / kBwdTileH;
@@ -128,7 +153,7 @@ void fill_desc(const itc_image* img, const itc_params* p, int M, ImageDesc* d) {
         const double r = on ? (double)pair_width(p, i) : 1.0, ss = on ? (double)self_width(p, i) : 1.0;
         d->sigma[i] = s;
         d->inv2s2[i] = on ? (float)(1.0 / (2.0 * (double)s * s)) : 0.f;
-        d->R[i] = on ? radius_of(s, p->trunc) : 0;
+        d->R[i] = on && !(p->flags & ITC_RECURSIVE) ? radius_of(s, p->trunc) : 0;
         d->rho[i] = (float)r;
         d->pinv2s2[i] = on ? (float)(1.0 / (2.0 * r * r)) : 0.f;
         d->kappa[i] = on ? (float)(((double)s * s) / (r * r)) : 0.f;
@@ -219,7 +244,7 @@ int relayout(PlanHeader* h, ImageDesc* descs, int* ints, CUtensorMap* tmaps) {
     for (int b = 0; b < h->B; ++b) {
         ImageDesc& d = descs[b];
         const ClassInfo& ci = h->cls[d.cls];
-        d.tiles_u = (d.H + ci.tile_h - 1) / ci.tile_h;
+        if (!ci.recursive) d.tiles_u = (d.H + ci.tile_h - 1) / ci.tile_h;
     }
     long long pbase = 0;
     for (int c = 0; c < h->ncls; ++c) {
@@ -322,6 +347,7 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
     if (rc) return rc;
     if ((rc = check_params(p, img->ndim))) return rc;
     if (!fields || !aligned(fields, 16)) return ITC_ERR_INVALID_ARG;
+    if (p->flags & ITC_RECURSIVE) return ITC_ERR_UNSUPPORTED;   // recursive fields need a plan's scratch planes
     const size_t need = itc_fields_workspace_bytes(img);
     if (!ws || ws_bytes < need || !aligned(ws, 16)) return ITC_ERR_WORKSPACE;
     FieldsLaunch L;
@@ -406,7 +432,7 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     CUtensorMap* tmaps = reinterpret_cast<CUtensorMap*>(buf.data() + tmap_off);
 
     // parameter classes: (ndim, dtype, sigma, trunc)
-    struct Key { int ndim, dtype; float s0, s1, s2, trunc; int self; };
+    struct Key { int ndim, dtype; float s0, s1, s2, trunc; int self, rec; };
     std::vector<Key> keys;
     std::vector<int> cls_of(B), self_of(B, -1);
     // the class of (image b, pass): fields classes by (ndim, dtype, sigma, trunc); images whose
@@ -415,7 +441,8 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         const int nd = imgs[b].ndim;
         float w[3];
         for (int i = 0; i < 3; ++i) w[i] = i < nd ? (self ? self_width(pb, i) : pb->sigma[i]) : 0.f;
-        Key k{nd, imgs[b].dtype, w[0], w[1], w[2], pb->trunc, self ? 1 : 0};
+        const int rec = (pb->flags & ITC_RECURSIVE) ? 1 : 0;
+        Key k{nd, imgs[b].dtype, w[0], w[1], w[2], rec ? 0.f : pb->trunc, self ? 1 : 0, rec};
         for (size_t i = 0; i < keys.size(); ++i)
             if (memcmp(&keys[i], &k, sizeof(Key)) == 0) return (int)i;
         if ((int)keys.size() == kMaxClasses) return -1;
@@ -428,7 +455,9 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         ci.absolute = 0;
         ci.self = self ? 1 : 0;
         ci.tile_h = tile_h_of(nd);
-        ci.tma = !self && fields_tma_supported(ci.ndim, ci.taps.R[0], ci.taps.R[1]) ? 1 : 0;
+        ci.recursive = rec;
+        if (rec) make_rec_coef(ci.taps.sigma, &ci.rc);
+        ci.tma = !self && !rec && fields_tma_supported(ci.ndim, ci.taps.R[0], ci.taps.R[1]) ? 1 : 0;
         return c;
     };
     for (int b = 0; b < B; ++b) {
@@ -455,7 +484,10 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         d.pad_off = padoff;
         padoff += (long long)d.H * d.fpitch;
         d.field_off = foff;
-        foff += (long long)align_up((size_t)(d.ndim + 1) * d.plane_floats, 64);
+        // recursive fields keep two scratch planes (the along-v results) after the field planes
+        const bool rec = (d.flags & ITC_RECURSIVE) != 0;
+        foff += (long long)align_up((size_t)(d.ndim + 1 + (rec ? 2 : 0)) * d.plane_floats, 64);
+        if (rec) h->has_recursive = 1;
         d.w_off = woff;
         woff += (long long)d.M * d.ndim;
         d.gh_off = ghoff;
@@ -472,8 +504,8 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     for (int b = 0; b < B; ++b) {
         ImageDesc& d = descs[b];
         if (d.self_cls < 0) continue;
-        d.self_off = foff;
-        foff += (long long)align_up((size_t)d.plane_floats, 64);
+        d.self_off = foff;   // A_s (plus one scratch plane for recursive fields)
+        foff += (long long)align_up((size_t)((d.flags & ITC_RECURSIVE) ? 2 : 1) * d.plane_floats, 64);
     }
     h->fields_floats = foff;
     h->total_pixels = ghoff;
@@ -581,8 +613,21 @@ int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, in
         L.tmaps = reinterpret_cast<const CUtensorMap*>(pd + h->tmap_off);
         L.grid_per_sm = ci.grid_per_sm;
         L.mode = ci.self ? 1 : 0;
-        const int rc = cuda_status(launch_fields_any(L, ci.tma != 0 && !ci.use_plain && !ci.self, t0, t1,
-                                                     ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
+        int rc;
+        if (ci.recursive) {
+            RecursiveLaunch R;
+            R.descs = L.descs;
+            R.fields = L.fields;
+            R.partials = L.partials;
+            R.img_list = L.img_list;
+            R.pos_base = p0;
+            R.mode = L.mode;
+            R.rc = ci.rc;
+            rc = cuda_status(launch_recursive(R, p1 - p0, s));
+        } else {
+            rc = cuda_status(launch_fields_any(L, ci.tma != 0 && !ci.use_plain && !ci.self, t0, t1, ci.taps.R[0],
+                                               ci.taps.R[1], ci.ndim, ci.dtype, s));
+        }
         if (rc) return rc;
     }
     return ITC_OK;
@@ -637,7 +682,7 @@ int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int
     };
     for (int c = 0; c < h->ncls && !rc; ++c) {
         ClassInfo& ci = h->cls[c];
-        if (ci.ndim != 2 || ci.self) continue;   // 3-D and self-overlap tiles have one configuration
+        if (ci.ndim != 2 || ci.self || ci.recursive) continue;   // one configuration for these
         struct Cand { int plain, tile_h, grid; };
         Cand cands[5];
         int nc = 0;
@@ -680,7 +725,7 @@ int itc_plan_class(const void* plan_host, int c, int* ndim, float* sigma, int* t
     if (sigma) for (int i = 0; i < 3; ++i) sigma[i] = ci.taps.sigma[i];
     if (tile_h) *tile_h = ci.tile_h;
     if (grid_per_sm) *grid_per_sm = ci.grid_per_sm;
-    if (staging) *staging = ci.self ? 2 : ((ci.tma && !ci.use_plain) ? 1 : 0);
+    if (staging) *staging = ci.recursive ? 3 : (ci.self ? 2 : ((ci.tma && !ci.use_plain) ? 1 : 0));
     if (images) *images = ci.nimg;
     if (tuned_ms) *tuned_ms = ci.tuned_ms;
     return ITC_OK;
@@ -692,7 +737,7 @@ int itc_plan_configure(void* plan_host, void* plan_dev, int c, int tile_h, int g
     if (!h || !plan_dev || !aligned(plan_dev, 16) || c < 0 || c >= h->ncls) return ITC_ERR_INVALID_ARG;
     if (grid_per_sm < 0 || grid_per_sm > 64 || (staging != 0 && staging != 1)) return ITC_ERR_INVALID_ARG;
     ClassInfo& ci = h->cls[c];
-    if (ci.self) return ITC_ERR_UNSUPPORTED;   // the self-overlap pass has one configuration
+    if (ci.self || ci.recursive) return ITC_ERR_UNSUPPORTED;   // one configuration for these
     if (staging == 1 && !ci.tma) return ITC_ERR_UNSUPPORTED;
     if (staging == 1 ? (tile_h != 32 && tile_h != 64) : tile_h != tile_h_of(ci.ndim)) return ITC_ERR_INVALID_ARG;
     ci.use_plain = staging ? 0 : 1;
@@ -878,6 +923,8 @@ int itc_backward(const void* plan_host, const void* plan_dev, const float* W, co
     const PlanHeader* h = plan_of(plan_host);
     if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
     if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    // the adjoint stamps truncated kernel boxes; recursive fields have none
+    if (h->has_recursive) return ITC_ERR_UNSUPPORTED;
     const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
     unsigned char* w = reinterpret_cast<unsigned char*>(ws);
     BackwardLaunch L;

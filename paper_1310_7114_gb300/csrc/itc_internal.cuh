@@ -66,6 +66,13 @@ struct ImageDesc {
                                 // (H rows of fpitch floats; chamfer weights)
 };
 
+// Deriche's recursive Gaussian for one class: per axis (u, v) and term t the complex pole
+// z = exp((-b_t + i omega_t) / sigma) and per term the complex weight c_t.
+struct RecCoef {
+    float zr[2][2], zi[2][2];
+    float cr[2], ci[2];
+};
+
 struct ClassInfo {
     Taps taps;
     int ndim, dtype, absolute, tile_h;
@@ -75,6 +82,8 @@ struct ClassInfo {
     int grid_per_sm;            // tuned persistent CTAs per SM (0: as many as fit)
     float tuned_ms;             // fields time of the class under the chosen configuration (0: untuned)
     int self;                   // self-overlap class: A at width s only, plain tiles
+    int recursive;              // fields by recursive filtering (ITC_RECURSIVE)
+    RecCoef rc;
     int list_off;               // offset (ints) of this class's image list in the plan int area
     int prefix_off;             // offset (ints) of the class tile prefix (nimg + 1 ints)
     long long partial_base;     // first partial of the class
@@ -101,6 +110,7 @@ struct PlanHeader {
     int bwd_order_off;          // offset (ints) of the backward image order (B ints, most tiles first)
     long long tmap_off;         // bytes from plan start to CUtensorMap[B] (input tiles)
     long long pad_floats;       // sum H*fpitch (padded per-pixel layout)
+    int has_recursive;          // some class computes its fields by recursion
     ClassInfo cls[kMaxClasses];
 };
 
@@ -166,6 +176,16 @@ struct BackwardLaunch {
 
 constexpr int kChamferMaxW = 1024;   // chamfer rows: 32 lanes x 32 segments of registers
 
+struct RecursiveLaunch {
+    const ImageDesc* descs;
+    float* fields;              // fields base (the images' planes and scratch planes)
+    double* partials;
+    const int* img_list;        // class image list
+    int pos_base;               // first list position of this launch
+    int mode;                   // 0: A, F_u, F_v and S_XX; 1: A_s and S_XX (self-overlap pass)
+    RecCoef rc;
+};
+
 struct ChamferLaunch {
     const ImageDesc* descs;
     float* out;                 // padded per-pixel layout (pad_off, rows of fpitch floats)
@@ -198,6 +218,7 @@ int fields_tma_box(int dtype, int R, int tile_h, int* box_w, int* box_h);
 cudaError_t launch_fields_tma(const FieldsLaunch& L, int ntiles, int R, int dtype, cudaStream_t s);
 // ndim: the lattice dimension of every image of the launch (2 or 3)
 cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s, int ndim);
+cudaError_t launch_recursive(const RecursiveLaunch& L, int nimg, cudaStream_t s);
 cudaError_t launch_chamfer(const ChamferLaunch& L, int max_W, cudaStream_t s);
 cudaError_t launch_segment(const SegmentLaunch& L, int B, int max_M, cudaStream_t s);
 cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles,

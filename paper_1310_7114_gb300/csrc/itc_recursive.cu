@@ -1,0 +1,150 @@
+// itc_recursive.cu -- 2-D fields for large widths by recursive filtering (Sec. 3.1 points to
+// recursive filters, citing Deriche 1992): the cost per pixel does not grow with sigma.
+//
+// Deriche's recursive Gaussian fits the kernel by two damped sinusoids,
+//     exp(-x^2/2) ~ sum_t Re(c_t exp((-b_t + i omega_t) x)),  x >= 0,
+// so with z_t = exp((-b_t + i omega_t) / sigma) the sampled kernel is g(j) ~ Re sum_t c_t z_t^j and
+// a convolution along one axis is four first-order complex recursions per signal:
+//   causal       s0[n] = x[n] + z s0[n-1],          s1[n] = z (s1[n-1] + s0[n-1])
+//   anticausal   r0[n] = z (r0[n+1] + x[n+1]),      r1[n] = z (r1[n+1] + r0[n+1] + x[n+1])
+//   g * x  = Re sum_t c_t (s0 + r0),     (d g) * x = Re sum_t c_t (r1 - s1)     (d = offset)
+// with zero states at the ends (no data outside the image), so the kernel is untruncated.
+//
+// Pass along v (one thread per row): T = g_v * h, T_v = (d g)_v * h into two scratch planes (the
+// causal part is stored, the anticausal part added).  Pass along u (one thread per column, so
+// warps read and write whole row segments): A = g_u * T, F_u = (d g)_u * T, F_v = g_u * T_v into
+// the field planes, same order; the column pass also sums h A per column (FP64) and each warp's
+// 32 columns into one S_XX partial, in a fixed order.  The self-overlap pass (mode 1) computes A
+// alone into the A_s plane with one scratch plane.
+#include "itc_internal.cuh"
+
+namespace itc {
+namespace {
+
+struct Cplx {
+    float r, i;
+};
+__device__ __forceinline__ Cplx cmul(Cplx a, Cplx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ Cplx cadd(Cplx a, Cplx b) { return {a.r + b.r, a.i + b.i}; }
+__device__ __forceinline__ float re_mul(Cplx c, Cplx s) { return c.r * s.r - c.i * s.i; }
+
+__device__ __forceinline__ float pixel(const ImageDesc& D, int u, int v) {
+    const size_t o = (size_t)u * D.pitch + v;
+    if (D.dtype == ITC_U8) return (float)__ldg(reinterpret_cast<const unsigned char*>(D.data) + o);
+    return __ldg(reinterpret_cast<const float*>(D.data) + o);
+}
+
+// one image per CTA: img = the class list entry of position base + blockIdx.x
+__device__ __forceinline__ const ImageDesc& rec_image(const RecursiveLaunch& L) {
+    return L.descs[__ldg(L.img_list + L.pos_base + blockIdx.x)];
+}
+
+__global__ void __launch_bounds__(256) rec_rows_kernel(const __grid_constant__ RecursiveLaunch L) {
+    const ImageDesc& D = rec_image(L);
+    const int H = D.H, W = D.W, fp = D.fpitch;
+    const bool moments = L.mode == 0;
+    float* P0 = L.fields + (moments ? D.field_off + 3 * D.plane_floats : D.self_off + D.plane_floats);
+    float* P1 = P0 + D.plane_floats;   // T_v (moments only)
+    const Cplx z0 = {L.rc.zr[1][0], L.rc.zi[1][0]}, z1 = {L.rc.zr[1][1], L.rc.zi[1][1]};
+    const Cplx c0 = {L.rc.cr[0], L.rc.ci[0]}, c1 = {L.rc.cr[1], L.rc.ci[1]};
+    for (int u = threadIdx.x; u < H; u += blockDim.x) {
+        float* t0 = P0 + (size_t)u * fp;
+        float* t1 = P1 + (size_t)u * fp;
+        Cplx a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, m0 = {0.f, 0.f}, m1 = {0.f, 0.f};   // s0, s1 per term
+        for (int v = 0; v < W; ++v) {
+            const float x = pixel(D, u, v);
+            m0 = cmul(z0, cadd(m0, a0));
+            m1 = cmul(z1, cadd(m1, a1));
+            a0 = cmul(z0, a0); a0.r += x;
+            a1 = cmul(z1, a1); a1.r += x;
+            t0[v] = re_mul(c0, a0) + re_mul(c1, a1);
+            if (moments) t1[v] = -(re_mul(c0, m0) + re_mul(c1, m1));
+        }
+        a0 = a1 = m0 = m1 = Cplx{0.f, 0.f};   // r0, r1 per term
+        for (int v = W - 1; v >= 0; --v) {
+            const float xn = v + 1 < W ? pixel(D, u, v + 1) : 0.f;
+            m0 = cmul(z0, cadd(cadd(m0, a0), Cplx{xn, 0.f}));
+            m1 = cmul(z1, cadd(cadd(m1, a1), Cplx{xn, 0.f}));
+            a0 = cmul(z0, cadd(a0, Cplx{xn, 0.f}));
+            a1 = cmul(z1, cadd(a1, Cplx{xn, 0.f}));
+            t0[v] += re_mul(c0, a0) + re_mul(c1, a1);
+            if (moments) t1[v] += re_mul(c0, m0) + re_mul(c1, m1);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) rec_cols_kernel(const __grid_constant__ RecursiveLaunch L) {
+    const ImageDesc& D = rec_image(L);
+    const int H = D.H, W = D.W, fp = D.fpitch;
+    const bool moments = L.mode == 0;
+    const long long pl = D.plane_floats;
+    const float* T = L.fields + (moments ? D.field_off + 3 * pl : D.self_off + pl);
+    const float* Tv = T + pl;
+    float* A = L.fields + (moments ? D.field_off : D.self_off);
+    float* Fu = A + pl;
+    float* Fv = A + 2 * pl;
+    const Cplx z0 = {L.rc.zr[0][0], L.rc.zi[0][0]}, z1 = {L.rc.zr[0][1], L.rc.zi[0][1]};
+    const Cplx c0 = {L.rc.cr[0], L.rc.ci[0]}, c1 = {L.rc.cr[1], L.rc.ci[1]};
+    const int lane = threadIdx.x & 31;
+    const long long poff = moments ? D.partial_off : D.sxx_off;
+    // whole warps walk the columns so that each warp's partial covers 32 consecutive columns
+    const int wcols = (W + 31) & ~31;
+    for (int v = threadIdx.x; v < wcols; v += blockDim.x) {
+        const bool on = v < W;
+        double hs = 0.0;
+        if (on) {
+            Cplx a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, m0 = {0.f, 0.f}, m1 = {0.f, 0.f}, b0 = {0.f, 0.f}, b1 = {0.f, 0.f};
+            for (int u = 0; u < H; ++u) {
+                const size_t o = (size_t)u * fp + v;
+                const float x = T[o];
+                m0 = cmul(z0, cadd(m0, a0));
+                m1 = cmul(z1, cadd(m1, a1));
+                a0 = cmul(z0, a0); a0.r += x;
+                a1 = cmul(z1, a1); a1.r += x;
+                A[o] = re_mul(c0, a0) + re_mul(c1, a1);
+                if (moments) {
+                    const float y = Tv[o];
+                    b0 = cmul(z0, b0); b0.r += y;
+                    b1 = cmul(z1, b1); b1.r += y;
+                    Fu[o] = -(re_mul(c0, m0) + re_mul(c1, m1));
+                    Fv[o] = re_mul(c0, b0) + re_mul(c1, b1);
+                }
+            }
+            a0 = a1 = m0 = m1 = b0 = b1 = Cplx{0.f, 0.f};
+            for (int u = H - 1; u >= 0; --u) {
+                const size_t o = (size_t)u * fp + v;
+                const float xn = u + 1 < H ? T[o + fp] : 0.f;
+                m0 = cmul(z0, cadd(cadd(m0, a0), Cplx{xn, 0.f}));
+                m1 = cmul(z1, cadd(cadd(m1, a1), Cplx{xn, 0.f}));
+                a0 = cmul(z0, cadd(a0, Cplx{xn, 0.f}));
+                a1 = cmul(z1, cadd(a1, Cplx{xn, 0.f}));
+                const float a = A[o] + re_mul(c0, a0) + re_mul(c1, a1);
+                A[o] = a;
+                if (moments) {
+                    const float yn = u + 1 < H ? Tv[o + fp] : 0.f;
+                    b0 = cmul(z0, cadd(b0, Cplx{yn, 0.f}));
+                    b1 = cmul(z1, cadd(b1, Cplx{yn, 0.f}));
+                    Fu[o] += re_mul(c0, m0) + re_mul(c1, m1);
+                    Fv[o] += re_mul(c0, b0) + re_mul(c1, b1);
+                }
+                hs += (double)pixel(D, u, v) * (double)a;
+            }
+        }
+        // S_XX share of these 32 columns: a fixed-order shuffle tree
+        for (int o = 16; o > 0; o >>= 1) hs += __shfl_xor_sync(0xffffffffu, hs, o);
+        if (lane == 0) L.partials[poff + (v >> 5)] = hs;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_recursive(const RecursiveLaunch& L, int nimg, cudaStream_t s) {
+    if (nimg <= 0) return cudaSuccess;
+    rec_rows_kernel<<<nimg, 256, 0, s>>>(L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    rec_cols_kernel<<<nimg, 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace itc

@@ -29,6 +29,7 @@ ITC_F32 = 1
 ITC_CONTINUOUS = 1
 ITC_FIELDS_ABSOLUTE = 2
 ITC_STOP_ON_FIXED = 4
+ITC_RECURSIVE = 8
 ITC_TEST_STALL_WAIT = 256
 
 # every symbol include/itc.h declares
@@ -360,7 +361,7 @@ class Plan:
             _check(lib().itc_plan_class(self.host_ptr, c, ctypes.byref(nd), sig, ctypes.byref(th), ctypes.byref(gp),
                                         ctypes.byref(st), ctypes.byref(ni), ctypes.byref(ms)), "itc_plan_class")
             out.append(dict(ndim=nd.value, sigma=[round(x, 4) for x in sig[:nd.value]], tile_h=th.value,
-                            ctas_per_sm=gp.value, staging={0: "plain", 1: "tma", 2: "self"}[st.value], images=ni.value,
+                            ctas_per_sm=gp.value, staging={0: "plain", 1: "tma", 2: "self", 3: "recursive"}[st.value], images=ni.value,
                             tuned_ms=ms.value))
         return out
 

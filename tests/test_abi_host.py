@@ -257,3 +257,19 @@ def test_chamfer_checks_and_padded_layout(L):
     wsz = ctypes.c_size_t(0)
     assert L.itc_plan(1, imgs, M, ps, 0, ctypes.cast(b2, ctypes.c_void_p), nb, ctypes.byref(wsz)) == 0
     assert L.itc_chamfer(ctypes.cast(b2, ctypes.c_void_p), 0x100000, 0x2000, None) == itc.ITC_ERR_INVALID_ARG
+
+
+def test_recursive_flag_checks(L):
+    img = itc.ItcImage(2, 64, 64, 1, 64, itc.ITC_U8, 0x1000, None)
+    p = itc.make_params(40.0, 3.0, flags=itc.ITC_RECURSIVE)     # far beyond the masks, fine when recursive
+    assert L.itc_fields(ctypes.byref(img), ctypes.byref(p), 0x2000, None, 0x4000, 1 << 20, None) == itc.ITC_ERR_UNSUPPORTED
+    g = itc.ItcImage(3, 64, 64, 16, 64, itc.ITC_U8, 0x1000, None)
+    assert L.itc_fields(ctypes.byref(g), ctypes.byref(itc.make_params((2.0, 2.0, 2.0), 3.0, flags=itc.ITC_RECURSIVE)),
+                        0x2000, None, 0x4000, 1 << 20, None) == itc.ITC_ERR_UNSUPPORTED
+    rc, buf, ws = _plan(L, [(64, 64), (40, 50)], [4, 4], [p, _p()])
+    assert rc == 0
+    hp = ctypes.cast(buf, ctypes.c_void_p)
+    st = ctypes.c_int()
+    assert L.itc_plan_class(hp, 0, None, None, None, None, ctypes.byref(st), None, None) == 0 and st.value == 3
+    assert L.itc_backward(hp, 0x100000, 0x1000, None, None, None, None, 0x4000, ws, None) == itc.ITC_ERR_UNSUPPORTED
+    assert L.itc_plan_configure(hp, 0x100000, 0, 64, 0, 0, None) == itc.ITC_ERR_UNSUPPORTED

@@ -301,6 +301,24 @@ int itc_run_pipelined(const void* plan_host, const void* plan_dev, float* W, itc
                       void* ws, size_t ws_bytes, void* stream, void* stream2, int chunks);
 
 /*
+ * itc_run_staged -- itc_run for images that are still in host memory: the images' bytes are
+ * copied to the device range by range (`chunks` image ranges, one cudaMemcpyAsync each) on
+ * `copy_stream`, and the fields of each range run on `stream` as soon as its bytes have landed,
+ * so the copy of range k+1 overlaps the fields of range k; the iterations of the whole batch
+ * follow in one launch.
+ * host_base / dev_base: a host copy and the device buffer that the plan's image pointers (data
+ * and weights) point into, same layout, `bytes` long; every image must lie inside the device
+ * buffer.  The host copy should be page-locked for the copies to overlap.  The copies start
+ * after the work already queued on `stream`; the results are those of itc_run.  copy_stream NULL
+ * or equal to stream: copies and work in order on one stream.  chunks in 1..64.
+ * Errors: ITC_ERR_INVALID_ARG (an image outside the buffer, bad sizes), ITC_ERR_WORKSPACE,
+ * ITC_ERR_CUDA; as itc_run.
+ */
+int itc_run_staged(const void* plan_host, const void* plan_dev, const void* host_base,
+                   void* dev_base, size_t bytes, float* W, itc_stats* stats, void* ws,
+                   size_t ws_bytes, int chunks, void* stream, void* copy_stream);
+
+/*
  * itc_autotune -- pick, per parameter class of a plan, the fields-pass configuration that runs
  * fastest on this GPU for this batch: the rows of output per tile (64 or 32, i.e. how much of
  * the R-wide halo the row pass recomputes), the number of persistent CTAs per SM (1 or as many

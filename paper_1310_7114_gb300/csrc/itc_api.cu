@@ -160,6 +160,12 @@ void fill_desc(const itc_image* img, const itc_params* p, int M, ImageDesc* d) {
         if (on) k += 0.5 * log(pow((double)s, 4) / (r * r * ss * ss));
     }
     d->dcs_const = k;
+    if (p->flags & ITC_RECURSIVE) {
+        float sw[3];
+        for (int i = 0; i < 3; ++i) sw[i] = i < img->ndim ? self_width(p, i) : 1.f;
+        make_rec_coef(p->sigma, &d->rc);
+        make_rec_coef(sw, &d->rc_self);
+    }
     d->self_tiles_u = d->tiles_u;
     d->self_off = -1;
     d->self_cls = -1;
@@ -442,6 +448,8 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         float w[3];
         for (int i = 0; i < 3; ++i) w[i] = i < nd ? (self ? self_width(pb, i) : pb->sigma[i]) : 0.f;
         const int rec = (pb->flags & ITC_RECURSIVE) ? 1 : 0;
+        // recursive fields take their widths from each image: one class for all of them
+        if (rec) w[0] = w[1] = w[2] = 0.f;
         Key k{nd, imgs[b].dtype, w[0], w[1], w[2], rec ? 0.f : pb->trunc, self ? 1 : 0, rec};
         for (size_t i = 0; i < keys.size(); ++i)
             if (memcmp(&keys[i], &k, sizeof(Key)) == 0) return (int)i;
@@ -456,7 +464,6 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         ci.self = self ? 1 : 0;
         ci.tile_h = tile_h_of(nd);
         ci.recursive = rec;
-        if (rec) make_rec_coef(ci.taps.sigma, &ci.rc);
         ci.tma = !self && !rec && fields_tma_supported(ci.ndim, ci.taps.R[0], ci.taps.R[1]) ? 1 : 0;
         return c;
     };
@@ -622,7 +629,6 @@ int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, in
             R.img_list = L.img_list;
             R.pos_base = p0;
             R.mode = L.mode;
-            R.rc = ci.rc;
             rc = cuda_status(launch_recursive(R, p1 - p0, s));
         } else {
             rc = cuda_status(launch_fields_any(L, ci.tma != 0 && !ci.use_plain && !ci.self, t0, t1, ci.taps.R[0],
@@ -905,6 +911,70 @@ int itc_run_pipelined(const void* plan_host, const void* plan_dev, float* W, itc
     // join: the first stream continues after the last iterations
     if (!rc) rc = cuda_status(cudaEventRecord(ev[n], s2));
     if (!rc) rc = cuda_status(cudaStreamWaitEvent(s1, ev[n], 0));
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);   // released once the work has run
+    return rc;
+}
+
+// Bytes [lo, hi) of the device image buffer that images [b0, b1) occupy (data and weights).
+static bool image_extent(const ImageDesc* d, int b0, int b1, const unsigned char* base, size_t bytes, size_t* lo,
+                         size_t* hi) {
+    size_t a = bytes, z = 0;
+    for (int b = b0; b < b1; ++b) {
+        const size_t es = d[b].dtype == ITC_F32 ? 4 : 1;
+        const size_t ext = ((size_t)(d[b].H - 1) * d[b].pitch + d[b].W);
+        const void* ptrs[2] = {d[b].data, d[b].weight};
+        const size_t sz[2] = {ext * es, ext * 4};
+        for (int q = 0; q < 2; ++q) {
+            if (!ptrs[q]) continue;
+            const unsigned char* p = reinterpret_cast<const unsigned char*>(ptrs[q]);
+            if (p < base || (size_t)(p - base) + sz[q] > bytes) return false;
+            a = std::min(a, (size_t)(p - base));
+            z = std::max(z, (size_t)(p - base) + sz[q]);
+        }
+    }
+    *lo = a < z ? a : 0;
+    *hi = a < z ? z : 0;
+    return true;
+}
+
+int itc_run_staged(const void* plan_host, const void* plan_dev, const void* host_base, void* dev_base, size_t bytes,
+                   float* W, itc_stats* stats, void* ws, size_t ws_bytes, int chunks, void* stream, void* copy_stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !W || !host_base || !dev_base || chunks < 1 || chunks > 64) return ITC_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    const ImageDesc* descs = reinterpret_cast<const ImageDesc*>(reinterpret_cast<const unsigned char*>(plan_host) +
+                                                                h->desc_off);
+    const unsigned char* base = reinterpret_cast<const unsigned char*>(dev_base);
+    const int n = chunks < h->B ? chunks : h->B;
+    std::vector<size_t> lo(n), hi(n);
+    for (int k = 0; k < n; ++k) {
+        const int b0 = (int)((long long)h->B * k / n), b1 = (int)((long long)h->B * (k + 1) / n);
+        if (!image_extent(descs, b0, b1, base, bytes, &lo[k], &hi[k])) return ITC_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t cs = copy_stream ? reinterpret_cast<cudaStream_t>(copy_stream) : s;
+    cudaEvent_t ev[65];
+    int made = 0, rc = ITC_OK;
+    for (; made <= n; ++made)
+        if (cudaEventCreateWithFlags(&ev[made], cudaEventDisableTiming) != cudaSuccess) { rc = ITC_ERR_CUDA; break; }
+    // the copies start after the work already queued on `stream` (it may still read the buffer)
+    if (!rc && cs != s) rc = cuda_status(cudaEventRecord(ev[n], s));
+    if (!rc && cs != s) rc = cuda_status(cudaStreamWaitEvent(cs, ev[n], 0));
+    for (int k = 0; k < n && !rc; ++k) {
+        if (hi[k] > lo[k])
+            rc = cuda_status(cudaMemcpyAsync(const_cast<unsigned char*>(base) + lo[k],
+                                             reinterpret_cast<const unsigned char*>(host_base) + lo[k], hi[k] - lo[k],
+                                             cudaMemcpyHostToDevice, cs));
+        if (!rc && cs != s) rc = cuda_status(cudaEventRecord(ev[k], cs));
+    }
+    // the fields of each range as soon as its bytes have landed; then the iterations of the whole
+    // batch in one launch (one CTA per image needs the whole batch to fill the GPU)
+    for (int k = 0; k < n && !rc; ++k) {
+        const int b0 = (int)((long long)h->B * k / n), b1 = (int)((long long)h->B * (k + 1) / n);
+        if (cs != s) rc = cuda_status(cudaStreamWaitEvent(s, ev[k], 0));
+        if (!rc) rc = itc_run_fields_range(plan_host, plan_dev, b0, b1, ws, ws_bytes, s);
+    }
+    if (!rc) rc = itc_run_iterate(plan_host, plan_dev, W, stats, ws, ws_bytes, s);
     for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);   // released once the work has run
     return rc;
 }

@@ -31,6 +31,13 @@ struct Taps {
     int R[3];
 };
 
+// Deriche's recursive Gaussian for one width: per axis (u, v) and term t the complex pole
+// z = exp((-b_t + i omega_t) / sigma) and per term the complex weight c_t.
+struct RecCoef {
+    float zr[2][2], zi[2][2];
+    float cr[2], ci[2];
+};
+
 // One image as the kernels see it (device-resident inside a plan, or passed by value).
 struct ImageDesc {
     const void* data;
@@ -64,14 +71,9 @@ struct ImageDesc {
     int self_cls;               // class of the self-overlap pass, -1: none
     long long pad_off;          // offset (floats) of the image in the padded per-pixel layout
                                 // (H rows of fpitch floats; chamfer weights)
+    RecCoef rc, rc_self;        // ITC_RECURSIVE: the recursions at sigma and at the V(X) width
 };
 
-// Deriche's recursive Gaussian for one class: per axis (u, v) and term t the complex pole
-// z = exp((-b_t + i omega_t) / sigma) and per term the complex weight c_t.
-struct RecCoef {
-    float zr[2][2], zi[2][2];
-    float cr[2], ci[2];
-};
 
 struct ClassInfo {
     Taps taps;
@@ -82,8 +84,7 @@ struct ClassInfo {
     int grid_per_sm;            // tuned persistent CTAs per SM (0: as many as fit)
     float tuned_ms;             // fields time of the class under the chosen configuration (0: untuned)
     int self;                   // self-overlap class: A at width s only, plain tiles
-    int recursive;              // fields by recursive filtering (ITC_RECURSIVE)
-    RecCoef rc;
+    int recursive;              // fields by recursive filtering (ITC_RECURSIVE); widths per image
     int list_off;               // offset (ints) of this class's image list in the plan int area
     int prefix_off;             // offset (ints) of the class tile prefix (nimg + 1 ints)
     long long partial_base;     // first partial of the class
@@ -183,7 +184,6 @@ struct RecursiveLaunch {
     const int* img_list;        // class image list
     int pos_base;               // first list position of this launch
     int mode;                   // 0: A, F_u, F_v and S_XX; 1: A_s and S_XX (self-overlap pass)
-    RecCoef rc;
 };
 
 struct ChamferLaunch {

@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(256) rec_rows_kernel(const __grid_constant__ R
     const bool moments = L.mode == 0;
     float* P0 = L.fields + (moments ? D.field_off + 3 * D.plane_floats : D.self_off + D.plane_floats);
     float* P1 = P0 + D.plane_floats;   // T_v (moments only)
-    const Cplx z0 = {L.rc.zr[1][0], L.rc.zi[1][0]}, z1 = {L.rc.zr[1][1], L.rc.zi[1][1]};
-    const Cplx c0 = {L.rc.cr[0], L.rc.ci[0]}, c1 = {L.rc.cr[1], L.rc.ci[1]};
+    const RecCoef& rc = moments ? D.rc : D.rc_self;
+    const Cplx z0 = {rc.zr[1][0], rc.zi[1][0]}, z1 = {rc.zr[1][1], rc.zi[1][1]};
+    const Cplx c0 = {rc.cr[0], rc.ci[0]}, c1 = {rc.cr[1], rc.ci[1]};
     for (int u = threadIdx.x; u < H; u += blockDim.x) {
         float* t0 = P0 + (size_t)u * fp;
         float* t1 = P1 + (size_t)u * fp;
@@ -83,8 +84,9 @@ __global__ void __launch_bounds__(256) rec_cols_kernel(const __grid_constant__ R
     float* A = L.fields + (moments ? D.field_off : D.self_off);
     float* Fu = A + pl;
     float* Fv = A + 2 * pl;
-    const Cplx z0 = {L.rc.zr[0][0], L.rc.zi[0][0]}, z1 = {L.rc.zr[0][1], L.rc.zi[0][1]};
-    const Cplx c0 = {L.rc.cr[0], L.rc.ci[0]}, c1 = {L.rc.cr[1], L.rc.ci[1]};
+    const RecCoef& rc = moments ? D.rc : D.rc_self;
+    const Cplx z0 = {rc.zr[0][0], rc.zi[0][0]}, z1 = {rc.zr[0][1], rc.zi[0][1]};
+    const Cplx c0 = {rc.cr[0], rc.ci[0]}, c1 = {rc.cr[1], rc.ci[1]};
     const int lane = threadIdx.x & 31;
     const long long poff = moments ? D.partial_off : D.sxx_off;
     // whole warps walk the columns so that each warp's partial covers 32 consecutive columns

@@ -39,7 +39,7 @@ EXPORTS = (
     "itc_run", "itc_run_fields", "itc_run_iterate", "itc_run_fields_range", "itc_run_iterate_range",
     "itc_run_pipelined", "itc_backward", "itc_fields_noalloc", "itc_autotune", "itc_plan_classes",
     "itc_plan_class", "itc_plan_configure", "itc_params_parzen", "itc_segment",
-    "itc_plan_padded_offset", "itc_chamfer",
+    "itc_plan_padded_offset", "itc_chamfer", "itc_run_staged",
 )
 
 
@@ -128,6 +128,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
         L.itc_run_pipelined.argtypes = [_P, _P, _P, _P, _P, _SZ, _P, _P, ctypes.c_int]
         L.itc_autotune.restype = ctypes.c_int
         L.itc_autotune.argtypes = [_P, _P, _P, _SZ, ctypes.c_int, _P]
+        L.itc_run_staged.restype = ctypes.c_int
+        L.itc_run_staged.argtypes = [_P, _P, _P, _P, _SZ, _P, _P, _P, _SZ, ctypes.c_int, _P, _P]
         L.itc_plan_padded_offset.restype = ctypes.c_longlong
         L.itc_plan_padded_offset.argtypes = [_P, ctypes.c_int]
         L.itc_chamfer.restype = ctypes.c_int
@@ -423,6 +425,19 @@ def segment(plan: Plan, W, labels=None, stream=None):
     _check(lib().itc_segment(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), labels.data_ptr(), _stream(stream)),
            "itc_segment")
     return labels
+
+
+def run_staged(plan: Plan, host_buf, dev_buf, W, stats=None, chunks: int = 8, stream=None, copy_stream=None):
+    """itc_run_staged: copy the images from the pinned host tensor ``host_buf`` into ``dev_buf``
+    (the buffer the plan's images live in) range by range on ``copy_stream`` while the fields and
+    iterations of the ranges already copied run on ``stream``."""
+    nbytes = dev_buf.numel() * dev_buf.element_size()
+    if host_buf.numel() * host_buf.element_size() != nbytes:
+        raise ValueError("host and device image buffers differ in size")
+    _check(lib().itc_run_staged(plan.host_ptr, plan.dev.data_ptr(), host_buf.data_ptr(), dev_buf.data_ptr(), nbytes,
+                                W.data_ptr(), _ptr(stats), plan.ws.data_ptr(), plan.ws.numel(), int(chunks),
+                                _stream(stream), _stream(copy_stream) if copy_stream is not None else None),
+           "itc_run_staged")
 
 
 def run_fields(plan: Plan, stream=None):

@@ -273,3 +273,12 @@ def test_recursive_flag_checks(L):
     assert L.itc_plan_class(hp, 0, None, None, None, None, ctypes.byref(st), None, None) == 0 and st.value == 3
     assert L.itc_backward(hp, 0x100000, 0x1000, None, None, None, None, 0x4000, ws, None) == itc.ITC_ERR_UNSUPPORTED
     assert L.itc_plan_configure(hp, 0x100000, 0, 64, 0, 0, None) == itc.ITC_ERR_UNSUPPORTED
+
+
+def test_staged_run_checks_the_image_buffer(L):
+    rc, buf, ws = _plan(L, [(64, 64), (40, 50)], [4, 4], _p(iters=2))
+    hp = ctypes.cast(buf, ctypes.c_void_p)
+    # images sit at 0x10000 and 0x20000 (see _plan); a buffer that does not hold both is refused
+    assert L.itc_run_staged(hp, 0x100000, 0x1000, 0x10000, 0x8000, 0x2000, None, 0x4000, ws, 2, None, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_run_staged(hp, 0x100000, 0x1000, 0x10000, 0x20000, 0x2000, None, 0x4000, ws, 0, None, None) == itc.ITC_ERR_INVALID_ARG
+    assert L.itc_run_staged(hp, 0x100000, None, 0x10000, 0x20000, 0x2000, None, 0x4000, ws, 2, None, None) == itc.ITC_ERR_INVALID_ARG

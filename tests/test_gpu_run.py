@@ -235,6 +235,32 @@ def test_pipelined_and_range_runs_equal_plain_run():
         assert np.array_equal(W, outs[0][0]) and st == outs[0][1]
 
 
+def test_staged_run_from_host_equals_plain_run():
+    """itc_run_staged (image bytes copied range by range on a second stream while earlier ranges
+    compute) gives the codebooks and stats of itc_run on device-resident images."""
+    import torch
+    images, Ms, sig = synth.c3_batch(40, start=700)
+    W0s = [synth.init_codebook(synth.rng_for(3, 60_000 + i), im.astype(np.float32), int(m))
+           for i, (im, m) in enumerate(zip(images, Ms))]
+    params = [itc.make_params(float(s), 3.0, 12) for s in sig]
+    buf, views = itc.pack_images(images, "cuda")
+    host = buf.cpu().pin_memory()
+    plan = itc.Plan(views, Ms, params)
+    W = plan.pack_W(W0s)
+    st = itc.new_stats(len(images), W.device)
+    itc.run(plan, W, st)
+    torch.cuda.synchronize()
+    ref = (W.cpu().numpy().copy(), st.cpu().numpy().tobytes())
+    side = torch.cuda.Stream()
+    for chunks in (1, 3, 8):
+        buf.zero_()
+        W2 = plan.pack_W(W0s)
+        st2 = itc.new_stats(len(images), W.device)
+        itc.run_staged(plan, host, buf, W2, st2, chunks=chunks, copy_stream=side)
+        torch.cuda.synchronize()
+        assert np.array_equal(W2.cpu().numpy(), ref[0]) and st2.cpu().numpy().tobytes() == ref[1], chunks
+
+
 def _fields_and_run(plan, W0s, iters_plan):
     import torch
     itc.run_fields(plan)

@@ -184,7 +184,7 @@ size_t plan_layout(int B, size_t* desc_off, size_t* ints_off, size_t* tmap_off =
     const size_t d = align_up((size_t)B * sizeof(ImageDesc), 256);
     // per class an image list and a tile prefix (an image is in at most two classes: its
     // fields class and its self-overlap class), then the backward image order
-    const size_t n = align_up((size_t)(5 * (size_t)B + kMaxClasses + 2) * sizeof(int), 256);
+    const size_t n = align_up((size_t)(6 * (size_t)B + kMaxClasses + 2) * sizeof(int), 256);
     const size_t m = align_up((size_t)B * sizeof(CUtensorMap), 256);
     if (desc_off) *desc_off = h;
     if (ints_off) *ints_off = h + d;
@@ -556,8 +556,19 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         });
         for (int b = 0; b < B; ++b) ints[io++] = order[b];
     }
+    // iterations: one CTA per image, the images with the most pair work (iters x M^2) first, so
+    // that the long ones do not start last
+    const int run_off = io;
+    {
+        std::vector<int> order(B);
+        for (int b = 0; b < B; ++b) order[b] = b;
+        auto cost = [&](int b) { return (double)(descs[b].iters + 1) * descs[b].M * descs[b].M; };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+        for (int b = 0; b < B; ++b) ints[io++] = order[b];
+    }
     h->nints = io;
     h->bwd_order_off = bwd_off;
+    h->run_order_off = run_off;
     h->bwd_tiles = bwd;
 
     // workspace: [fields][S_XX partials][per-image backward scalars]
@@ -845,8 +856,17 @@ int itc_plan_classes(const void* plan_host) {
     return h ? h->ncls : ITC_ERR_INVALID_ARG;
 }
 
+static int run_iterate_images(const void* plan_host, const void* plan_dev, int b0, int b1, bool whole, float* W,
+                              itc_stats* stats, void* ws, size_t ws_bytes, void* stream);
+
 int itc_run_iterate_range(const void* plan_host, const void* plan_dev, int b0, int b1, float* W, itc_stats* stats,
                           void* ws, size_t ws_bytes, void* stream) {
+    return run_iterate_images(plan_host, plan_dev, b0, b1, false, W, stats, ws, ws_bytes, stream);
+}
+
+// images [b0, b1) in order, or (whole) every image of the plan in the plan's iteration order
+static int run_iterate_images(const void* plan_host, const void* plan_dev, int b0, int b1, bool whole, float* W,
+                              itc_stats* stats, void* ws, size_t ws_bytes, void* stream) {
     const PlanHeader* h = plan_of(plan_host);
     if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
     if (b0 < 0 || b1 > h->B || b0 > b1) return ITC_ERR_INVALID_ARG;
@@ -865,6 +885,7 @@ int itc_run_iterate_range(const void* plan_host, const void* plan_dev, int b0, i
     R.absolute = 0;
     R.final_eval = 1;
     R.img_base = b0;
+    if (whole && b0 == 0 && b1 == h->B) R.order = reinterpret_cast<const int*>(pd + h->ints_off) + h->run_order_off;
     for (int nd = 2; nd <= 3; ++nd) {
         if (!(h->ndim_mask & (1 << nd))) continue;
         const int rc = cuda_status(launch_run(R, b1 - b0, h->max_M, h->max_dim, reinterpret_cast<cudaStream_t>(stream), nd));
@@ -883,7 +904,7 @@ int itc_run_iterate(const void* plan_host, const void* plan_dev, float* W, itc_s
                     size_t ws_bytes, void* stream) {
     const PlanHeader* h = plan_of(plan_host);
     if (!h) return ITC_ERR_INVALID_ARG;
-    return itc_run_iterate_range(plan_host, plan_dev, 0, h->B, W, stats, ws, ws_bytes, stream);
+    return run_iterate_images(plan_host, plan_dev, 0, h->B, true, W, stats, ws, ws_bytes, stream);
 }
 
 int itc_run_pipelined(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,

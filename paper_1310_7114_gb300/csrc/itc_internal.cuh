@@ -109,6 +109,7 @@ struct PlanHeader {
     long long ws_scal_off;      // bytes: per-image backward scalars (4 doubles each)
     long long bwd_tiles;        // backward pixel tiles over all images
     int bwd_order_off;          // offset (ints) of the backward image order (B ints, most tiles first)
+    int run_order_off;          // offset (ints) of the iteration order (B ints, most pair work first)
     long long tmap_off;         // bytes from plan start to CUtensorMap[B] (input tiles)
     long long pad_floats;       // sum H*fpitch (padded per-pixel layout)
     int has_recursive;          // some class computes its fields by recursion
@@ -159,6 +160,7 @@ struct RunLaunch {
     int absolute;
     int final_eval;             // 1: stats at the final W (itc_run); 0: stats at W_in (itc_step)
     int img_base;               // image of blockIdx.x == 0 (image sub-ranges)
+    const int* order;           // whole batch: image of each CTA, costliest first (else img_base + blockIdx.x)
 };
 
 struct BackwardLaunch {

@@ -98,7 +98,7 @@ struct Img {
 template <int NPER, int ND>
 __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_constant__ RunLaunch L) {
     using P = typename std::conditional<ND == 2, float2, float4>::type;
-    const int img = L.img_base + blockIdx.x;
+    const int img = L.order ? __ldg(L.order + blockIdx.x) : L.img_base + blockIdx.x;
     const ImageDesc& Dg = L.descs ? L.descs[img] : L.one;
     if (Dg.ndim != ND) return;   // a mixed plan launches once per dimension
     Img D;

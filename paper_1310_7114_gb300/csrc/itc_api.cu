@@ -501,6 +501,7 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         ghoff += (long long)d.H * d.W;
         d.bwd_tile_begin = bwd;
         bwd += d.bwd_tiles_u * d.bwd_tiles_v;
+        h->max_bwd_tiles = std::max(h->max_bwd_tiles, d.bwd_tiles_u * d.bwd_tiles_v);
         if (d.M > maxM) maxM = d.M;
         h->max_dim[0] = d.H > h->max_dim[0] ? d.H : h->max_dim[0];
         h->max_dim[1] = d.W > h->max_dim[1] ? d.W : h->max_dim[1];
@@ -1031,7 +1032,7 @@ int itc_backward(const void* plan_host, const void* plan_dev, const float* W, co
     L.scal = reinterpret_cast<double*>(w + h->ws_scal_off);
     L.bwd_order = reinterpret_cast<const int*>(pd + h->ints_off) + h->bwd_order_off;
     L.B = h->B;
-    return cuda_status(launch_backward(L, h->B, h->max_M, h->bwd_tiles,
+    return cuda_status(launch_backward(L, h->B, h->max_M, h->bwd_tiles, h->max_bwd_tiles,
                                        reinterpret_cast<cudaStream_t>(stream)));
 }
 

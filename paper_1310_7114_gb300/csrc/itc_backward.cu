@@ -209,7 +209,9 @@ constexpr int kChunk = 64;   // codebooks staged per round in the pixel kernel
 // every thread accumulates a 4 x 4 block of pixels in l order (deterministic, no atomics).  In
 // 3-D the g factor depends on each pixel's gray level and is applied per pixel and codebook.
 __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_constant__ BackwardLaunch L) {
-    const int img = __ldg(L.bwd_order + blockIdx.x);
+    // split CTAs per image (few large images): CTA s of an image takes its tiles s, s + split, ...
+    const int split = L.split;
+    const int img = __ldg(L.bwd_order + blockIdx.x / split), part = blockIdx.x % split;
     const ImageDesc& D = L.descs[img];
     const int M = D.M, nd = D.ndim, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int H = D.H, Wd = D.W, G = D.G, fpitch = D.fpitch, tiles_v = D.bwd_tiles_v;
@@ -242,7 +244,8 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
     __syncthreads();
 
     const int pr = (tid >> 4) * 4, pc = (tid & 15) * 4;   // this thread's 4 x 4 block
-    for (int t = 0; t < ntiles; ++t) {
+    if (part >= ntiles) return;
+    for (int t = part; t < ntiles; t += split) {
         const int u0 = (t / tiles_v) * kBwdTileH, v0 = (t % tiles_v) * kBwdTileW;
         // field values of this thread's block, loaded first so their latency overlaps the stamp
         float4 a4[4];
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
 
 }  // namespace
 
-cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles,
+cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles, int max_image_tiles,
                             cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
     const size_t smem1 = (size_t)max_M * kCodebookSmemFloats * sizeof(float);
@@ -375,7 +378,20 @@ cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long
     const size_t smem2 = (size_t)max_M * 7 * sizeof(int);   // positions, sites, tile list
     e = cudaFuncSetAttribute(bwd_pixels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
-    bwd_pixels_kernel<<<(unsigned)B, kThreads, smem2, s>>>(L);
+    // one CTA per image when the batch fills the GPU; otherwise each image's tiles are shared out
+    // over `split` CTAs (a single large image would else run on one SM)
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_pixels_kernel, kThreads, smem2)) != cudaSuccess)
+        return e;
+    const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    long long split = (slots + B - 1) / B;
+    if (split > max_image_tiles) split = max_image_tiles;
+    if (split < 1) split = 1;
+    BackwardLaunch L2 = L;
+    L2.split = (int)split;
+    bwd_pixels_kernel<<<(unsigned)(B * split), kThreads, smem2, s>>>(L2);
     return cudaGetLastError();
 }
 

@@ -108,6 +108,7 @@ struct PlanHeader {
     long long nints;
     long long ws_scal_off;      // bytes: per-image backward scalars (4 doubles each)
     long long bwd_tiles;        // backward pixel tiles over all images
+    int max_bwd_tiles;          // most backward pixel tiles of one image
     int bwd_order_off;          // offset (ints) of the backward image order (B ints, most tiles first)
     int run_order_off;          // offset (ints) of the iteration order (B ints, most pair work first)
     long long tmap_off;         // bytes from plan start to CUtensorMap[B] (input tiles)
@@ -175,6 +176,7 @@ struct BackwardLaunch {
     double* scal;               // per-image scalars in workspace: S_XW, S_WW, S_XX, gD
     const int* bwd_order;       // image of each backward pixel CTA (B ints, most tiles first)
     int B;
+    int split;                  // pixel-pass CTAs per image (set at launch)
 };
 
 constexpr int kChamferMaxW = 1024;   // chamfer rows: 32 lanes x 32 segments of registers
@@ -223,6 +225,6 @@ cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_d
 cudaError_t launch_recursive(const RecursiveLaunch& L, int nimg, cudaStream_t s);
 cudaError_t launch_chamfer(const ChamferLaunch& L, int max_W, cudaStream_t s);
 cudaError_t launch_segment(const SegmentLaunch& L, int B, int max_M, cudaStream_t s);
-cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles,
+cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles, int max_image_tiles,
                             cudaStream_t s);
 }  // namespace itc

@@ -10,7 +10,8 @@
 //   g * x  = Re sum_t c_t (s0 + r0),     (d g) * x = Re sum_t c_t (r1 - s1)     (d = offset)
 // with zero states at the ends (no data outside the image), so the kernel is untruncated.
 //
-// Pass along v (one thread per row): T = g_v * h, T_v = (d g)_v * h into two scratch planes (the
+// Pass along v (one lane per row, rows staged through shared memory in 32 x 32 tiles so that
+// global accesses are coalesced): T = g_v * h, T_v = (d g)_v * h into two scratch planes (the
 // causal part is stored, the anticausal part added).  Pass along u (one thread per column, so
 // warps read and write whole row segments): A = g_u * T, F_u = (d g)_u * T, F_v = g_u * T_v into
 // the field planes, same order; the column pass also sums h A per column (FP64) and each warp's
@@ -39,7 +40,12 @@ __device__ __forceinline__ const ImageDesc& rec_image(const RecursiveLaunch& L) 
     return L.descs[__ldg(L.img_list + L.pos_base + blockIdx.x)];
 }
 
-__global__ void __launch_bounds__(256) rec_rows_kernel(const __grid_constant__ RecursiveLaunch L) {
+// Along v: a warp takes 32 rows at a time, one lane per row, and walks them in 32 x 32 tiles
+// staged in shared memory (rows of 33 floats), so every global load and store is a coalesced row
+// segment while each lane runs its row's recursion on the staged tile.
+constexpr int kRecRowWarps = 3;   // three 32 x 33 float tiles per warp: 38 KB of static shared memory
+
+__global__ void __launch_bounds__(32 * kRecRowWarps) rec_rows_kernel(const __grid_constant__ RecursiveLaunch L) {
     const ImageDesc& D = rec_image(L);
     const int H = D.H, W = D.W, fp = D.fpitch;
     const bool moments = L.mode == 0;
@@ -48,28 +54,80 @@ __global__ void __launch_bounds__(256) rec_rows_kernel(const __grid_constant__ R
     const RecCoef& rc = moments ? D.rc : D.rc_self;
     const Cplx z0 = {rc.zr[1][0], rc.zi[1][0]}, z1 = {rc.zr[1][1], rc.zi[1][1]};
     const Cplx c0 = {rc.cr[0], rc.ci[0]}, c1 = {rc.cr[1], rc.ci[1]};
-    for (int u = threadIdx.x; u < H; u += blockDim.x) {
-        float* t0 = P0 + (size_t)u * fp;
-        float* t1 = P1 + (size_t)u * fp;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ float sx[kRecRowWarps][32][33], so0[kRecRowWarps][32][33], so1[kRecRowWarps][32][33];
+    float (*X)[33] = sx[wid];
+    float (*O0)[33] = so0[wid];
+    float (*O1)[33] = so1[wid];
+    const int ntc = (W + 31) / 32;
+    for (int r0 = wid * 32; r0 < H; r0 += 32 * kRecRowWarps) {
+        const int nr = min(32, H - r0);
+        auto load_x = [&](int cb) {   // input tile: rows r0.., columns cb..
+            for (int rr = 0; rr < nr; ++rr) {
+                const int v = cb + lane;
+                X[rr][lane] = v < W ? pixel(D, r0 + rr, v) : 0.f;
+            }
+            __syncwarp();
+        };
+        // causal: tiles left to right
         Cplx a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, m0 = {0.f, 0.f}, m1 = {0.f, 0.f};   // s0, s1 per term
-        for (int v = 0; v < W; ++v) {
-            const float x = pixel(D, u, v);
-            m0 = cmul(z0, cadd(m0, a0));
-            m1 = cmul(z1, cadd(m1, a1));
-            a0 = cmul(z0, a0); a0.r += x;
-            a1 = cmul(z1, a1); a1.r += x;
-            t0[v] = re_mul(c0, a0) + re_mul(c1, a1);
-            if (moments) t1[v] = -(re_mul(c0, m0) + re_mul(c1, m1));
+        for (int tc = 0; tc < ntc; ++tc) {
+            const int cb = tc * 32, nc = min(32, W - cb);
+            load_x(cb);
+            if (lane < nr) {
+                for (int cc = 0; cc < nc; ++cc) {
+                    const float x = X[lane][cc];
+                    m0 = cmul(z0, cadd(m0, a0));
+                    m1 = cmul(z1, cadd(m1, a1));
+                    a0 = cmul(z0, a0); a0.r += x;
+                    a1 = cmul(z1, a1); a1.r += x;
+                    O0[lane][cc] = re_mul(c0, a0) + re_mul(c1, a1);
+                    if (moments) O1[lane][cc] = -(re_mul(c0, m0) + re_mul(c1, m1));
+                }
+            }
+            __syncwarp();
+            for (int rr = 0; rr < nr; ++rr) {
+                if (lane < nc) {
+                    P0[(size_t)(r0 + rr) * fp + cb + lane] = O0[rr][lane];
+                    if (moments) P1[(size_t)(r0 + rr) * fp + cb + lane] = O1[rr][lane];
+                }
+            }
+            __syncwarp();
         }
+        // anticausal: tiles right to left; x[v + 1] of a tile's last column is the first column
+        // of the tile to its right
         a0 = a1 = m0 = m1 = Cplx{0.f, 0.f};   // r0, r1 per term
-        for (int v = W - 1; v >= 0; --v) {
-            const float xn = v + 1 < W ? pixel(D, u, v + 1) : 0.f;
-            m0 = cmul(z0, cadd(cadd(m0, a0), Cplx{xn, 0.f}));
-            m1 = cmul(z1, cadd(cadd(m1, a1), Cplx{xn, 0.f}));
-            a0 = cmul(z0, cadd(a0, Cplx{xn, 0.f}));
-            a1 = cmul(z1, cadd(a1, Cplx{xn, 0.f}));
-            t0[v] += re_mul(c0, a0) + re_mul(c1, a1);
-            if (moments) t1[v] += re_mul(c0, m0) + re_mul(c1, m1);
+        float xnext = 0.f;
+        for (int tc = ntc - 1; tc >= 0; --tc) {
+            const int cb = tc * 32, nc = min(32, W - cb);
+            load_x(cb);
+            for (int rr = 0; rr < nr; ++rr) {
+                if (lane < nc) {
+                    O0[rr][lane] = P0[(size_t)(r0 + rr) * fp + cb + lane];
+                    if (moments) O1[rr][lane] = P1[(size_t)(r0 + rr) * fp + cb + lane];
+                }
+            }
+            __syncwarp();
+            if (lane < nr) {
+                for (int cc = nc - 1; cc >= 0; --cc) {
+                    const float xn = cc + 1 < nc ? X[lane][cc + 1] : xnext;
+                    m0 = cmul(z0, cadd(cadd(m0, a0), Cplx{xn, 0.f}));
+                    m1 = cmul(z1, cadd(cadd(m1, a1), Cplx{xn, 0.f}));
+                    a0 = cmul(z0, cadd(a0, Cplx{xn, 0.f}));
+                    a1 = cmul(z1, cadd(a1, Cplx{xn, 0.f}));
+                    O0[lane][cc] += re_mul(c0, a0) + re_mul(c1, a1);
+                    if (moments) O1[lane][cc] += re_mul(c0, m0) + re_mul(c1, m1);
+                }
+                xnext = X[lane][0];
+            }
+            __syncwarp();
+            for (int rr = 0; rr < nr; ++rr) {
+                if (lane < nc) {
+                    P0[(size_t)(r0 + rr) * fp + cb + lane] = O0[rr][lane];
+                    if (moments) P1[(size_t)(r0 + rr) * fp + cb + lane] = O1[rr][lane];
+                }
+            }
+            __syncwarp();
         }
     }
 }
@@ -142,7 +200,7 @@ __global__ void __launch_bounds__(256) rec_cols_kernel(const __grid_constant__ R
 
 cudaError_t launch_recursive(const RecursiveLaunch& L, int nimg, cudaStream_t s) {
     if (nimg <= 0) return cudaSuccess;
-    rec_rows_kernel<<<nimg, 256, 0, s>>>(L);
+    rec_rows_kernel<<<nimg, 32 * kRecRowWarps, 0, s>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     rec_cols_kernel<<<nimg, 256, 0, s>>>(L);

@@ -269,6 +269,12 @@ def run_ours(args, rank, world, local_rank):
     plan = itc.Plan(views, Ms, params, ndims=ndims, Gs=Gs)
     # per sigma class: fields tile height, persistent CTAs per SM, staging -- timed on this batch
     tuning = plan.classes() if args.no_tune else plan.autotune(reps=3)
+    if args.fields_ctas is not None:
+        # leave room on every SM for the iteration CTAs of the pipelined step
+        for c, info in enumerate(tuning):
+            if info["staging"] == "tma":
+                plan.configure(c, info["tile_h"], args.fields_ctas, "tma")
+        tuning = plan.classes()
     W0 = plan.pack_W(W0s)
     W = W0.clone()
     stats = itc.new_stats(B, dev)
@@ -425,6 +431,43 @@ def run_ours(args, rank, world, local_rank):
         cham = c0.elapsed_time(c1) / args.steps
         del cbuf
 
+    # Algorithm 1's own stopping test (step 11, theta = 0: stop once no codebook moves), same
+    # images and step otherwise; the codebooks equal those of the full iteration count
+    stop = None
+    if WORKLOADS[name]["iters"] > 0:
+        pparams = [itc.make_params(p["sigma"], 3.0, p["iters"], flags=itc.ITC_STOP_ON_FIXED) for p in pk]
+        pplan = itc.Plan(views, Ms, pparams, ndims=ndims, Gs=Gs)
+        for c, info in enumerate(tuning):   # the tuned fields configuration of the main plan
+            if info["staging"] in ("tma", "plain") and pplan.classes()[c]["staging"] in ("tma", "plain"):
+                pplan.configure(c, info["tile_h"], info["ctas_per_sm"], info["staging"])
+        pW = pplan.pack_W(W0s)
+        pst = itc.new_stats(B, dev)
+        pgW = torch.empty_like(pW)
+
+        def stop_step():
+            pW.copy_(W0)
+            itc.run(pplan, pW, pst)
+            itc.backward(pplan, pW, grad_W=pgW, grad_h=gh)
+
+        for _ in range(args.warmup):
+            stop_step()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            stop_step()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / args.steps
+        done = itc.stats_to_numpy(pst)["iters_done"]
+        same = bool(torch.equal(pW, W))
+        stop = {"value": world * B / (pms / 1000.0), "unit": "images/s", "ms_per_step": pms,
+                "iters_done_mean": float(np.mean(done)), "iters_done_max": int(np.max(done)),
+                "codebooks_equal_full_run": same,
+                "note": "ITC_STOP_ON_FIXED: Algorithm 1 step 11 with theta = 0; not the headline (the workload "
+                        "fixes the iteration count)"}
+        del pplan, pW, pst, pgW
+
     # the paper's width schedule of Sec. 4 (omega = sqrt(N/M)/2, xi = omega/2 per image) on the
     # same images: its widths are far beyond the masks, so the fields come from the recursive
     # filters; fields + iterations (the adjoint needs mask fields), timed on their own
@@ -514,6 +557,7 @@ def run_ours(args, rank, world, local_rank):
         "segment": segment_report(images, seg_ms, world, B, peaks, peak_src),
         "chamfer": chamfer_report(images, cham, world, B, peaks, peak_src),
         "schedule": sched,
+        "stop_on_fixed": stop,
         "phases_ms": {"fields": f_avg, "iterate": statistics.mean(i_ms), "backward": statistics.mean(b_ms),
                       "note": "phases run in sequence in a separate timed loop; the headline step overlaps "
                               f"fields and iterations over {args.chunks} image ranges on two streams"},
@@ -593,6 +637,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default fields configuration")
     ap.add_argument("--e2e-chunks", type=int, default=4, help="image ranges of the staged end-to-end step")
     ap.add_argument("--no-schedule", action="store_true", help="skip the Sec. 4 width-schedule timing")
+    ap.add_argument("--fields-ctas", type=int, default=None,
+                    help="persistent fields CTAs per SM after tuning (room for overlapping iterations)")
     ap.add_argument("--chunks", type=int, default=1, help="image ranges of the pipelined fields/iterations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else max(args.warmup, 1)

@@ -250,6 +250,16 @@ def alu_roofline(images, pk, ndims, fields_ms, clocks, dev):
                     "tiles and windows that hold no data are skipped, so this may exceed what executes"}
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (the slowest rank's time); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1310_7114_gb300 import build, itc
@@ -327,11 +337,7 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.steps):
         step_phases(ev[k])
     torch.cuda.synchronize()
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
     ms_step = ms / args.steps
     f_ms = [e[0].elapsed_time(e[1]) for e in ev]
     i_ms = [e[1].elapsed_time(e[2]) for e in ev]
@@ -392,11 +398,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     h2d = buf.numel() * buf.element_size() + W0.numel() * 4
     d2h = 2 * W.numel() * 4 + stats.numel()
 

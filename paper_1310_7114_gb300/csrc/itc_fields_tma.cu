@@ -202,25 +202,29 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
     // whose previous tile (n - NST) has finished both passes by the time the copy is started
     // called by all of warp 0: remember the cursor's tile for its stage, lane 0 starts the copy
     uint32_t inflight = 0;   // (thread 0) bit b: a copy into stage b has been started, not yet waited for
-    TileCursor cur = {};
+    // the cursor lives in shared memory and is advanced by thread 0 alone (it costs the other
+    // threads no registers)
+    __shared__ TileCursor s_cur;
     auto issue = [&](int buf, bool copy) {
         if (tid == 0) {
-            const int tv = cur.local % cur.tv, tu = cur.local / cur.tv;
-            const CUtensorMap* map = L.descs ? L.tmaps + cur.img : &L.tmap_one;
-            s_img[buf] = cur.img;
-            s_local[buf] = cur.local;
+            const int tv = s_cur.local % s_cur.tv, tu = s_cur.local / s_cur.tv;
+            const CUtensorMap* map = L.descs ? L.tmaps + s_cur.img : &L.tmap_one;
+            s_img[buf] = s_cur.img;
+            s_local[buf] = s_cur.local;
             if (copy) {
                 mbar_expect_tx(&bar[buf], BOX_BYTES);
                 tma_load_2d(stage0 + buf * STAGE_BYTES, map, tv * TW - RA, tu * TH - R, &bar[buf]);
                 inflight |= 1u << buf;
             }
+            s_cur.advance(L);
         }
-        cur.advance(L);
     };
 
     int t = t_lo;
     if (tid < 32 && t_lo < t_hi) {
-        cur.start(L, t_lo);
+        TileCursor c0 = {};
+        c0.start(L, t_lo);   // the whole warp: the first lookup is a warp search
+        if (tid == 0) s_cur = c0;
         for (int b = 0; b < NST; ++b)
             if (t + b < t_hi)
                 // the test hook starts no copy for the first tile of CTA 0: its wait cannot end

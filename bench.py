@@ -36,7 +36,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per pixel of the fields pass, from one ncu capture of the C3 workload
 # with 1024 images (profiles/fields_tma_kernel_c3_1024.md), valid only for the kernel source it was
 # taken on (sha256 prefix below); scaled to a launch by its pixel count.
-FIELDS_TRAFFIC = {"workload": "c3", "bytes_per_pixel": 1008.5e6 / 86358723, "source_sha256": "71a6ebf2c1b65b7a",
+FIELDS_TRAFFIC = {"workload": "c3", "bytes_per_pixel": 1040.9e6 / 86358723, "source_sha256": "0a12926a67c1d526",
                   "source": "paper_1310_7114_gb300/csrc/itc_fields_tma.cu"}
 
 
@@ -398,9 +398,64 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    e2e_single_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     h2d = buf.numel() * buf.element_size() + W0.numel() * 4
     d2h = 2 * W.numel() * 4 + stats.numel()
+
+    # the same per step, as a stream of batches would run it: two image buffers and two plans, the
+    # copies of step k+1 (copy stream) overlapping the work of step k; every step still copies its
+    # inputs from pinned host memory and reads its results back
+    buf2, views2 = itc.pack_images(images, dev)
+    plan2 = itc.Plan(views2, Ms, params, ndims=ndims, Gs=Gs)
+    for c, info in enumerate(tuning):
+        if info["staging"] in ("tma", "plain") and plan2.classes()[c]["staging"] in ("tma", "plain"):
+            plan2.configure(c, info["tile_h"], info["ctas_per_sm"], info["staging"])
+    sets = [(plan, buf, W, stats, gW, gh), (plan2, buf2, torch.empty_like(W), itc.new_stats(B, dev),
+                                            torch.empty_like(gW), torch.empty_like(gh))]
+    host_out = [(out_W, out_gW, out_st),
+                (torch.empty_like(out_W).pin_memory(), torch.empty_like(out_gW).pin_memory(),
+                 torch.empty_like(out_st).pin_memory())]
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    released = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def stage(k):   # the image copy of step k, on the copy stream, once step k-2 has released the buffer
+        _, bk, Wk, _, _, _ = sets[k % 2]
+        copy_stream.wait_event(released[k % 2])
+        with torch.cuda.stream(copy_stream):
+            bk.copy_(host_buf, non_blocking=True)
+            Wk.copy_(host_W0, non_blocking=True)
+        copied[k % 2].record(copy_stream)
+
+    def compute(k):
+        pk_, _, Wk, stk, gWk, ghk = sets[k % 2]
+        stream.wait_event(copied[k % 2])
+        itc.run(pk_, Wk, stk)
+        itc.backward(pk_, Wk, grad_W=gWk, grad_h=ghk)
+        oW, ogW, ost = host_out[k % 2]
+        oW.copy_(Wk, non_blocking=True)
+        ogW.copy_(gWk, non_blocking=True)
+        ost.copy_(stk, non_blocking=True)
+        released[k % 2].record(stream)   # the buffers of this step may be refilled after the read-back
+
+    def stream_steps(n):
+        stage(0)
+        for k in range(n):
+            if k + 1 < n:
+                stage(k + 1)
+            compute(k)
+
+    for b_ in range(2):
+        released[b_].record(stream)
+    stream_steps(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    stream_steps(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    same = bool(torch.equal(sets[0][2], sets[1][2]))
+    del plan2, buf2, sets
 
     # the same work launched image by image (one plan per image), on a prefix of the batch
     # segmentation of every image by its final codebook (outside the step), its own timing
@@ -572,9 +627,13 @@ def run_ours(args, rank, world, local_rank):
         "roofline_alu": alu_roofline(images, pk, ndims, f_avg, clk.summary(), dev),
         "e2e": {"value": world * B / (e2e_ms / 1000.0), "unit": "images/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
-                "path": "itc_run_staged (image ranges copied on a second stream while the fields of earlier ranges run, "
-                        f"{args.e2e_chunks} ranges) + itc_backward through the C ABI; inputs from pinned host "
-                        "memory; W, grad_W, stats back to the host"},
+                "pipeline": "two image buffers and plans: the host-to-device copy of step k+1 runs on a copy "
+                            "stream while step k computes (itc_run + itc_backward); both buffers give the same "
+                            f"codebooks: {same}",
+                "single_buffer": {"value": world * B / (e2e_single_ms / 1000.0), "ms_per_step": e2e_single_ms,
+                                  "path": "itc_run_staged: the copy overlaps only this step's fields"},
+                "path": "inputs from pinned host memory every step (images and codebooks), results (W, grad_W, "
+                        "stats) back to pinned host memory every step, through the C ABI"},
         "graph": ({"value": world * B / (graph_ms / 1000.0), "unit": "images/s", "ms_per_step": graph_ms,
                    "note": "the same step captured in one CUDA graph and replayed"}
                   if isinstance(graph_ms, float) else {"error": graph_ms}),

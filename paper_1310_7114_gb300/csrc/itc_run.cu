@@ -24,6 +24,8 @@
 namespace itc {
 namespace {
 
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -117,6 +119,11 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
     const int M = D.M, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smraw[];
     P* sw = reinterpret_cast<P*>(smraw);   // M positions
+    // the same positions by axis (even length), so that the pair sums read two j at a time
+    const int Mp = (M + 1) & ~1;
+    float* sx = reinterpret_cast<float*>(smraw + (size_t)M * sizeof(P));
+    float* sy = sx + Mp;
+    float* sz = sy + Mp;
     __shared__ float red[3 * (kRunThreads / 32)];
     __shared__ double s_sxx;
 
@@ -137,6 +144,9 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
         w.y = Win[k * ND + 1];
         if constexpr (ND == 3) { w.z = Win[k * ND + 2]; w.w = 0.f; }
         sw[k] = w;
+        sx[k] = w.x;
+        sy[k] = w.y;
+        if constexpr (ND == 3) sz[k] = w.z;
     }
     __syncthreads();
     const double sxx = s_sxx;
@@ -168,41 +178,47 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
             float f[ND];
 #pragma unroll
             for (int i = 0; i < ND; ++i) f[i] = __ldg(D.A + (i + 1) * D.plane + o);
-            // pair sums over every j, two interleaved accumulators
-            float s0 = 0.f, s1 = 0.f, e0[ND], e1[ND];
-#pragma unroll
-            for (int i = 0; i < ND; ++i) { e0[i] = 0.f; e1[i] = 0.f; }
+            // pair sums over every j in order, two j per packed FP32 operation (the .x lanes take the
+            // even j, the .y lanes the odd j; summed at the end)
+            const float2 nk0 = f2(-wk.x, -wk.x), nk1 = f2(-wk.y, -wk.y);
+            const float2 cc0 = f2(c0, c0), cc1 = f2(c1, c1), cc2 = f2(c2, c2);
+            float2 nk2 = f2(0.f, 0.f);
+            if constexpr (ND == 3) nk2 = f2(-wk.z, -wk.z);
+            float2 sp = f2(0.f, 0.f), ep0 = f2(0.f, 0.f), ep1 = f2(0.f, 0.f), ep2 = f2(0.f, 0.f);
             int j = 0;
             for (; j + 1 < M; j += 2) {
-                const P wa = sw[j], wb = sw[j + 1];
-                const float da0 = wa.x - wk.x, da1 = wa.y - wk.y;
-                const float db0 = wb.x - wk.x, db1 = wb.y - wk.y;
-                float xa = da0 * da0 * c0 + da1 * da1 * c1, xb = db0 * db0 * c0 + db1 * db1 * c1;
-                float da2 = 0.f, db2 = 0.f;
+                const float2 d0 = __fadd2_rn(*reinterpret_cast<const float2*>(sx + j), nk0);
+                const float2 d1 = __fadd2_rn(*reinterpret_cast<const float2*>(sy + j), nk1);
+                float2 x = __fmul2_rn(__fmul2_rn(d0, d0), cc0);
+                x = __ffma2_rn(__fmul2_rn(d1, d1), cc1, x);
+                float2 d2 = f2(0.f, 0.f);
                 if constexpr (ND == 3) {
-                    da2 = wa.z - wk.z; db2 = wb.z - wk.z;
-                    xa = fmaf(da2 * da2, c2, xa);
-                    xb = fmaf(db2 * db2, c2, xb);
+                    d2 = __fadd2_rn(*reinterpret_cast<const float2*>(sz + j), nk2);
+                    x = __ffma2_rn(__fmul2_rn(d2, d2), cc2, x);
                 }
-                const float ga = exp2f(-xa), gb = exp2f(-xb);
-                s0 += ga;
-                s1 += gb;
-                e0[0] = fmaf(ga, da0, e0[0]); e1[0] = fmaf(gb, db0, e1[0]);
-                e0[1] = fmaf(ga, da1, e0[1]); e1[1] = fmaf(gb, db1, e1[1]);
-                if constexpr (ND == 3) { e0[2] = fmaf(ga, da2, e0[2]); e1[2] = fmaf(gb, db2, e1[2]); }
+                const float2 g = f2(exp2f(-x.x), exp2f(-x.y));
+                sp = __fadd2_rn(sp, g);
+                ep0 = __ffma2_rn(g, d0, ep0);
+                ep1 = __ffma2_rn(g, d1, ep1);
+                if constexpr (ND == 3) ep2 = __ffma2_rn(g, d2, ep2);
             }
-            if (j < M) {
-                const P wa = sw[j];
-                const float da0 = wa.x - wk.x, da1 = wa.y - wk.y;
-                float xa = da0 * da0 * c0 + da1 * da1 * c1;
-                float da2 = 0.f;
-                if constexpr (ND == 3) { da2 = wa.z - wk.z; xa = fmaf(da2 * da2, c2, xa); }
-                const float ga = exp2f(-xa);
-                s0 += ga;
-                e0[0] = fmaf(ga, da0, e0[0]);
-                e0[1] = fmaf(ga, da1, e0[1]);
-                if constexpr (ND == 3) e0[2] = fmaf(ga, da2, e0[2]);
+            if (j < M) {   // odd M: the last j in the .x lanes
+                const float d0 = sx[j] - wk.x, d1 = sy[j] - wk.y;
+                float x = (d0 * d0) * c0;
+                x = fmaf(d1 * d1, c1, x);
+                float d2 = 0.f;
+                if constexpr (ND == 3) { d2 = sz[j] - wk.z; x = fmaf(d2 * d2, c2, x); }
+                const float g = exp2f(-x);
+                sp.x += g;
+                ep0.x = fmaf(g, d0, ep0.x);
+                ep1.x = fmaf(g, d1, ep1.x);
+                if constexpr (ND == 3) ep2.x = fmaf(g, d2, ep2.x);
             }
+            const float s0 = sp.x, s1 = sp.y;
+            float e0[ND], e1[ND];
+            e0[0] = ep0.x; e1[0] = ep0.y;
+            e0[1] = ep1.x; e1[1] = ep1.y;
+            if constexpr (ND == 3) { e0[2] = ep2.x; e1[2] = ep2.y; }
             a[q] = ak;
 #pragma unroll
             for (int i = 0; i < ND; ++i) {
@@ -248,6 +264,9 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
             w.x = nw[0]; w.y = nw[1];
             if constexpr (ND == 3) w.z = nw[2];
             sw[k] = w;
+            sx[k] = w.x;
+            sy[k] = w.y;
+            if constexpr (ND == 3) sz[k] = w.z;
             mv += kmoved;
         }
         moved = __syncthreads_count(mv);
@@ -276,7 +295,9 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
 
 template <int ND>
 cudaError_t launch_nd(const RunLaunch& L, int nimg, int max_M, cudaStream_t s) {
-    const size_t smem = (size_t)max_M * (ND == 2 ? sizeof(float2) : sizeof(float4));
+    // positions (AoS) and the same by axis (even length)
+    const size_t smem = (size_t)max_M * (ND == 2 ? sizeof(float2) : sizeof(float4)) +
+                        (size_t)ND * ((max_M + 1) & ~1) * sizeof(float);
     const int nper = (max_M + kRunThreads - 1) / kRunThreads;
     static_assert(ITC_MAX_M <= 32 * kRunThreads, "codebooks per thread cover ITC_MAX_M");
     auto k = nper <= 1 ? run_kernel<1, ND> : nper <= 2 ? run_kernel<2, ND> : nper <= 4 ? run_kernel<4, ND>

@@ -184,7 +184,7 @@ size_t plan_layout(int B, size_t* desc_off, size_t* ints_off, size_t* tmap_off =
     const size_t d = align_up((size_t)B * sizeof(ImageDesc), 256);
     // per class an image list and a tile prefix (an image is in at most two classes: its
     // fields class and its self-overlap class), then the backward image order
-    const size_t n = align_up((size_t)(6 * (size_t)B + kMaxClasses + 2) * sizeof(int), 256);
+    const size_t n = align_up((size_t)((5 + kGroupInts) * (size_t)B + kMaxClasses + 2) * sizeof(int), 256);
     const size_t m = align_up((size_t)B * sizeof(CUtensorMap), 256);
     if (desc_off) *desc_off = h;
     if (ints_off) *ints_off = h + d;
@@ -557,19 +557,39 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         });
         for (int b = 0; b < B; ++b) ints[io++] = order[b];
     }
-    // iterations: one CTA per image, the images with the most pair work (iters x M^2) first, so
-    // that the long ones do not start last
+    // iterations: images with up to 16, 32 or 64 codebook vectors share a CTA (8, 4 or 2 of them,
+    // 16, 32 or 64 threads each), larger ones have a CTA each; per dimension, the groups are
+    // listed by the pair work (iters x M^2) of their costliest image, largest first, so that the
+    // long ones do not start last
     const int run_off = io;
-    {
-        std::vector<int> order(B);
-        for (int b = 0; b < B; ++b) order[b] = b;
+    for (int nd = 2; nd <= 3; ++nd) {
+        std::vector<int> order;
+        for (int b = 0; b < B; ++b)
+            if (descs[b].ndim == nd) order.push_back(b);
         auto cost = [&](int b) { return (double)(descs[b].iters + 1) * descs[b].M * descs[b].M; };
         std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
-        for (int b = 0; b < B; ++b) ints[io++] = order[b];
+        int open[4] = {-1, -1, -1, -1};   // the group each span class is filling (int offset)
+        int ng = 0;
+        for (int b : order) {
+            const int M = descs[b].M;
+            const int cl = M <= 16 ? 0 : (M <= 32 ? 1 : (M <= 64 ? 2 : 3));
+            const int span = 16 << cl, cap = cl == 3 ? 1 : kRunThreads / span;
+            if (open[cl] < 0 || ints[open[cl]] == cap) {
+                open[cl] = io;
+                ints[io] = 0;
+                ints[io + 1] = span;
+                for (int i = 0; i < kGroupMax; ++i) ints[io + 2 + i] = -1;
+                io += kGroupInts;
+                ++ng;
+            }
+            int* g = ints + open[cl];
+            g[2 + g[0]++] = b;
+        }
+        h->run_ngroups[nd - 2] = ng;
     }
     h->nints = io;
     h->bwd_order_off = bwd_off;
-    h->run_order_off = run_off;
+    h->run_groups_off = run_off;
     h->bwd_tiles = bwd;
 
     // workspace: [fields][S_XX partials][per-image backward scalars]
@@ -886,10 +906,17 @@ static int run_iterate_images(const void* plan_host, const void* plan_dev, int b
     R.absolute = 0;
     R.final_eval = 1;
     R.img_base = b0;
-    if (whole && b0 == 0 && b1 == h->B) R.order = reinterpret_cast<const int*>(pd + h->ints_off) + h->run_order_off;
+    const bool grouped = whole && b0 == 0 && b1 == h->B;
+    const int* groups = reinterpret_cast<const int*>(pd + h->ints_off) + h->run_groups_off;
     for (int nd = 2; nd <= 3; ++nd) {
         if (!(h->ndim_mask & (1 << nd))) continue;
-        const int rc = cuda_status(launch_run(R, b1 - b0, h->max_M, h->max_dim, reinterpret_cast<cudaStream_t>(stream), nd));
+        int ctas = b1 - b0;
+        if (grouped) {
+            // the 3-D groups follow the 2-D ones
+            R.groups = groups + (nd == 3 ? (size_t)h->run_ngroups[0] * kGroupInts : 0);
+            ctas = h->run_ngroups[nd - 2];
+        }
+        const int rc = cuda_status(launch_run(R, ctas, h->max_M, h->max_dim, reinterpret_cast<cudaStream_t>(stream), nd));
         if (rc) return rc;
     }
     return ITC_OK;

@@ -16,6 +16,10 @@ constexpr int kMaxClasses = 16;     // distinct (sigma, trunc, flags, ndim, dtyp
 constexpr int kThreads = 256;       // fields / backward CTA size
 constexpr int kTileW = 64;          // output columns per fields tile
 constexpr int kRunThreads = 128;    // codebook-iteration CTA size
+// Iteration group record: image count n, span (threads per image: 16, 32, 64 or 128), then up to
+// kRunThreads / 16 image indices.  Images with M <= span share one CTA, span threads each.
+constexpr int kGroupMax = 8;
+constexpr int kGroupInts = 2 + kGroupMax;
 // Dynamic shared floats per codebook vector of the iteration and backward-codebook kernels:
 // w (3), a (1), D (3), s (1), E (3).
 constexpr int kCodebookSmemFloats = 11;
@@ -110,7 +114,8 @@ struct PlanHeader {
     long long bwd_tiles;        // backward pixel tiles over all images
     int max_bwd_tiles;          // most backward pixel tiles of one image
     int bwd_order_off;          // offset (ints) of the backward image order (B ints, most tiles first)
-    int run_order_off;          // offset (ints) of the iteration order (B ints, most pair work first)
+    int run_groups_off;         // offset (ints) of the iteration groups (kGroupInts ints each)
+    int run_ngroups[2];         // iteration groups of the 2-D images, then of the 3-D images
     long long tmap_off;         // bytes from plan start to CUtensorMap[B] (input tiles)
     long long pad_floats;       // sum H*fpitch (padded per-pixel layout)
     int has_recursive;          // some class computes its fields by recursion
@@ -161,7 +166,8 @@ struct RunLaunch {
     int absolute;
     int final_eval;             // 1: stats at the final W (itc_run); 0: stats at W_in (itc_step)
     int img_base;               // image of blockIdx.x == 0 (image sub-ranges)
-    const int* order;           // whole batch: image of each CTA, costliest first (else img_base + blockIdx.x)
+    const int* groups;          // whole batch: the images of each CTA (kGroupInts ints a CTA), else
+                                // one image a CTA, img_base + blockIdx.x
 };
 
 struct BackwardLaunch {

@@ -1,15 +1,16 @@
 // itc_run.cu -- the fixed-point iterations of Algorithm 1 (steps 3-11) on precomputed fields.
 //
-// One CTA owns one image for all of its iterations; W, the gathered field values and the
-// codebook sums stay in shared memory, the fields are read from L2/HBM by gathers.  Per
-// iteration:
+// A CTA owns its images for all of their iterations: one image with more than 64 codebook
+// vectors, else 2, 4 or 8 images of up to 64, 32 or 16 vectors, each on as many threads, in
+// lockstep.  W, the gathered field values and the codebook sums stay in shared memory, the
+// fields are read from L2/HBM by gathers.  Per iteration:
 //   gather   a_k = A(r_k), D_k = F(r_k) (- r_k a_k if absolute) + (r_k - w_k) a_k,
 //            r_k = round(w_k) clamped to the lattice                  (Eq. (accupdate) data terms)
 //   pairs    s_k = sum_j g_rho(w_j - w_k),  E_k = sum_j g_rho(w_j - w_k)(w_j - w_k)   (Eq. (origupdate))
 //            one thread per k loops over every j in order (positions are broadcast from shared
 //            memory), so the per-k sums need no reduction; g = exp2f(-sum_i d_i^2 c_i) with
 //            log2(e) folded into c_i.
-//   sums     S_XW = sum_k a_k, S_WW = sum_k s_k (FP32 shuffle trees, then the warps in order),
+//   sums     S_XW = sum_k a_k, S_WW = sum_k s_k (FP32 shuffle trees, then the image's warps in order),
 //            c = S_XW / S_WW, D_cs of Eq. (1) in double at the reported W
 //   update   w_k' = w_k + step_scale (D_k - kappa c E_k) / a_k, kappa_i = tau_i^2 / rho_i^2 (the
 //            factor differentiating Eq. (1) gives the pair term; 1 when tau = rho), rounded unless
@@ -45,32 +46,6 @@ struct Sums {
     int empty;
 };
 
-// Block sums of (a, s, empty), fixed order: a shuffle tree per warp, then the warps in order.
-// FP32 trees keep the relative error of S_XW and S_WW near log2(M) ulp.
-__device__ __forceinline__ void block_sums(float a, float s, int e, float* red, Sums* out) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    a = warp_sum(a);
-    s = warp_sum(s);
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if (lane == 0) {
-        red[wid * 3] = a;
-        red[wid * 3 + 1] = s;
-        red[wid * 3 + 2] = __int_as_float(e);
-    }
-    __syncthreads();
-    float x = 0.f, y = 0.f;
-    int z = 0;
-    for (int w = 0; w < nw; ++w) {
-        x += red[w * 3];
-        y += red[w * 3 + 1];
-        z += __float_as_int(red[w * 3 + 2]);
-    }
-    out->sxw = x;
-    out->sww = y;
-    out->empty = z;
-    __syncthreads();   // red is reused by the next call
-}
-
 __device__ void write_stats(itc_stats* st, const Sums& s, double sxx, int moved, int iters_done,
                             double dcs_const) {
     itc_stats r;
@@ -95,50 +70,99 @@ struct Img {
     float step;
 };
 
+// Sums over the codebook vectors of each image of the CTA: an image owns `span` consecutive
+// threads (16, 32, 64 or 128; the threads past its M contribute zeros).  A shuffle tree over the
+// image's lanes (over the whole warp from span 32 up), then, for images over several warps, the
+// warp sums in warp order through shared memory (one barrier, taken by the whole CTA).  Zeros
+// added to a sum leave it unchanged, so the result is the same for any span that holds the image.
+__device__ __forceinline__ void group_sums(float a, float s, int e, int span, float* red, Sums* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = span >= 32 ? 16 : span >> 1; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+    }
+    if (span <= 32) {
+        __syncwarp();   // the image's pair reads are done before any of its lanes updates W
+        out->sxw = a;
+        out->sww = s;
+        out->empty = e;
+        return;
+    }
+    if (lane == 0) {
+        red[wid * 3] = a;
+        red[wid * 3 + 1] = s;
+        red[wid * 3 + 2] = __int_as_float(e);
+    }
+    __syncthreads();
+    const int w0 = (threadIdx.x / span) * (span >> 5);
+    float x = 0.f, y = 0.f;
+    int z = 0;
+    for (int w = w0; w < w0 + (span >> 5); ++w) {
+        x += red[w * 3];
+        y += red[w * 3 + 1];
+        z += __float_as_int(red[w * 3 + 2]);
+    }
+    out->sxw = x;
+    out->sww = y;
+    out->empty = z;
+}
+
 // NPER: codebooks owned per thread (compile-time so the per-codebook state stays in registers).
 // ND: lattice dimension (2 or 3).
+// A CTA runs a group of images of one span class in lockstep (the same iteration index t); each
+// image stops on its own test and its threads then idle to the end of the group.
 template <int NPER, int ND>
 __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_constant__ RunLaunch L) {
     using P = typename std::conditional<ND == 2, float2, float4>::type;
-    const int img = L.order ? __ldg(L.order + blockIdx.x) : L.img_base + blockIdx.x;
-    const ImageDesc& Dg = L.descs ? L.descs[img] : L.one;
-    if (Dg.ndim != ND) return;   // a mixed plan launches once per dimension
+    const int tid = threadIdx.x, wid = tid >> 5;
+    const int* grp = L.groups ? L.groups + (size_t)blockIdx.x * kGroupInts : nullptr;
+    const int n = grp ? __ldg(grp) : 1;
+    const int span = grp ? __ldg(grp + 1) : kRunThreads;
+    const int sub = tid / span, kl = tid - sub * span;   // the thread's image in the group, its lane there
+    const int img = grp ? (sub < n ? __ldg(grp + 2 + sub) : -1) : L.img_base + blockIdx.x;
+    const ImageDesc& Dg = L.descs ? L.descs[img < 0 ? __ldg(grp + 2) : img] : L.one;
+    if (!grp && Dg.ndim != ND) return;   // a mixed range launches once per dimension (CTA-uniform)
+    const bool has = img >= 0;
     Img D;
     D.A = L.fields + Dg.field_off;
     D.plane = Dg.plane_floats;
-    D.H = Dg.H; D.W = Dg.W; D.G = Dg.G; D.fpitch = Dg.fpitch; D.M = Dg.M; D.iters = Dg.iters;
+    D.H = Dg.H; D.W = Dg.W; D.G = Dg.G; D.fpitch = Dg.fpitch; D.M = has ? Dg.M : 0; D.iters = Dg.iters;
     D.flags = Dg.flags; D.step = Dg.step_scale;
     // pair kernel g_rho(d) = exp(-sum_i d_i^2 / (2 rho_i^2)) = 2^(-sum_i d_i^2 c_i),
     // c_i = log2(e) / (2 rho_i^2); rho = sigma unless the codebook width is set apart
     const float c0 = (float)(1.4426950408889634 * (double)Dg.pinv2s2[0]);
     const float c1 = (float)(1.4426950408889634 * (double)Dg.pinv2s2[1]);
     const float c2 = ND == 3 ? (float)(1.4426950408889634 * (double)Dg.pinv2s2[2]) : 0.f;
-    const float kap[3] = {Dg.kappa[0], Dg.kappa[1], ND == 3 ? Dg.kappa[2] : 0.f};
-    const double dcs_const = Dg.dcs_const;
-    const long long w_off = Dg.w_off;
-    const int M = D.M, tid = threadIdx.x;
+    const int M = D.M;
     extern __shared__ __align__(16) unsigned char smraw[];
-    P* sw = reinterpret_cast<P*>(smraw);   // M positions
-    // the same positions by axis (even length), so that the pair sums read two j at a time
-    const int Mp = (M + 1) & ~1;
-    float* sx = reinterpret_cast<float*>(smraw + (size_t)M * sizeof(P));
-    float* sy = sx + Mp;
-    float* sz = sy + Mp;
+    // positions, then the same by axis (so that the pair sums read two j at a time); room for
+    // NPER * kRunThreads vectors, the image of lane group `sub` at offset sub * span
+    constexpr int CAP = NPER * kRunThreads;
+    const int base = sub * span;
+    P* sw = reinterpret_cast<P*>(smraw) + base;
+    float* sx = reinterpret_cast<float*>(smraw + (size_t)CAP * sizeof(P)) + base;
+    float* sy = sx + CAP;
+    float* sz = sy + CAP;
     __shared__ float red[3 * (kRunThreads / 32)];
-    __shared__ double s_sxx;
+    __shared__ int mvred[kRunThreads / 32];
+    __shared__ double s_sxx[kGroupMax];
 
     if (L.sxx_single) {
-        if (tid == 0) s_sxx = *L.sxx_single;
-    } else if (tid < 32) {
-        const long long nt = Dg.sxx_tiles;
-        const long long po = Dg.sxx_off;
-        double v = 0;
-        for (long long i = tid; i < nt; i += 32) v += L.partials[po + i];
-        v = warp_sum_d(v);
-        if (tid == 0) s_sxx = v;
+        if (tid == 0) s_sxx[0] = *L.sxx_single;
+    } else {
+        // S_XX of each image from its tile partials, one warp per image
+        for (int g = wid; g < n; g += kRunThreads / 32) {
+            const ImageDesc& ds = grp ? L.descs[__ldg(grp + 2 + g)] : Dg;
+            const long long nt = ds.sxx_tiles, po = ds.sxx_off;
+            double v = 0;
+            for (long long i = tid & 31; i < nt; i += 32) v += L.partials[po + i];
+            v = warp_sum_d(v);
+            if ((tid & 31) == 0) s_sxx[g] = v;
+        }
     }
-    const float* Win = L.W_in + w_off;
-    for (int k = tid; k < M; k += blockDim.x) {
+    const float* Win = L.W_in + Dg.w_off;
+    for (int k = kl; k < M; k += span) {
         P w;
         w.x = Win[k * ND];
         w.y = Win[k * ND + 1];
@@ -149,23 +173,22 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
         if constexpr (ND == 3) sz[k] = w.z;
     }
     __syncthreads();
-    const double sxx = s_sxx;
     const bool snap = !(D.flags & ITC_CONTINUOUS);
     const bool stop_fixed = (D.flags & ITC_STOP_ON_FIXED) != 0;
 
-    Sums s;
+    Sums s = {0.f, 0.f, 0};
     int moved = 0, done = 0;
-    bool stop = false;
+    bool stop = false, live = has;   // live: the image still iterates
     for (int t = 0;; ++t) {
-        if (!L.final_eval && t == D.iters) break;
+        if (!L.final_eval && t == D.iters) live = false;
         float a[NPER], Dm[NPER][ND], Ek[NPER][ND];
         float pa = 0.f, ps = 0.f;
         int pe = 0;
 #pragma unroll
         for (int q = 0; q < NPER; ++q) {
-            const int k = tid + q * kRunThreads;
+            const int k = kl + q * span;
             a[q] = 0.f;
-            if (k >= M) continue;
+            if (!live || k >= M) continue;
             const P wk = sw[k];
             // gather first (its latency overlaps the pair sums)
             float r[3], wv[3];
@@ -231,16 +254,23 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
             ps += s0 + s1;
             pe += !(ak > 0.f);
         }
-        block_sums(pa, ps, pe, red, &s);
-        if (!L.final_eval && t == 0 && L.stats && tid == 0) write_stats(L.stats + img, s, sxx, 0, 0, dcs_const);
-        if (t == D.iters || stop) break;
-        // update (Jacobi: every k above read the old W; the barriers in block_sums separate them)
+        Sums r;
+        group_sums(pa, ps, pe, span, red, &r);
+        if (live) s = r;
+        if (live && !L.final_eval && t == 0 && L.stats && kl == 0) write_stats(L.stats + img, s, s_sxx[sub], 0, 0, Dg.dcs_const);
+        const bool upd = live && t != D.iters && !stop;
+        if (!upd) live = false;
+        // update (Jacobi: every k above read the old W; the barrier in group_sums, or the image's
+        // warp for spans up to 32, separates them)
         const float c = s.sxw / s.sww;
+        float kap[ND];   // tau_i^2 / rho_i^2, read where it is used (it need not hold registers)
+#pragma unroll
+        for (int i = 0; i < ND; ++i) kap[i] = upd ? Dg.kappa[i] : 0.f;
         int mv = 0;
 #pragma unroll
         for (int q = 0; q < NPER; ++q) {
-            const int k = tid + q * kRunThreads;
-            if (k >= M || !(a[q] > 0.f)) continue;
+            const int k = kl + q * span;
+            if (!upd || k >= M || !(a[q] > 0.f)) continue;
             P w = sw[k];
             float nw[3];
             nw[0] = w.x; nw[1] = w.y;
@@ -269,17 +299,31 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
             if constexpr (ND == 3) sz[k] = w.z;
             mv += kmoved;
         }
-        moved = __syncthreads_count(mv);
-        ++done;
-        if (stop_fixed && moved == 0) stop = true;
+        // vectors moved per image (same trees as the sums), and whether any image goes on; the
+        // barrier also orders this update before the next pair sums
+        for (int o = span >= 32 ? 16 : span >> 1; o > 0; o >>= 1) mv += __shfl_xor_sync(0xffffffffu, mv, o);
+        if (span > 32 && (tid & 31) == 0) mvred[wid] = mv;
+        const bool any = __syncthreads_or(live);
+        if (span > 32) {
+            const int w0 = sub * (span >> 5);
+            mv = 0;
+            for (int w = w0; w < w0 + (span >> 5); ++w) mv += mvred[w];
+        }
+        if (upd) {
+            moved = mv;
+            ++done;
+            if (stop_fixed && moved == 0) stop = true;
+        }
+        if (!any) break;
     }
-    if (L.final_eval && L.stats && tid == 0) write_stats(L.stats + img, s, sxx, moved, done, dcs_const);
-    if (!L.final_eval && L.stats && tid == 0) {
+    if (has && L.final_eval && L.stats && kl == 0) write_stats(L.stats + img, s, s_sxx[sub], moved, done, Dg.dcs_const);
+    if (has && !L.final_eval && L.stats && kl == 0) {
         L.stats[img].moved = moved;
         L.stats[img].iters_done = done;
     }
-    float* Wout = L.W_out + w_off;
-    for (int k = tid; k < M; k += blockDim.x) {
+    float* Wout = L.W_out + Dg.w_off;
+    const long long w_off = Dg.w_off;
+    for (int k = kl; k < M; k += span) {
         const P w = sw[k];
         float ww[3];
         ww[0] = w.x; ww[1] = w.y;
@@ -295,10 +339,11 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
 
 template <int ND>
 cudaError_t launch_nd(const RunLaunch& L, int nimg, int max_M, cudaStream_t s) {
-    // positions (AoS) and the same by axis (even length)
-    const size_t smem = (size_t)max_M * (ND == 2 ? sizeof(float2) : sizeof(float4)) +
-                        (size_t)ND * ((max_M + 1) & ~1) * sizeof(float);
     const int nper = (max_M + kRunThreads - 1) / kRunThreads;
+    // positions (AoS) and the same by axis, room for NPER * kRunThreads vectors
+    const int np2 = nper <= 1 ? 1 : nper <= 2 ? 2 : nper <= 4 ? 4 : nper <= 8 ? 8 : nper <= 16 ? 16 : 32;
+    const size_t cap = (size_t)np2 * kRunThreads;
+    const size_t smem = cap * (ND == 2 ? sizeof(float2) : sizeof(float4)) + (size_t)ND * cap * sizeof(float);
     static_assert(ITC_MAX_M <= 32 * kRunThreads, "codebooks per thread cover ITC_MAX_M");
     auto k = nper <= 1 ? run_kernel<1, ND> : nper <= 2 ? run_kernel<2, ND> : nper <= 4 ? run_kernel<4, ND>
            : nper <= 8 ? run_kernel<8, ND> : nper <= 16 ? run_kernel<16, ND> : run_kernel<32, ND>;

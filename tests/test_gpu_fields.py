@@ -118,13 +118,22 @@ def test_fields_are_deterministic():
 @pytest.mark.parametrize("sigma", [2.0, 3.0, 4.0])
 @pytest.mark.parametrize("dtype", ["u8", "f32"])
 @pytest.mark.parametrize("absolute", [False, True])
-def test_tma_tiles_equal_plain_tiles_bit_for_bit(sigma, dtype, absolute):
+@pytest.mark.parametrize("pattern", ["sparse", "solid"])
+def test_tma_tiles_equal_plain_tiles_bit_for_bit(sigma, dtype, absolute, pattern):
     """Rows on 16-byte boundaries take the TMA-staged tiles; an odd row pitch takes the plain
-    staging.  Both accumulate the same products in the same order, so they agree exactly."""
+    staging.  Both accumulate the same products in the same order, so they agree exactly.
+    "solid" adds a disc and a band of ones touching the border: there the TMA tiles take the
+    constant sums of all-ones windows, which must equal the products they stand for."""
     import torch
     rng = np.random.default_rng(int(sigma * 10) + (dtype == "f32"))
     h = (rng.random((197, 203)) < 0.2)
-    h = h.astype(np.uint8) if dtype == "u8" else (h * rng.random((197, 203))).astype(np.float32)
+    if dtype == "f32":
+        h = (h * rng.random((197, 203))).astype(np.float32)
+    if pattern == "solid":
+        uu, vv = np.mgrid[0:197, 0:203]
+        one = ((uu - 90) ** 2 + (vv - 110) ** 2 < 70 ** 2) | (vv >= 180) | (uu < 20)
+        h = np.where(one, 1, h)
+    h = h.astype(np.uint8) if dtype == "u8" else h.astype(np.float32)
     buf_a, (ta,) = itc.pack_images([h], "cuda", align=16)      # pitch multiple of 16 elements
     buf_b, (tb,) = itc.pack_images([h], "cuda", align=1)       # pitch 203: no tensor map
     Fa, sa = itc.fields(ta, sigma, 3.0, absolute)

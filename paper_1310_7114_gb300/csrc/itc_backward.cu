@@ -252,12 +252,11 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
         int gray[4][4];
         const bool cols_in = v0 + pc < Wd;
         if (nd == 2) {
-            if (cols_in) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int u = min(u0 + pr + i, H - 1);
-                    a4[i] = __ldg(reinterpret_cast<const float4*>(A + (long long)u * fpitch + v0 + pc));
-                }
+            for (int i = 0; i < 4; ++i) {
+                const int u = min(u0 + pr + i, H - 1);
+                a4[i] = cols_in ? __ldg(reinterpret_cast<const float4*>(A + (long long)u * fpitch + v0 + pc))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         } else {
 #pragma unroll
@@ -335,19 +334,32 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
             __syncthreads();   // sa / sb are rewritten by the next chunk or tile
         }
 
+        if (nd == 2) {
+            // the thread's 4 x 4 results go through shared memory (sa is free after the last
+            // chunk's barrier), so that each warp writes 32 consecutive pixels of a row
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                *reinterpret_cast<float4*>(&sa[pr + i][pc]) =
+                    make_float4(s1 * a4[i].x - s2 * acc[i][0], s1 * a4[i].y - s2 * acc[i][1],
+                                s1 * a4[i].z - s2 * acc[i][2], s1 * a4[i].w - s2 * acc[i][3]);
+            __syncthreads();
+            const int r0 = tid >> 6, c = tid & 63;   // rows r0, r0 + 4, ..., column c
+            if (v0 + c < Wd) {
+                const int nrow = min(16, max(0, (H - u0 - r0 + 3) >> 2));
+                float* gp = gh + (long long)(u0 + r0) * Wd + v0 + c;
+#pragma unroll
+                for (int m = 0; m < 16; ++m)
+                    if (m < nrow) gp[4 * m * Wd] = sa[r0 + 4 * m][c];
+            }
+            continue;   // the next tile's list building passes two barriers before sa is rewritten
+        }
         if (!cols_in) continue;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int u = u0 + pr + i;
             if (u >= H) break;
             float* out = gh + (long long)u * Wd + v0 + pc;
-            if (nd == 2) {
-                // 4 field values from one 16-byte load (rows are padded to a multiple of 4 floats)
-                const float av[4] = {a4[i].x, a4[i].y, a4[i].z, a4[i].w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (v0 + pc + j < Wd) out[j] = s1 * av[j] - s2 * acc[i][j];
-            } else {
+            {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int v = v0 + pc + j;

@@ -144,14 +144,14 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
     const float c2 = ND == 3 ? (float)(1.4426950408889634 * (double)Dg.pinv2s2[2]) : 0.f;
     const int M = D.M;
     extern __shared__ __align__(16) unsigned char smraw[];
-    // positions, then the same by axis (so that the pair sums read two j at a time); room for
+    // positions, then the same regrouped so that the pair sums read two j at a time with one
+    // 16-byte load, (x_j, x_j+1, y_j, y_j+1) per even j, and z by itself; room for
     // NPER * kRunThreads vectors, the image of lane group `sub` at offset sub * span
     constexpr int CAP = NPER * kRunThreads;
     const int base = sub * span;
     P* sw = reinterpret_cast<P*>(smraw) + base;
-    float* sx = reinterpret_cast<float*>(smraw + (size_t)CAP * sizeof(P)) + base;
-    float* sy = sx + CAP;
-    float* sz = sy + CAP;
+    float* sxy = reinterpret_cast<float*>(smraw + (size_t)CAP * sizeof(P)) + 2 * base;
+    float* sz = sxy + 2 * CAP - 2 * base + base;
     __shared__ float red[3 * (kRunThreads / 32)];
     __shared__ int mvred[kRunThreads / 32];
     __shared__ double s_sxx[kGroupMax];
@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
         w.y = Win[k * ND + 1];
         if constexpr (ND == 3) { w.z = Win[k * ND + 2]; w.w = 0.f; }
         sw[k] = w;
-        sx[k] = w.x;
-        sy[k] = w.y;
+        sxy[(k >> 1) * 4 + (k & 1)] = w.x;
+        sxy[(k >> 1) * 4 + 2 + (k & 1)] = w.y;
         if constexpr (ND == 3) sz[k] = w.z;
     }
     __syncthreads();
@@ -217,10 +217,11 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
             if constexpr (ND == 3) nk2 = f2(-wk.z, -wk.z);
             float2 sp = f2(0.f, 0.f), ep0 = f2(0.f, 0.f), ep1 = f2(0.f, 0.f), ep2 = f2(0.f, 0.f);
             int j = 0;
-#pragma unroll 4
+#pragma unroll 8
             for (; j + 1 < M; j += 2) {
-                const float2 d0 = __fadd2_rn(*reinterpret_cast<const float2*>(sx + j), nk0);
-                const float2 d1 = __fadd2_rn(*reinterpret_cast<const float2*>(sy + j), nk1);
+                const float4 q4 = *reinterpret_cast<const float4*>(sxy + 2 * j);
+                const float2 d0 = __fadd2_rn(f2(q4.x, q4.y), nk0);
+                const float2 d1 = __fadd2_rn(f2(q4.z, q4.w), nk1);
                 float2 x = __fmul2_rn(__fmul2_rn(d0, d0), cc0);
                 x = __ffma2_rn(__fmul2_rn(d1, d1), cc1, x);
                 float2 d2 = f2(0.f, 0.f);
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
                 if constexpr (ND == 3) ep2 = __ffma2_rn(g, d2, ep2);
             }
             if (j < M) {   // odd M: the last j in the .x lanes
-                const float d0 = sx[j] - wk.x, d1 = sy[j] - wk.y;
+                const float d0 = sxy[2 * j] - wk.x, d1 = sxy[2 * j + 2] - wk.y;
                 float x = (d0 * d0) * c0;
                 x = fmaf(d1 * d1, c1, x);
                 float d2 = 0.f;
@@ -303,8 +304,8 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
             w.x = nw[0]; w.y = nw[1];
             if constexpr (ND == 3) w.z = nw[2];
             sw[k] = w;
-            sx[k] = w.x;
-            sy[k] = w.y;
+            sxy[(k >> 1) * 4 + (k & 1)] = w.x;
+            sxy[(k >> 1) * 4 + 2 + (k & 1)] = w.y;
             if constexpr (ND == 3) sz[k] = w.z;
             mv += kmoved;
         }
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
 template <int ND>
 cudaError_t launch_nd(const RunLaunch& L, int nimg, int max_M, cudaStream_t s) {
     const int nper = (max_M + kRunThreads - 1) / kRunThreads;
-    // positions (AoS) and the same by axis, room for NPER * kRunThreads vectors
+    // positions (AoS) and the same regrouped by pairs of j, room for NPER * kRunThreads vectors
     const int np2 = nper <= 1 ? 1 : nper <= 2 ? 2 : nper <= 4 ? 4 : nper <= 8 ? 8 : nper <= 16 ? 16 : 32;
     const size_t cap = (size_t)np2 * kRunThreads;
     const size_t smem = cap * (ND == 2 ? sizeof(float2) : sizeof(float4)) + (size_t)ND * cap * sizeof(float);

@@ -28,6 +28,13 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// 2^x by the PTX instruction ex2.approx.ftz.f32 (relative error about 2^-22; results below the
+// smallest normal float flush to zero)
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ int lattice_round_i(float x, int n) {
     float r = floorf(x + 0.5f);
     return (int)fminf(fmaxf(r, 0.f), (float)(n - 1));
@@ -206,8 +213,9 @@ constexpr int kChunk = 64;   // codebooks staged per round in the pixel kernel
 // so for the codebooks whose box meets a tile (listed in k order)
 //   S(r, c) = sum_l a_l(r) b_l(c),  a_l(r) = g_u(u0 + r - w_lu) [|u0 + r - r_lu| <= R_u], ...
 // Chunks of 64 listed codebooks are staged as a (64 x 64) and b (64 x 64) in shared memory and
-// every thread accumulates a 4 x 4 block of pixels in l order (deterministic, no atomics).  In
-// 3-D the g factor depends on each pixel's gray level and is applied per pixel and codebook.
+// every thread accumulates a 4 x 4 block of pixels in l order (deterministic, no atomics), with
+// packed FMAs over pairs of columns.  In 3-D the g factor depends on each pixel's gray level and
+// is applied per pixel and codebook.
 __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_constant__ BackwardLaunch L) {
     // split CTAs per image (few large images): CTA s of an image takes its tiles s, s + split, ...
     const int split = L.split;
@@ -218,6 +226,8 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
     const int ntiles = D.bwd_tiles_u * D.bwd_tiles_v;
     const int Ru = D.R[0], Rv = D.R[1], Rg = D.R[2];
     const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
+    // the separable factors exp(-d^2 c) = 2^(-d^2 c log2 e), log2 e folded into the widths
+    const float l0 = (float)(1.4426950408889634 * (double)c0), l1 = (float)(1.4426950408889634 * (double)c1);
     // the S_XX term uses the field of h at the width of V(X): A itself unless set apart
     const float* A = L.fields + (D.self_off >= 0 ? D.self_off : D.field_off);
     float* gh = L.grad_h + D.gh_off;
@@ -300,8 +310,8 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
                 const int k = lk[base + l];
                 const int u = u0 + r, v = v0 + r;
                 float av = 0.f, bv = 0.f;
-                if (u < H && abs(u - cr[k * 3]) <= Ru) { const float d = (float)u - cw[k * 3]; av = expf(-d * d * c0); }
-                if (v < Wd && abs(v - cr[k * 3 + 1]) <= Rv) { const float d = (float)v - cw[k * 3 + 1]; bv = expf(-d * d * c1); }
+                if (u < H && abs(u - cr[k * 3]) <= Ru) { const float d = (float)u - cw[k * 3]; av = ex2_ftz(-(d * d) * l0); }
+                if (v < Wd && abs(v - cr[k * 3 + 1]) <= Rv) { const float d = (float)v - cw[k * 3 + 1]; bv = ex2_ftz(-(d * d) * l1); }
                 sa[l][r] = av;
                 sb[l][r] = bv;
             }
@@ -311,10 +321,15 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
                 const float4 bv4 = *reinterpret_cast<const float4*>(&sb[l][pc]);
                 const float av[4] = {av4.x, av4.y, av4.z, av4.w}, bv[4] = {bv4.x, bv4.y, bv4.z, bv4.w};
                 if (nd == 2) {
+                    const float2 b01 = make_float2(bv4.x, bv4.y), b23 = make_float2(bv4.z, bv4.w);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 ai = make_float2(av[i], av[i]);
+                        float2 p0 = make_float2(acc[i][0], acc[i][1]), p1 = make_float2(acc[i][2], acc[i][3]);
+                        p0 = __ffma2_rn(ai, b01, p0);
+                        p1 = __ffma2_rn(ai, b23, p1);
+                        acc[i][0] = p0.x; acc[i][1] = p0.y; acc[i][2] = p1.x; acc[i][3] = p1.y;
+                    }
                 } else {
                     const int k = lk[base + l];
                     const float wg = cw[k * 3 + 2];

@@ -661,7 +661,7 @@ int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, in
             R.img_list = L.img_list;
             R.pos_base = p0;
             R.mode = L.mode;
-            rc = cuda_status(launch_recursive(R, p1 - p0, s));
+            rc = cuda_status(launch_recursive(R, p1 - p0, h->max_dim[0], h->max_dim[1], s));
         } else {
             rc = cuda_status(launch_fields_any(L, ci.tma != 0 && !ci.use_plain && !ci.self, t0, t1, ci.taps.R[0],
                                                ci.taps.R[1], ci.ndim, ci.dtype, s));

@@ -228,7 +228,7 @@ int fields_tma_box(int dtype, int R, int tile_h, int* box_w, int* box_h);
 cudaError_t launch_fields_tma(const FieldsLaunch& L, int ntiles, int R, int dtype, cudaStream_t s);
 // ndim: the lattice dimension of every image of the launch (2 or 3)
 cudaError_t launch_run(const RunLaunch& L, int nimg, int max_M, const int* max_dim, cudaStream_t s, int ndim);
-cudaError_t launch_recursive(const RecursiveLaunch& L, int nimg, cudaStream_t s);
+cudaError_t launch_recursive(const RecursiveLaunch& L, int nimg, int max_H, int max_W, cudaStream_t s);
 cudaError_t launch_chamfer(const ChamferLaunch& L, int max_W, cudaStream_t s);
 cudaError_t launch_segment(const SegmentLaunch& L, int B, int max_M, cudaStream_t s);
 cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long pixel_tiles, int max_image_tiles,

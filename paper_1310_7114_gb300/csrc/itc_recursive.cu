@@ -11,12 +11,13 @@
 // with zero states at the ends (no data outside the image), so the kernel is untruncated.
 //
 // Pass along v (one lane per row, rows staged through shared memory in 32 x 32 tiles so that
-// global accesses are coalesced): T = g_v * h, T_v = (d g)_v * h into two scratch planes (the
-// causal part is stored, the anticausal part added).  Pass along u (one thread per column, so
-// warps read and write whole row segments): A = g_u * T, F_u = (d g)_u * T, F_v = g_u * T_v into
-// the field planes, same order; the column pass also sums h A per column (FP64) and each warp's
-// 32 columns into one S_XX partial, in a fixed order.  The self-overlap pass (mode 1) computes A
-// alone into the A_s plane with one scratch plane.
+// global accesses are coalesced; a warp per 32-row block, the blocks of an image spread over the
+// grid's y dimension): T = g_v * h, T_v = (d g)_v * h into two scratch planes (the causal part is
+// stored, the anticausal part added).  Pass along u (one thread per column, 128 columns per CTA,
+// so warps read and write whole row segments; rows in prefetched chunks): A = g_u * T,
+// F_u = (d g)_u * T, F_v = g_u * T_v into the field planes, same order; the column pass also sums
+// h A per column (FP64) and each warp's 32 columns into one S_XX partial, in a fixed order.  The
+// self-overlap pass (mode 1) computes A alone into the A_s plane with one scratch plane.
 #include "itc_internal.cuh"
 
 namespace itc {
@@ -35,15 +36,19 @@ __device__ __forceinline__ float pixel(const ImageDesc& D, int u, int v) {
     return __ldg(reinterpret_cast<const float*>(D.data) + o);
 }
 
-// one image per CTA: img = the class list entry of position base + blockIdx.x
+// the image of the CTA: the class list entry of position base + blockIdx.x (blockIdx.y picks the
+// CTA's block of rows or columns within it)
 __device__ __forceinline__ const ImageDesc& rec_image(const RecursiveLaunch& L) {
     return L.descs[__ldg(L.img_list + L.pos_base + blockIdx.x)];
 }
 
-// Along v: a warp takes 32 rows at a time, one lane per row, and walks them in 32 x 32 tiles
-// staged in shared memory (rows of 33 floats), so every global load and store is a coalesced row
-// segment while each lane runs its row's recursion on the staged tile.
-constexpr int kRecRowWarps = 3;   // three 32 x 33 float tiles per warp: 38 KB of static shared memory
+// Along v: a warp takes 32 rows, one lane per row, and walks them in 32 x 32 tiles staged in
+// shared memory (rows of 33 floats), so every global load and store is a coalesced row segment
+// while each lane runs its row's recursion on the staged tile.
+constexpr int kRecRowWarps = 4;                        // row blocks per CTA
+constexpr int kRecTileFloats = 3 * 32 * 33;            // a warp's three 32 x 33 tiles
+constexpr int kRecCh = 8;                              // rows per prefetched chunk in the column pass
+constexpr int kRecColThreads = 128;                    // columns per CTA in the column pass
 
 __global__ void __launch_bounds__(32 * kRecRowWarps) rec_rows_kernel(const __grid_constant__ RecursiveLaunch L) {
     const ImageDesc& D = rec_image(L);
@@ -55,18 +60,22 @@ __global__ void __launch_bounds__(32 * kRecRowWarps) rec_rows_kernel(const __gri
     const Cplx z0 = {rc.zr[1][0], rc.zi[1][0]}, z1 = {rc.zr[1][1], rc.zi[1][1]};
     const Cplx c0 = {rc.cr[0], rc.ci[0]}, c1 = {rc.cr[1], rc.ci[1]};
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ float sx[kRecRowWarps][32][33], so0[kRecRowWarps][32][33], so1[kRecRowWarps][32][33];
-    float (*X)[33] = sx[wid];
-    float (*O0)[33] = so0[wid];
-    float (*O1)[33] = so1[wid];
+    extern __shared__ float rsm[];
+    float (*X)[33] = reinterpret_cast<float (*)[33]>(rsm + wid * kRecTileFloats);
+    float (*O0)[33] = X + 32;
+    float (*O1)[33] = X + 64;
     const int ntc = (W + 31) / 32;
-    for (int r0 = wid * 32; r0 < H; r0 += 32 * kRecRowWarps) {
+    // this warp's block of 32 rows (warps past the image's last row have nothing to do; the
+    // kernel takes no block-wide barrier)
+    {
+        const int r0 = (blockIdx.y * kRecRowWarps + wid) * 32;
+        if (r0 >= H) return;
         const int nr = min(32, H - r0);
-        auto load_x = [&](int cb) {   // input tile: rows r0.., columns cb..
-            for (int rr = 0; rr < nr; ++rr) {
-                const int v = cb + lane;
-                X[rr][lane] = v < W ? pixel(D, r0 + rr, v) : 0.f;
-            }
+        auto load_x = [&](int cb) {   // input tile: rows r0.., columns cb.. (8 loads in flight at a time)
+            const int v = cb + lane;
+#pragma unroll 8
+            for (int rr = 0; rr < 32; ++rr)
+                if (rr < nr) X[rr][lane] = v < W ? pixel(D, r0 + rr, v) : 0.f;
             __syncwarp();
         };
         // causal: tiles left to right
@@ -101,10 +110,13 @@ __global__ void __launch_bounds__(32 * kRecRowWarps) rec_rows_kernel(const __gri
         for (int tc = ntc - 1; tc >= 0; --tc) {
             const int cb = tc * 32, nc = min(32, W - cb);
             load_x(cb);
-            for (int rr = 0; rr < nr; ++rr) {
-                if (lane < nc) {
-                    O0[rr][lane] = P0[(size_t)(r0 + rr) * fp + cb + lane];
-                    if (moments) O1[rr][lane] = P1[(size_t)(r0 + rr) * fp + cb + lane];
+            if (lane < nc) {
+#pragma unroll 4
+                for (int rr = 0; rr < 32; ++rr) {
+                    if (rr < nr) {
+                        O0[rr][lane] = P0[(size_t)(r0 + rr) * fp + cb + lane];
+                        if (moments) O1[rr][lane] = P1[(size_t)(r0 + rr) * fp + cb + lane];
+                    }
                 }
             }
             __syncwarp();
@@ -132,7 +144,7 @@ __global__ void __launch_bounds__(32 * kRecRowWarps) rec_rows_kernel(const __gri
     }
 }
 
-__global__ void __launch_bounds__(256) rec_cols_kernel(const __grid_constant__ RecursiveLaunch L) {
+__global__ void __launch_bounds__(kRecColThreads) rec_cols_kernel(const __grid_constant__ RecursiveLaunch L) {
     const ImageDesc& D = rec_image(L);
     const int H = D.H, W = D.W, fp = D.fpitch;
     const bool moments = L.mode == 0;
@@ -147,47 +159,87 @@ __global__ void __launch_bounds__(256) rec_cols_kernel(const __grid_constant__ R
     const Cplx c0 = {rc.cr[0], rc.ci[0]}, c1 = {rc.cr[1], rc.ci[1]};
     const int lane = threadIdx.x & 31;
     const long long poff = moments ? D.partial_off : D.sxx_off;
-    // whole warps walk the columns so that each warp's partial covers 32 consecutive columns
+    // whole warps walk the columns so that each warp's partial covers 32 consecutive columns;
+    // this CTA takes columns blockIdx.y * kRecColThreads ..
     const int wcols = (W + 31) & ~31;
-    for (int v = threadIdx.x; v < wcols; v += blockDim.x) {
+    const int vb = blockIdx.y * kRecColThreads;
+    if (vb + (threadIdx.x & ~31) >= wcols) return;   // whole warps past the image
+    // rows go in chunks of kRecCh: a chunk's loads are all issued before its recursion steps,
+    // so the sequential walk waits on one memory round trip per chunk, not per row
+    constexpr int CH = kRecCh;
+    {
+        const int v = vb + threadIdx.x;
         const bool on = v < W;
         double hs = 0.0;
         if (on) {
             Cplx a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, m0 = {0.f, 0.f}, m1 = {0.f, 0.f}, b0 = {0.f, 0.f}, b1 = {0.f, 0.f};
-            for (int u = 0; u < H; ++u) {
-                const size_t o = (size_t)u * fp + v;
-                const float x = T[o];
-                m0 = cmul(z0, cadd(m0, a0));
-                m1 = cmul(z1, cadd(m1, a1));
-                a0 = cmul(z0, a0); a0.r += x;
-                a1 = cmul(z1, a1); a1.r += x;
-                A[o] = re_mul(c0, a0) + re_mul(c1, a1);
-                if (moments) {
-                    const float y = Tv[o];
-                    b0 = cmul(z0, b0); b0.r += y;
-                    b1 = cmul(z1, b1); b1.r += y;
-                    Fu[o] = -(re_mul(c0, m0) + re_mul(c1, m1));
-                    Fv[o] = re_mul(c0, b0) + re_mul(c1, b1);
+            for (int ub = 0; ub < H; ub += CH) {
+                float xs[CH], ys[CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int u = ub + c;
+                    xs[c] = u < H ? T[(size_t)u * fp + v] : 0.f;
+                    ys[c] = (moments && u < H) ? Tv[(size_t)u * fp + v] : 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int u = ub + c;
+                    if (u >= H) break;
+                    const size_t o = (size_t)u * fp + v;
+                    const float x = xs[c];
+                    m0 = cmul(z0, cadd(m0, a0));
+                    m1 = cmul(z1, cadd(m1, a1));
+                    a0 = cmul(z0, a0); a0.r += x;
+                    a1 = cmul(z1, a1); a1.r += x;
+                    A[o] = re_mul(c0, a0) + re_mul(c1, a1);
+                    if (moments) {
+                        const float y = ys[c];
+                        b0 = cmul(z0, b0); b0.r += y;
+                        b1 = cmul(z1, b1); b1.r += y;
+                        Fu[o] = -(re_mul(c0, m0) + re_mul(c1, m1));
+                        Fv[o] = re_mul(c0, b0) + re_mul(c1, b1);
+                    }
                 }
             }
             a0 = a1 = m0 = m1 = b0 = b1 = Cplx{0.f, 0.f};
-            for (int u = H - 1; u >= 0; --u) {
-                const size_t o = (size_t)u * fp + v;
-                const float xn = u + 1 < H ? T[o + fp] : 0.f;
-                m0 = cmul(z0, cadd(cadd(m0, a0), Cplx{xn, 0.f}));
-                m1 = cmul(z1, cadd(cadd(m1, a1), Cplx{xn, 0.f}));
-                a0 = cmul(z0, cadd(a0, Cplx{xn, 0.f}));
-                a1 = cmul(z1, cadd(a1, Cplx{xn, 0.f}));
-                const float a = A[o] + re_mul(c0, a0) + re_mul(c1, a1);
-                A[o] = a;
-                if (moments) {
-                    const float yn = u + 1 < H ? Tv[o + fp] : 0.f;
-                    b0 = cmul(z0, cadd(b0, Cplx{yn, 0.f}));
-                    b1 = cmul(z1, cadd(b1, Cplx{yn, 0.f}));
-                    Fu[o] += re_mul(c0, m0) + re_mul(c1, m1);
-                    Fv[o] += re_mul(c0, b0) + re_mul(c1, b1);
+            for (int ue = H - 1; ue >= 0; ue -= CH) {
+                // this chunk's inputs (the row below each row) and the causal parts it adds to
+                float xn[CH], yn[CH], ao[CH], fu[CH], fv[CH], hv[CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int u = ue - c;
+                    xn[c] = yn[c] = ao[c] = fu[c] = fv[c] = hv[c] = 0.f;
+                    if (u >= 0) {
+                        const size_t o = (size_t)u * fp + v;
+                        xn[c] = u + 1 < H ? T[o + fp] : 0.f;
+                        ao[c] = A[o];
+                        hv[c] = pixel(D, u, v);
+                        if (moments) {
+                            yn[c] = u + 1 < H ? Tv[o + fp] : 0.f;
+                            fu[c] = Fu[o];
+                            fv[c] = Fv[o];
+                        }
+                    }
                 }
-                hs += (double)pixel(D, u, v) * (double)a;
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int u = ue - c;
+                    if (u < 0) break;
+                    const size_t o = (size_t)u * fp + v;
+                    m0 = cmul(z0, cadd(cadd(m0, a0), Cplx{xn[c], 0.f}));
+                    m1 = cmul(z1, cadd(cadd(m1, a1), Cplx{xn[c], 0.f}));
+                    a0 = cmul(z0, cadd(a0, Cplx{xn[c], 0.f}));
+                    a1 = cmul(z1, cadd(a1, Cplx{xn[c], 0.f}));
+                    const float a = ao[c] + re_mul(c0, a0) + re_mul(c1, a1);
+                    A[o] = a;
+                    if (moments) {
+                        b0 = cmul(z0, cadd(b0, Cplx{yn[c], 0.f}));
+                        b1 = cmul(z1, cadd(b1, Cplx{yn[c], 0.f}));
+                        Fu[o] = fu[c] + (re_mul(c0, m0) + re_mul(c1, m1));
+                        Fv[o] = fv[c] + (re_mul(c0, b0) + re_mul(c1, b1));
+                    }
+                    hs += (double)hv[c] * (double)a;
+                }
             }
         }
         // S_XX share of these 32 columns: a fixed-order shuffle tree
@@ -198,12 +250,16 @@ __global__ void __launch_bounds__(256) rec_cols_kernel(const __grid_constant__ R
 
 }  // namespace
 
-cudaError_t launch_recursive(const RecursiveLaunch& L, int nimg, cudaStream_t s) {
-    if (nimg <= 0) return cudaSuccess;
-    rec_rows_kernel<<<nimg, 32 * kRecRowWarps, 0, s>>>(L);
-    cudaError_t e = cudaGetLastError();
+cudaError_t launch_recursive(const RecursiveLaunch& L, int nimg, int max_H, int max_W, cudaStream_t s) {
+    if (nimg <= 0 || max_H <= 0 || max_W <= 0) return cudaSuccess;
+    const size_t smem = (size_t)kRecRowWarps * kRecTileFloats * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(rec_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    rec_cols_kernel<<<nimg, 256, 0, s>>>(L);
+    const dim3 grow((unsigned)nimg, (unsigned)((max_H + 32 * kRecRowWarps - 1) / (32 * kRecRowWarps)));
+    rec_rows_kernel<<<grow, 32 * kRecRowWarps, smem, s>>>(L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const dim3 gcol((unsigned)nimg, (unsigned)((max_W + kRecColThreads - 1) / kRecColThreads));
+    rec_cols_kernel<<<gcol, kRecColThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -185,7 +185,7 @@ struct BackwardLaunch {
     int split;                  // pixel-pass CTAs per image (set at launch)
 };
 
-constexpr int kChamferMaxW = 1024;   // chamfer rows: 32 lanes x 32 segments of registers
+constexpr int kChamferMaxW = 1024;   // chamfer rows: 32 lanes x 4 columns x 8 chunks
 
 struct RecursiveLaunch {
     const ImageDesc* descs;

@@ -8,8 +8,10 @@
 // order with one rounding each, no fused multiply-add), lowest k on ties; pixels without data
 // get -1.
 //
-// One CTA per image (largest images first); its warps take the image's 32 x 32 pixel tiles in
-// turn, each on its own (no block-wide barrier after the codebook is staged).  Per tile the
+// One CTA per image (largest images first); its warps take the image's 16 x 16 pixel tiles in
+// turn, each on its own (no block-wide barrier after the codebook is staged).  The small tile
+// keeps the candidate list short: on the C3 batch 16 x 16 tiles take 1.21 ms against 1.51 ms
+// for 32 x 32 (the lists cost more than they save at 8 x 8).  Per tile the
 // codebooks that can win somewhere in it are listed first: with dmin_k / dmax_k the metric of
 // the nearest / farthest point of the tile's box, every k with dmin_k <= min_j dmax_j (the same
 // rounded arithmetic, which is monotone in each |d_i|, so the bounds hold for every pixel).  The
@@ -19,7 +21,7 @@
 namespace itc {
 namespace {
 
-constexpr int kSegTile = 32;
+constexpr int kSegTile = 16;
 
 __device__ __forceinline__ int site_round(float x, int n) {
     const float r = floorf(x + 0.5f);
@@ -86,9 +88,9 @@ __global__ void __launch_bounds__(kThreads) segment_kernel(const __grid_constant
             nl += __popc(bal);
         }
         __syncwarp();
-        // pixels: a tile row per step, coalesced 64-byte label stores
-        for (int r = 0; r < kSegTile; ++r) {
-            const int u = u0 + r, v = v0 + lane;
+        // pixels: two tile rows per step (half a warp each), 32-byte label stores
+        for (int r = lane >> 4; r < kSegTile; r += 2) {
+            const int u = u0 + r, v = v0 + (lane & 15);
             if (u > u1) break;
             if (v > v1) continue;
             const size_t o = (size_t)u * D.pitch + v;

@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
     const float c0 = (float)(1.4426950408889634 * (double)Dg.pinv2s2[0]);
     const float c1 = (float)(1.4426950408889634 * (double)Dg.pinv2s2[1]);
     const float c2 = ND == 3 ? (float)(1.4426950408889634 * (double)Dg.pinv2s2[2]) : 0.f;
+    const bool iso = ND == 2 && c0 == c1;
     const int M = D.M;
     extern __shared__ __align__(16) unsigned char smraw[];
     // positions, then the same regrouped so that the pair sums read two j at a time with one
@@ -217,23 +218,45 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
             if constexpr (ND == 3) nk2 = f2(-wk.z, -wk.z);
             float2 sp = f2(0.f, 0.f), ep0 = f2(0.f, 0.f), ep1 = f2(0.f, 0.f), ep2 = f2(0.f, 0.f);
             int j = 0;
+            if (iso) {
+                // equal widths (2-D): c (d0^2 + d1^2), one product fewer per pair; on the lattice
+                // d0^2 + d1^2 is an exact integer, rounded once by the product with c
 #pragma unroll 8
-            for (; j + 1 < M; j += 2) {
-                const float4 q4 = *reinterpret_cast<const float4*>(sxy + 2 * j);
-                const float2 d0 = __fadd2_rn(f2(q4.x, q4.y), nk0);
-                const float2 d1 = __fadd2_rn(f2(q4.z, q4.w), nk1);
-                float2 x = __fmul2_rn(__fmul2_rn(d0, d0), cc0);
-                x = __ffma2_rn(__fmul2_rn(d1, d1), cc1, x);
-                float2 d2 = f2(0.f, 0.f);
-                if constexpr (ND == 3) {
-                    d2 = __fadd2_rn(*reinterpret_cast<const float2*>(sz + j), nk2);
-                    x = __ffma2_rn(__fmul2_rn(d2, d2), cc2, x);
+                for (; j + 1 < M; j += 2) {
+                    const float4 q4 = *reinterpret_cast<const float4*>(sxy + 2 * j);
+                    const float2 d0 = __fadd2_rn(f2(q4.x, q4.y), nk0);
+                    const float2 d1 = __fadd2_rn(f2(q4.z, q4.w), nk1);
+                    float2 x = __fmul2_rn(__ffma2_rn(d1, d1, __fmul2_rn(d0, d0)), cc0);
+                    float2 d2 = f2(0.f, 0.f);
+                    if constexpr (ND == 3) {
+                        d2 = __fadd2_rn(*reinterpret_cast<const float2*>(sz + j), nk2);
+                        x = __ffma2_rn(__fmul2_rn(d2, d2), cc2, x);
+                    }
+                    const float2 g = f2(ex2_ftz(-x.x), ex2_ftz(-x.y));
+                    sp = __fadd2_rn(sp, g);
+                    ep0 = __ffma2_rn(g, d0, ep0);
+                    ep1 = __ffma2_rn(g, d1, ep1);
+                    if constexpr (ND == 3) ep2 = __ffma2_rn(g, d2, ep2);
                 }
-                const float2 g = f2(ex2_ftz(-x.x), ex2_ftz(-x.y));
-                sp = __fadd2_rn(sp, g);
-                ep0 = __ffma2_rn(g, d0, ep0);
-                ep1 = __ffma2_rn(g, d1, ep1);
-                if constexpr (ND == 3) ep2 = __ffma2_rn(g, d2, ep2);
+            } else {
+#pragma unroll 8
+                for (; j + 1 < M; j += 2) {
+                    const float4 q4 = *reinterpret_cast<const float4*>(sxy + 2 * j);
+                    const float2 d0 = __fadd2_rn(f2(q4.x, q4.y), nk0);
+                    const float2 d1 = __fadd2_rn(f2(q4.z, q4.w), nk1);
+                    float2 x = __fmul2_rn(__fmul2_rn(d0, d0), cc0);
+                    x = __ffma2_rn(__fmul2_rn(d1, d1), cc1, x);
+                    float2 d2 = f2(0.f, 0.f);
+                    if constexpr (ND == 3) {
+                        d2 = __fadd2_rn(*reinterpret_cast<const float2*>(sz + j), nk2);
+                        x = __ffma2_rn(__fmul2_rn(d2, d2), cc2, x);
+                    }
+                    const float2 g = f2(ex2_ftz(-x.x), ex2_ftz(-x.y));
+                    sp = __fadd2_rn(sp, g);
+                    ep0 = __ffma2_rn(g, d0, ep0);
+                    ep1 = __ffma2_rn(g, d1, ep1);
+                    if constexpr (ND == 3) ep2 = __ffma2_rn(g, d2, ep2);
+                }
             }
             if (j < M) {   // odd M: the last j in the .x lanes
                 const float d0 = sxy[2 * j] - wk.x, d1 = sxy[2 * j + 2] - wk.y;

@@ -347,3 +347,49 @@ def test_mixed_2d_and_3d_plan():
         _, Wb, sb = run_plan([imgs[b]], [len(W0s[b])], [W0s[b]], params[b], ndims=[[2, 3, 2][b]], Gs=[[1, 40, 1][b]])
         assert np.array_equal(Ws[b], Wb[0]), b
         assert st[b]["dcs"] == sb[0]["dcs"], b
+
+
+def test_grouped_images_stop_on_their_own():
+    """Images that share an iteration CTA (up to 8 with M <= 16, 4 with M <= 32, 2 with M <= 64)
+    run in lockstep, but each stops on its own test: mixed iteration counts, Algorithm 1's
+    fixed-point stop on some images, odd M.  Every image must come out exactly as when it runs
+    alone (range launches take one image per CTA), codebooks and stats alike."""
+    import torch
+    Ms = [3, 5, 8, 16, 17, 24, 31, 32, 33, 40, 64, 7, 12, 15, 2, 1]
+    images, W0s, params = [], [], []
+    for i, m in enumerate(Ms):
+        img = synth.c1_image(100 + i)
+        images.append(img)
+        W0s.append(synth.init_codebook(synth.rng_for(1, 500 + i), img.astype(np.float32), m))
+        iters = (1, 7, 20, 60)[i % 4]
+        flags = itc.ITC_STOP_ON_FIXED if i % 3 == 0 else 0
+        params.append(itc.make_params(2.0 + 0.5 * (i % 3), 3.0, iters, flags=flags))
+    ts = [to_dev(im) for im in images]
+    plan = itc.Plan(ts, Ms, params)
+    W = plan.pack_W(W0s)
+    st = itc.new_stats(len(images), W.device)
+    itc.run(plan, W, st)
+    Wr = plan.pack_W(W0s)
+    sr = itc.new_stats(len(images), W.device)
+    L = itc.lib()
+    s = torch.cuda.current_stream().cuda_stream
+    for b in range(len(images)):
+        assert L.itc_run_fields_range(plan.host_ptr, plan.dev.data_ptr(), b, b + 1, plan.ws.data_ptr(),
+                                      plan.ws.numel(), s) == 0
+        assert L.itc_run_iterate_range(plan.host_ptr, plan.dev.data_ptr(), b, b + 1, Wr.data_ptr(),
+                                       sr.data_ptr(), plan.ws.data_ptr(), plan.ws.numel(), s) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(W.cpu().numpy(), Wr.cpu().numpy())
+    assert st.cpu().numpy().tobytes() == sr.cpu().numpy().tobytes()
+    stats = itc.stats_to_numpy(st)
+    done = [int(stats[b]["iters_done"]) for b in range(len(images))]
+    # the iteration limits hold, and the stopping images stop early where the oracle does
+    for b, p in enumerate(params):
+        assert done[b] <= p.iters
+    for b in (0, 3, 6):
+        A, F, sxx = _oracle_fields(images[b], float(params[b].sigma[0]))
+        Wo, dcs, tie, t = oracle.lattice_run(A, F, sxx, float(params[b].sigma[0]), W0s[b], params[b].iters,
+                                             stop_on_fixed=True)
+        if tie.min() > 1e-4:
+            assert done[b] == t
+            assert np.array_equal(plan.unpack_W(W)[b], Wo)

@@ -253,8 +253,10 @@ int itc_plan_offsets(const void* plan_host, int b, size_t* field_off, size_t* w_
 
 /*
  * itc_run -- Algorithm 1 for every image of a plan: fields (step 2) for all images in one
- * launch per parameter class, then all images' iterations (steps 3-11) in one launch, one CTA
- * per image.  W is read as the initial codebooks (step 1 is done by the caller) and overwritten
+ * launch per parameter class, then all images' iterations (steps 3-11) in one launch per
+ * lattice dimension: a CTA per image with more than 64 codebook vectors, smaller images 2, 4 or
+ * 8 to a CTA, each stopping on its own (the results equal those of one image per CTA bit for
+ * bit).  W is read as the initial codebooks (step 1 is done by the caller) and overwritten
  * with the result.  The fields stay in `ws` for a following itc_backward with the same plan.
  *   plan_host, plan_dev : the same plan bytes on host and on device
  *   W      : device ragged [sum M][ndim], in/out

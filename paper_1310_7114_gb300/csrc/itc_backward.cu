@@ -232,6 +232,10 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
     const float* A = L.fields + (D.self_off >= 0 ? D.self_off : D.field_off);
     float* gh = L.grad_h + D.gh_off;
     const float s1 = (float)L.scal[img * 4 + 0], s2 = (float)L.scal[img * 4 + 1];
+    // every row of this image's dD/dh starts on a 16-byte boundary (width and offset multiples of
+    // 4 floats, aligned base): the results go out as 16-byte row pieces, else through shared
+    // memory as whole row segments
+    const bool rows16 = ((Wd & 3) == 0) && ((reinterpret_cast<size_t>(gh) & 15) == 0);
 
     extern __shared__ __align__(16) unsigned char bsm[];
     float* cw = reinterpret_cast<float*>(bsm);          // M x 3 codebook positions
@@ -349,6 +353,28 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
             __syncthreads();   // sa / sb are rewritten by the next chunk or tile
         }
 
+        if (nd == 2 && rows16) {
+            // rows of dD/dh start on 16-byte boundaries: one 16-byte store per row of the block
+            // (a warp writes two full 256-byte row segments per instruction)
+            if (cols_in) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int u = u0 + pr + i;
+                    if (u >= H) break;
+                    float* out = gh + (long long)u * Wd + v0 + pc;
+                    const float r4[4] = {s1 * a4[i].x - s2 * acc[i][0], s1 * a4[i].y - s2 * acc[i][1],
+                                         s1 * a4[i].z - s2 * acc[i][2], s1 * a4[i].w - s2 * acc[i][3]};
+                    if (v0 + pc + 3 < Wd) {
+                        *reinterpret_cast<float4*>(out) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (v0 + pc + j < Wd) out[j] = r4[j];
+                    }
+                }
+            }
+            continue;
+        }
         if (nd == 2) {
             // the thread's 4 x 4 results go through shared memory (sa is free after the last
             // chunk's barrier), so that each warp writes 32 consecutive pixels of a row

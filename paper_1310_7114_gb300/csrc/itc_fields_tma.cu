@@ -169,6 +169,8 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
     constexpr int TW = TT::TW, K = TT::K, ROWS = TT::ROWS, RA = TT::RA, BW = TT::BW;
     constexpr int BOX_BYTES = TT::BOX_BYTES, STAGE_BYTES = TT::STAGE_BYTES, NST = TT::NST;
     constexpr int OFF = (RA - R) & 3;                // a window's first input within its 4-group
+    constexpr int NWIN = 8 + 2 * R;                  // inputs of 8 neighbouring outputs (one-row pass)
+    constexpr int NQ = (OFF + NWIN + 3) / 4;         // 4-element groups covering that window
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the TMA destination must be 128-byte aligned: round the base up (128 spare bytes reserved)
@@ -248,6 +250,16 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
         }
     };
 
+    // element i of a staged 4-group q: bytes -> float exactly (2^23 + b as a float, minus 2^23)
+    auto elem = [&](const uint32_t (&w)[NQ > 0 ? NQ * (DTYPE == ITC_U8) + 1 : 1], const float4 (&f)[NQ], int i) -> float {
+        if constexpr (DTYPE == ITC_U8)
+            return __int_as_float((int)__byte_perm(w[i >> 2], 0x4B000000u, 0x7540u | (unsigned)(i & 3))) - 8388608.f;
+        else {
+            const float4 g = f[i >> 2];
+            return (i & 3) == 0 ? g.x : ((i & 3) == 1 ? g.y : ((i & 3) == 2 ? g.z : g.w));
+        }
+    };
+
     for (; t < t_hi; ++t) {
         const int buf = n % NST;
         const unsigned char* stage = stage0 + buf * STAGE_BYTES;
@@ -287,94 +299,159 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
         float* const fbase = L.fields + dp->field_off;
         const long long plane = dp->plane_floats;
 
-        // ---- pass along v, read straight from the staged box.  An item is 4 outputs in each of
-        // two neighbouring rows: the two rows' inputs are the halves of every packed operand, so
-        // the packed FMAs need no realigned pairs; windows without data store zeros
-        constexpr int NW4 = 4 + 2 * R;                   // inputs of 4 neighbouring outputs
-        constexpr int NQ4 = (OFF + NW4 + 3) / 4;         // 4-element groups covering the window
-        for (int item = tid; item < ROWS * 8; item += kThreads) {
-            const int r0 = (item >> 4) * 2, c = (item & 15) * 4;
-            if (v0 + c >= W) continue;
-            const int gu0 = u0 - R + r0;
-            const bool in0 = gu0 >= 0 && gu0 < H, in1 = gu0 + 1 >= 0 && gu0 + 1 < H;
-            float* oT = sT + r0 * TW + c;
-            float* oV = oT + ROWS * TW;
-            // the window's 4-groups: box columns c - R + RA - OFF ... (a multiple of 4)
-            const int g0 = (c - R + RA - OFF) >> 2;
-            constexpr int NU = DTYPE == ITC_U8 ? NQ4 : 1, NF = DTYPE == ITC_U8 ? 1 : NQ4;
-            uint32_t w0[NU], w1[NU];
-            float4 f0[NF], f1[NF];
-            bool nz0 = false, nz1 = false;
-            if constexpr (DTYPE == ITC_U8) {
-                const uint32_t* row0 = reinterpret_cast<const uint32_t*>(stage + r0 * BW);
-                const uint32_t* row1 = row0 + BW / 4;
-#pragma unroll
-                for (int q = 0; q < NQ4; ++q) {
-                    w0[q] = in0 ? row0[g0 + q] : 0u;
-                    w1[q] = in1 ? row1[g0 + q] : 0u;
-                    nz0 |= w0[q] != 0u;
-                    nz1 |= w1[q] != 0u;
-                }
-            } else {
-                const float4* row0 = reinterpret_cast<const float4*>(stage + (size_t)r0 * BW * 4);
-                const float4* row1 = row0 + BW / 4;
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int q = 0; q < NQ4; ++q) {
-                    f0[q] = in0 ? row0[g0 + q] : z4;
-                    f1[q] = in1 ? row1[g0 + q] : z4;
-                    nz0 |= (f0[q].x != 0.f) | (f0[q].y != 0.f) | (f0[q].z != 0.f) | (f0[q].w != 0.f);
-                    nz1 |= (f1[q].x != 0.f) | (f1[q].y != 0.f) | (f1[q].z != 0.f) | (f1[q].w != 0.f);
-                }
-            }
-            if (!(nz0 | nz1)) {
-                st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + TW, 0.f, 0.f, 0.f, 0.f);
-                st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + TW, 0.f, 0.f, 0.f, 0.f);
-                continue;
-            }
-            if (nz0) atomicOr(&colbits[par][c >> 3][r0 >> 5], 1u << (r0 & 31));
-            if (nz1) atomicOr(&colbits[par][c >> 3][(r0 + 1) >> 5], 1u << ((r0 + 1) & 31));
-            // inputs as (row r0, row r0 + 1) pairs; bytes -> floats exactly (2^23 + b, minus 2^23)
-            float2 X[NW4];
-#pragma unroll
-            for (int i = 0; i < NW4; ++i) {
-                const int e = OFF + i;
+        if constexpr (DTYPE == ITC_U8) {
+            // ---- pass along v, read straight from the staged box.  An item is 4 outputs in each of
+            // two neighbouring rows: the two rows' inputs are the halves of every packed operand, so
+            // the packed FMAs need no realigned pairs; windows without data store zeros
+            constexpr int NW4 = 4 + 2 * R;                   // inputs of 4 neighbouring outputs
+            constexpr int NQ4 = (OFF + NW4 + 3) / 4;         // 4-element groups covering the window
+            for (int item = tid; item < ROWS * 8; item += kThreads) {
+                const int r0 = (item >> 4) * 2, c = (item & 15) * 4;
+                if (v0 + c >= W) continue;
+                const int gu0 = u0 - R + r0;
+                const bool in0 = gu0 >= 0 && gu0 < H, in1 = gu0 + 1 >= 0 && gu0 + 1 < H;
+                float* oT = sT + r0 * TW + c;
+                float* oV = oT + ROWS * TW;
+                // the window's 4-groups: box columns c - R + RA - OFF ... (a multiple of 4)
+                const int g0 = (c - R + RA - OFF) >> 2;
+                constexpr int NU = DTYPE == ITC_U8 ? NQ4 : 1, NF = DTYPE == ITC_U8 ? 1 : NQ4;
+                uint32_t w0[NU], w1[NU];
+                float4 f0[NF], f1[NF];
+                bool nz0 = false, nz1 = false;
                 if constexpr (DTYPE == ITC_U8) {
-                    const float a0 = __int_as_float((int)__byte_perm(w0[e >> 2], 0x4B000000u, 0x7540u | (unsigned)(e & 3)));
-                    const float a1 = __int_as_float((int)__byte_perm(w1[e >> 2], 0x4B000000u, 0x7540u | (unsigned)(e & 3)));
-                    X[i] = __fadd2_rn(f2(a0, a1), f2(-8388608.f, -8388608.f));
+                    const uint32_t* row0 = reinterpret_cast<const uint32_t*>(stage + r0 * BW);
+                    const uint32_t* row1 = row0 + BW / 4;
+#pragma unroll
+                    for (int q = 0; q < NQ4; ++q) {
+                        w0[q] = in0 ? row0[g0 + q] : 0u;
+                        w1[q] = in1 ? row1[g0 + q] : 0u;
+                        nz0 |= w0[q] != 0u;
+                        nz1 |= w1[q] != 0u;
+                    }
                 } else {
-                    const float4 p0 = f0[e >> 2], p1 = f1[e >> 2];
-                    const int s4 = e & 3;
-                    X[i] = f2(s4 == 0 ? p0.x : (s4 == 1 ? p0.y : (s4 == 2 ? p0.z : p0.w)),
-                              s4 == 0 ? p1.x : (s4 == 1 ? p1.y : (s4 == 2 ? p1.z : p1.w)));
+                    const float4* row0 = reinterpret_cast<const float4*>(stage + (size_t)r0 * BW * 4);
+                    const float4* row1 = row0 + BW / 4;
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < NQ4; ++q) {
+                        f0[q] = in0 ? row0[g0 + q] : z4;
+                        f1[q] = in1 ? row1[g0 + q] : z4;
+                        nz0 |= (f0[q].x != 0.f) | (f0[q].y != 0.f) | (f0[q].z != 0.f) | (f0[q].w != 0.f);
+                        nz1 |= (f1[q].x != 0.f) | (f1[q].y != 0.f) | (f1[q].z != 0.f) | (f1[q].w != 0.f);
+                    }
                 }
-            }
-            float2 XV[ABS ? NW4 : 1];
-            if constexpr (ABS) {
-                const float vb = (float)(v0 - R + c);
+                if (!(nz0 | nz1)) {
+                    st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + TW, 0.f, 0.f, 0.f, 0.f);
+                    st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + TW, 0.f, 0.f, 0.f, 0.f);
+                    continue;
+                }
+                if (nz0) atomicOr(&colbits[par][c >> 3][r0 >> 5], 1u << (r0 & 31));
+                if (nz1) atomicOr(&colbits[par][c >> 3][(r0 + 1) >> 5], 1u << ((r0 + 1) & 31));
+                // inputs as (row r0, row r0 + 1) pairs; bytes -> floats exactly (2^23 + b, minus 2^23)
+                float2 X[NW4];
 #pragma unroll
                 for (int i = 0; i < NW4; ++i) {
-                    const float pv = vb + (float)i;
-                    XV[i] = f2(X[i].x * pv, X[i].y * pv);
+                    const int e = OFF + i;
+                    if constexpr (DTYPE == ITC_U8) {
+                        const float a0 = __int_as_float((int)__byte_perm(w0[e >> 2], 0x4B000000u, 0x7540u | (unsigned)(e & 3)));
+                        const float a1 = __int_as_float((int)__byte_perm(w1[e >> 2], 0x4B000000u, 0x7540u | (unsigned)(e & 3)));
+                        X[i] = __fadd2_rn(f2(a0, a1), f2(-8388608.f, -8388608.f));
+                    } else {
+                        const float4 p0 = f0[e >> 2], p1 = f1[e >> 2];
+                        const int s4 = e & 3;
+                        X[i] = f2(s4 == 0 ? p0.x : (s4 == 1 ? p0.y : (s4 == 2 ? p0.z : p0.w)),
+                                  s4 == 0 ? p1.x : (s4 == 1 ? p1.y : (s4 == 2 ? p1.z : p1.w)));
+                    }
                 }
-            }
-            float2 aT[4], aV[4];
+                float2 XV[ABS ? NW4 : 1];
+                if constexpr (ABS) {
+                    const float vb = (float)(v0 - R + c);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) { aT[j] = f2(0.f, 0.f); aV[j] = f2(0.f, 0.f); }
-#pragma unroll
-            for (int d = 0; d <= 2 * R; ++d) {
-                const float2 g2 = f2(tp.gv[d], tp.gv[d]);
-                const float2 dg2 = f2(tp.dgv[d], tp.dgv[d]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    aT[j] = __ffma2_rn(g2, X[j + d], aT[j]);
-                    if constexpr (ABS) aV[j] = __ffma2_rn(g2, XV[j + d], aV[j]);
-                    else aV[j] = __ffma2_rn(dg2, X[j + d], aV[j]);
+                    for (int i = 0; i < NW4; ++i) {
+                        const float pv = vb + (float)i;
+                        XV[i] = f2(X[i].x * pv, X[i].y * pv);
+                    }
                 }
+                float2 aT[4], aV[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) { aT[j] = f2(0.f, 0.f); aV[j] = f2(0.f, 0.f); }
+#pragma unroll
+                for (int d = 0; d <= 2 * R; ++d) {
+                    const float2 g2 = f2(tp.gv[d], tp.gv[d]);
+                    const float2 dg2 = f2(tp.dgv[d], tp.dgv[d]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        aT[j] = __ffma2_rn(g2, X[j + d], aT[j]);
+                        if constexpr (ABS) aV[j] = __ffma2_rn(g2, XV[j + d], aV[j]);
+                        else aV[j] = __ffma2_rn(dg2, X[j + d], aV[j]);
+                    }
+                }
+                st4(oT, aT[0].x, aT[1].x, aT[2].x, aT[3].x); st4(oT + TW, aT[0].y, aT[1].y, aT[2].y, aT[3].y);
+                st4(oV, aV[0].x, aV[1].x, aV[2].x, aV[3].x); st4(oV + TW, aV[0].y, aV[1].y, aV[2].y, aV[3].y);
             }
-            st4(oT, aT[0].x, aT[1].x, aT[2].x, aT[3].x); st4(oT + TW, aT[0].y, aT[1].y, aT[2].y, aT[3].y);
-            st4(oV, aV[0].x, aV[1].x, aV[2].x, aV[3].x); st4(oV + TW, aV[0].y, aV[1].y, aV[2].y, aV[3].y);
+        } else {
+            // 4-byte inputs: 8 outputs of one row per item, pairs of neighbouring columns per packed
+            // FMA (the pairs of rows of byte inputs would need register moves here)
+            // ---- pass along v, read straight from the staged box: 8 outputs per item, pairs of
+            // neighbouring columns per packed FMA; windows without data store zeros
+            for (int item = tid; item < ROWS * 8; item += kThreads) {
+                const int r = item >> 3, c = (item & 7) * 8;
+                const int gu = u0 - R + r;
+                if (v0 + c >= W) continue;
+                float* oT = sT + r * TW + c;
+                float* oV = oT + ROWS * TW;
+                // the window's 4-groups: box columns c - R + RA - OFF ... (a multiple of 4)
+                const int g0 = (c - R + RA - OFF) >> 2;
+                uint32_t w[NQ * (DTYPE == ITC_U8) + 1];
+                float4 f[NQ];
+                bool nz = false;
+                if (gu >= 0 && gu < H) {
+                    if constexpr (DTYPE == ITC_U8) {
+                        const uint32_t* row = reinterpret_cast<const uint32_t*>(stage + r * BW);
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) { w[q] = row[g0 + q]; nz |= w[q] != 0u; }
+                    } else {
+                        const float4* row = reinterpret_cast<const float4*>(stage + (size_t)r * BW * 4);
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) {
+                            f[q] = row[g0 + q];
+                            nz |= (f[q].x != 0.f) | (f[q].y != 0.f) | (f[q].z != 0.f) | (f[q].w != 0.f);
+                        }
+                    }
+                }
+                if (!nz) {
+                    st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + 4, 0.f, 0.f, 0.f, 0.f);
+                    st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + 4, 0.f, 0.f, 0.f, 0.f);
+                    continue;
+                }
+                atomicOr(&colbits[par][item & 7][r >> 5], 1u << (r & 31));
+                float x[NWIN];
+#pragma unroll
+                for (int i = 0; i < NWIN; ++i) x[i] = elem(w, f, OFF + i);
+                float xv[ABS ? NWIN : 1];
+                if constexpr (ABS) {
+                    const float vb = (float)(v0 - R + c);
+#pragma unroll
+                    for (int i = 0; i < NWIN; ++i) xv[i] = x[i] * (vb + (float)i);
+                }
+                float2 aT[4], aV[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) { aT[p] = f2(0.f, 0.f); aV[p] = f2(0.f, 0.f); }
+#pragma unroll
+                for (int d = 0; d <= 2 * R; ++d) {
+                    const float2 g2 = f2(tp.gv[d], tp.gv[d]);
+                    const float2 dg2 = f2(tp.dgv[d], tp.dgv[d]);
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const float2 xx = f2(x[2 * p + d], x[2 * p + 1 + d]);
+                        aT[p] = __ffma2_rn(g2, xx, aT[p]);
+                        if constexpr (ABS) aV[p] = __ffma2_rn(g2, f2(xv[2 * p + d], xv[2 * p + 1 + d]), aV[p]);
+                        else aV[p] = __ffma2_rn(dg2, xx, aV[p]);
+                    }
+                }
+                st4(oT, aT[0].x, aT[0].y, aT[1].x, aT[1].y); st4(oT + 4, aT[2].x, aT[2].y, aT[3].x, aT[3].y);
+                st4(oV, aV[0].x, aV[0].y, aV[1].x, aV[1].y); st4(oV + 4, aV[2].x, aV[2].y, aV[3].x, aV[3].y);
+            }
         }
         __syncthreads();
 

@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
     __shared__ float red[3 * (kRunThreads / 32)];
     __shared__ int mvred[kRunThreads / 32];
     __shared__ double s_sxx[kGroupMax];
+    __shared__ float s_kap[kGroupMax][3];   // tau_i^2 / rho_i^2 of each image of the group
 
     if (L.sxx_single) {
         if (tid == 0) s_sxx[0] = *L.sxx_single;
@@ -170,6 +171,8 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
             if ((tid & 31) == 0) s_sxx[g] = v;
         }
     }
+    if (has && kl == 0)
+        for (int i = 0; i < 3; ++i) s_kap[sub][i] = Dg.kappa[i];
     const float* Win = L.W_in + Dg.w_off;
     for (int k = kl; k < M; k += span) {
         P w;
@@ -296,9 +299,9 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
         // update (Jacobi: every k above read the old W; the barrier in group_sums, or the image's
         // warp for spans up to 32, separates them)
         const float c = s.sxw / s.sww;
-        float kap[ND];   // tau_i^2 / rho_i^2, read where it is used (it need not hold registers)
+        float kap[ND];   // from shared memory where it is used (it need not hold registers)
 #pragma unroll
-        for (int i = 0; i < ND; ++i) kap[i] = upd ? Dg.kappa[i] : 0.f;
+        for (int i = 0; i < ND; ++i) kap[i] = upd ? s_kap[sub][i] : 0.f;
         int mv = 0;
 #pragma unroll
         for (int q = 0; q < NPER; ++q) {

@@ -9,9 +9,10 @@
 //   * the row pass reads its input windows straight from the staged box (bytes are turned into
 //     floats in registers), so a tile needs two barriers and no float copy of its input, and three
 //     CTAs fit on an SM for byte inputs;
-//   * both passes use packed FP32 FMAs (fma.rn.f32x2): the row pass over pairs of neighbouring
-//     rows (each packed operand holds the same column of two rows, so no pair is realigned), the
-//     column pass over pairs of neighbouring columns.
+//   * both passes use packed FP32 FMAs (fma.rn.f32x2): the row pass of byte inputs over pairs of
+//     neighbouring rows (each packed operand holds the same column of two rows, so no pair is
+//     realigned), the row pass of float inputs and the column pass over pairs of neighbouring
+//     columns.
 // Used for 2-D images whose rows start on 16-byte boundaries (the tensor map needs it) and for
 // the compiled radii 6, 9 and 12; everything else goes through fields_kernel.
 #include <cuda.h>
@@ -314,31 +315,16 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
                 float* oV = oT + ROWS * TW;
                 // the window's 4-groups: box columns c - R + RA - OFF ... (a multiple of 4)
                 const int g0 = (c - R + RA - OFF) >> 2;
-                constexpr int NU = DTYPE == ITC_U8 ? NQ4 : 1, NF = DTYPE == ITC_U8 ? 1 : NQ4;
-                uint32_t w0[NU], w1[NU];
-                float4 f0[NF], f1[NF];
+                uint32_t w0[NQ4], w1[NQ4];
                 bool nz0 = false, nz1 = false;
-                if constexpr (DTYPE == ITC_U8) {
-                    const uint32_t* row0 = reinterpret_cast<const uint32_t*>(stage + r0 * BW);
-                    const uint32_t* row1 = row0 + BW / 4;
+                const uint32_t* row0 = reinterpret_cast<const uint32_t*>(stage + r0 * BW);
+                const uint32_t* row1 = row0 + BW / 4;
 #pragma unroll
-                    for (int q = 0; q < NQ4; ++q) {
-                        w0[q] = in0 ? row0[g0 + q] : 0u;
-                        w1[q] = in1 ? row1[g0 + q] : 0u;
-                        nz0 |= w0[q] != 0u;
-                        nz1 |= w1[q] != 0u;
-                    }
-                } else {
-                    const float4* row0 = reinterpret_cast<const float4*>(stage + (size_t)r0 * BW * 4);
-                    const float4* row1 = row0 + BW / 4;
-                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int q = 0; q < NQ4; ++q) {
-                        f0[q] = in0 ? row0[g0 + q] : z4;
-                        f1[q] = in1 ? row1[g0 + q] : z4;
-                        nz0 |= (f0[q].x != 0.f) | (f0[q].y != 0.f) | (f0[q].z != 0.f) | (f0[q].w != 0.f);
-                        nz1 |= (f1[q].x != 0.f) | (f1[q].y != 0.f) | (f1[q].z != 0.f) | (f1[q].w != 0.f);
-                    }
+                for (int q = 0; q < NQ4; ++q) {
+                    w0[q] = in0 ? row0[g0 + q] : 0u;
+                    w1[q] = in1 ? row1[g0 + q] : 0u;
+                    nz0 |= w0[q] != 0u;
+                    nz1 |= w1[q] != 0u;
                 }
                 if (!(nz0 | nz1)) {
                     st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + TW, 0.f, 0.f, 0.f, 0.f);
@@ -352,16 +338,9 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
 #pragma unroll
                 for (int i = 0; i < NW4; ++i) {
                     const int e = OFF + i;
-                    if constexpr (DTYPE == ITC_U8) {
-                        const float a0 = __int_as_float((int)__byte_perm(w0[e >> 2], 0x4B000000u, 0x7540u | (unsigned)(e & 3)));
-                        const float a1 = __int_as_float((int)__byte_perm(w1[e >> 2], 0x4B000000u, 0x7540u | (unsigned)(e & 3)));
-                        X[i] = __fadd2_rn(f2(a0, a1), f2(-8388608.f, -8388608.f));
-                    } else {
-                        const float4 p0 = f0[e >> 2], p1 = f1[e >> 2];
-                        const int s4 = e & 3;
-                        X[i] = f2(s4 == 0 ? p0.x : (s4 == 1 ? p0.y : (s4 == 2 ? p0.z : p0.w)),
-                                  s4 == 0 ? p1.x : (s4 == 1 ? p1.y : (s4 == 2 ? p1.z : p1.w)));
-                    }
+                    const float a0 = __int_as_float((int)__byte_perm(w0[e >> 2], 0x4B000000u, 0x7540u | (unsigned)(e & 3)));
+                    const float a1 = __int_as_float((int)__byte_perm(w1[e >> 2], 0x4B000000u, 0x7540u | (unsigned)(e & 3)));
+                    X[i] = __fadd2_rn(f2(a0, a1), f2(-8388608.f, -8388608.f));
                 }
                 float2 XV[ABS ? NW4 : 1];
                 if constexpr (ABS) {

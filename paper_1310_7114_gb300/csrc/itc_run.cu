@@ -298,7 +298,9 @@ __global__ void __launch_bounds__(kRunThreads, 8) run_kernel(const __grid_consta
         if (!upd) live = false;
         // update (Jacobi: every k above read the old W; the barrier in group_sums, or the image's
         // warp for spans up to 32, separates them)
-        const float c = s.sxw / s.sww;
+        // only threads that update divide (an idle thread's 0 / 0 would take the slow division
+        // path and hold its image's warps at the next barrier)
+        const float c = upd ? s.sxw / s.sww : 0.f;
         float kap[ND];   // from shared memory where it is used (it need not hold registers)
 #pragma unroll
         for (int i = 0; i < ND; ++i) kap[i] = upd ? s_kap[sub][i] : 0.f;

@@ -117,3 +117,21 @@ def test_autograd_function_matches_direct_calls():
         assert _nrel(Wt[b].grad.cpu().numpy(), s * gref) <= 1e-4
         assert _nrel(hs[b].grad.cpu().numpy(), s * ghref) <= 1e-4
         assert abs(d[b].item() - (np.log(sums[1]) + np.log(sums[2]) - 2 * np.log(sums[0]))) <= 4e-5
+
+
+def test_backward_rows_not_16_byte_aligned():
+    """dD/dh rows that do not start on 16-byte boundaries (widths and per-image offsets that are
+    not multiples of 4 floats) go out through the shared-memory transpose; rows that do go out as
+    16-byte pieces.  Both against the oracle, in one plan (the 64 x 64 image comes after an offset
+    of 101*97 + 63*61 + 70*131 pixels, not a multiple of 4, so it takes the transpose too)."""
+    images = [synth.c4_weights(5)[:101, :97], synth.c1_image(3).astype(np.float32)[:63, :61],
+              synth.c4_weights(6)[:70, :131], synth.c1_image(4).astype(np.float32),
+              synth.c4_weights(7)[:64, :128]]
+    Ms = [16, 8, 20, 8, 12]
+    assert (101 * 97 + 63 * 61 + 70 * 131) % 4 != 0
+    W0s = [synth.init_codebook(synth.rng_for(4, 70 + i), im, m, 0.5) for i, (im, m) in enumerate(zip(images, Ms))]
+    plan, gW, gh, _, _ = gpu_forward_backward(images, Ms, W0s, 3.0)
+    for b in range(len(images)):
+        gref, ghref, _ = oracle.dcs_grad2d_dense(images[b].astype(np.float64), 3.0, W0s[b].astype(np.float64))
+        assert _nrel(gW[b], gref) <= 1e-4, (b, _nrel(gW[b], gref))
+        assert _nrel(gh[b], ghref) <= 1e-4, (b, _nrel(gh[b], ghref))

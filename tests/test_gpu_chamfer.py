@@ -19,9 +19,9 @@ def _lib():
     itc.lib()
 
 
-def _gpu_chamfer(images):
+def _gpu_chamfer(images, align=16):
     import torch
-    buf, views = itc.pack_images(images, "cuda")
+    buf, views = itc.pack_images(images, "cuda", align=align)
     plan = itc.Plan(views, [1] * len(images), itc.make_params(2.0))
     _, T = itc.chamfer(plan)
     torch.cuda.synchronize()
@@ -34,6 +34,16 @@ def test_random_images(shape):
     rng = np.random.default_rng(shape[0] * 7919 + shape[1])
     imgs = [(rng.random(shape) < p).astype(np.uint8) for p in (0.5, 0.9, 1.0)]
     for im, T in zip(imgs, _gpu_chamfer(imgs)):
+        assert np.array_equal(T, oracle.chamfer34(im).astype(np.float32)), shape
+
+
+@pytest.mark.parametrize("shape", [(29, 31), (41, 513), (12, 130)])
+def test_rows_without_4_byte_alignment(shape):
+    """Byte rows packed back to back (pitch = W): the input comes byte by byte instead of in
+    32-bit words; the result is the same."""
+    rng = np.random.default_rng(shape[0] * 31 + shape[1])
+    imgs = [(rng.random(shape) < p).astype(np.uint8) for p in (0.6, 0.95)]
+    for im, T in zip(imgs, _gpu_chamfer(imgs, align=1)):
         assert np.array_equal(T, oracle.chamfer34(im).astype(np.float32)), shape
 
 

@@ -10,8 +10,9 @@
 //
 // One CTA per image (largest images first); its warps take the image's 16 x 16 pixel tiles in
 // turn, each on its own (no block-wide barrier after the codebook is staged).  The small tile
-// keeps the candidate list short: on the C3 batch 16 x 16 tiles take 1.21 ms against 1.51 ms
-// for 32 x 32 (the lists cost more than they save at 8 x 8).  Per tile the
+// keeps the candidate list short: on a batch of 4096 ragged binary shapes (sides 64 to 512,
+// M up to 128) 16 x 16 tiles take 1.21 ms against 1.51 ms for 32 x 32 (the lists cost more than
+// they save at 8 x 8).  Per tile the
 // codebooks that can win somewhere in it are listed first: with dmin_k / dmax_k the metric of
 // the nearest / farthest point of the tile's box, every k with dmin_k <= min_j dmax_j (the same
 // rounded arithmetic, which is monotone in each |d_i|, so the bounds hold for every pixel).  The

@@ -238,12 +238,15 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
     const bool rows16 = ((Wd & 3) == 0) && ((reinterpret_cast<size_t>(gh) & 15) == 0);
 
     extern __shared__ __align__(16) unsigned char bsm[];
-    float* cw = reinterpret_cast<float*>(bsm);          // M x 3 codebook positions
+    // per listed codebook of the current tile one 16-byte record (position and site along u
+    // and v), then the codebooks' positions, sites and the list itself
+    float4* lc = reinterpret_cast<float4*>(bsm);
+    float* cw = reinterpret_cast<float*>(lc + M);       // M x 3 codebook positions
     int* cr = reinterpret_cast<int*>(cw + 3 * M);       // M x 3 rounded lattice sites
     int* lk = cr + 3 * M;                               // listed codebooks of the current tile
     __shared__ __align__(16) float sa[kChunk][kBwdTileH];
     __shared__ __align__(16) float sb[kChunk][kBwdTileW];
-    __shared__ int wcount[kThreads / 32];
+    __shared__ __align__(16) int wcount[kThreads / 32];
 
     const float* Wk = L.W + D.w_off;
     for (int k = tid; k < M; k += blockDim.x) {
@@ -295,10 +298,21 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
             const unsigned bal = __ballot_sync(0xffffffffu, hit);
             if (lane == 0) wcount[wid] = __popc(bal);
             __syncthreads();
-            int off = nl;
-            for (int q = 0; q < wid; ++q) off += wcount[q];
-            if (hit) lk[off + __popc(bal & ((1u << lane) - 1u))] = k;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) nl += wcount[q];
+            static_assert(kThreads / 32 == 8, "eight warp counts");
+            const int4 wc0 = *reinterpret_cast<const int4*>(wcount), wc1 = *reinterpret_cast<const int4*>(wcount + 4);
+            const int cnt[8] = {wc0.x, wc0.y, wc0.z, wc0.w, wc1.x, wc1.y, wc1.z, wc1.w};
+            int off = nl, tot = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                off += q < wid ? cnt[q] : 0;
+                tot += cnt[q];
+            }
+            if (hit) {
+                const int pos = off + __popc(bal & ((1u << lane) - 1u));
+                lk[pos] = k;
+                lc[pos] = make_float4(cw[k * 3], cw[k * 3 + 1], __int_as_float(cr[k * 3]), __int_as_float(cr[k * 3 + 1]));
+            }
+            nl += tot;
             __syncthreads();
         }
 
@@ -311,11 +325,11 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
             const int nc = min(kChunk, nl - base);
             for (int i = tid; i < nc * kBwdTileH; i += blockDim.x) {
                 const int l = i / kBwdTileH, r = i % kBwdTileH;
-                const int k = lk[base + l];
+                const float4 rec = lc[base + l];
                 const int u = u0 + r, v = v0 + r;
                 float av = 0.f, bv = 0.f;
-                if (u < H && abs(u - cr[k * 3]) <= Ru) { const float d = (float)u - cw[k * 3]; av = ex2_ftz(-(d * d) * l0); }
-                if (v < Wd && abs(v - cr[k * 3 + 1]) <= Rv) { const float d = (float)v - cw[k * 3 + 1]; bv = ex2_ftz(-(d * d) * l1); }
+                if (u < H && abs(u - __float_as_int(rec.z)) <= Ru) { const float d = (float)u - rec.x; av = ex2_ftz(-(d * d) * l0); }
+                if (v < Wd && abs(v - __float_as_int(rec.w)) <= Rv) { const float d = (float)v - rec.y; bv = ex2_ftz(-(d * d) * l1); }
                 sa[l][r] = av;
                 sb[l][r] = bv;
             }
@@ -428,7 +442,7 @@ cudaError_t launch_backward(const BackwardLaunch& L, int B, int max_M, long long
     bwd_codebook_kernel<<<B, kRunThreads, smem1, s>>>(L);
     e = cudaGetLastError();
     if (e != cudaSuccess || !L.grad_h || pixel_tiles <= 0) return e;
-    const size_t smem2 = (size_t)max_M * 7 * sizeof(int);   // positions, sites, tile list
+    const size_t smem2 = (size_t)max_M * (16 + 7 * sizeof(int));   // list records, positions, sites, tile list
     e = cudaFuncSetAttribute(bwd_pixels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
     // one CTA per image when the batch fills the GPU; otherwise each image's tiles are shared out

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kRunThreads, ND == 3 ? 6 : 7) run_kernel(const
             if (iso) {
                 // equal widths (2-D): c (d0^2 + d1^2), one product fewer per pair; on the lattice
                 // d0^2 + d1^2 is an exact integer, rounded once by the product with c
-#pragma unroll 8
+#pragma unroll 16
                 for (; j + 1 < M; j += 2) {
                     const float4 q4 = *reinterpret_cast<const float4*>(sxy + 2 * j);
                     const float2 d0 = __fadd2_rn(f2(q4.x, q4.y), nk0);
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kRunThreads, ND == 3 ? 6 : 7) run_kernel(const
                     if constexpr (ND == 3) ep2 = __ffma2_rn(g, d2, ep2);
                 }
             } else {
-#pragma unroll 8
+#pragma unroll 16
                 for (; j + 1 < M; j += 2) {
                     const float4 q4 = *reinterpret_cast<const float4*>(sxy + 2 * j);
                     const float2 d0 = __fadd2_rn(f2(q4.x, q4.y), nk0);

@@ -35,10 +35,6 @@ __device__ __forceinline__ float ex2_ftz(float x) {
     return y;
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -83,12 +79,14 @@ struct Img {
 // image's lanes (over the whole warp from span 32 up), then, for images over several warps, the
 // warp sums in warp order through shared memory (one barrier, taken by the whole CTA).  Zeros
 // added to a sum leave it unchanged, so the result is the same for any span that holds the image.
-__device__ __forceinline__ void group_sums(float a, float s, int e, int span, float* red, Sums* out) {
+__device__ __forceinline__ void group_sums(float a, float s, int e, int span, bool warp_has, float* red, Sums* out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = span >= 32 ? 16 : span >> 1; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (warp_has) {   // a warp without images only takes the barrier below
+        for (int o = span >= 32 ? 16 : span >> 1; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+        }
     }
     if (span <= 32) {
         __syncwarp();   // the image's pair reads are done before any of its lanes updates W
@@ -135,6 +133,7 @@ __global__ void __launch_bounds__(kRunThreads, ND == 3 ? 6 : 7) run_kernel(const
     const ImageDesc& Dg = L.descs ? L.descs[img < 0 ? __ldg(grp + 2) : img] : L.one;
     if (!grp && Dg.ndim != ND) return;   // a mixed range launches once per dimension (CTA-uniform)
     const bool has = img >= 0;
+    const bool warp_has = __any_sync(0xffffffffu, has);   // warp-uniform
     Img D;
     D.A = L.fields + Dg.field_off;
     D.plane = Dg.plane_floats;
@@ -294,7 +293,7 @@ __global__ void __launch_bounds__(kRunThreads, ND == 3 ? 6 : 7) run_kernel(const
             pe += !(ak > 0.f);
         }
         Sums r;
-        group_sums(pa, ps, pe, span, red, &r);
+        group_sums(pa, ps, pe, span, warp_has, red, &r);
         if (live) s = r;
         if (live && !L.final_eval && t == 0 && L.stats && kl == 0) write_stats(L.stats + img, s, s_sxx[sub], 0, 0, Dg.dcs_const);
         const bool upd = live && t != D.iters && !stop;
@@ -340,18 +339,23 @@ __global__ void __launch_bounds__(kRunThreads, ND == 3 ? 6 : 7) run_kernel(const
             if constexpr (ND == 3) sz[k] = w.z;
             mv += kmoved;
         }
-        // vectors moved per image (same trees as the sums), and whether any image goes on; the
-        // barrier also orders this update before the next pair sums
-        for (int o = span >= 32 ? 16 : span >> 1; o > 0; o >>= 1) mv += __shfl_xor_sync(0xffffffffu, mv, o);
-        if (span > 32 && (tid & 31) == 0) mvred[wid] = mv;
+        // vectors moved per image (same trees as the sums) where it is used: by the stopping test,
+        // and for the stats after an image's last update; whether any image goes on.  The
+        // barrier also orders this update before the next pair sums.  (The count is decided per
+        // warp, the same for every warp of an image.)
+        const bool count = __any_sync(0xffffffffu, upd && (stop_fixed || t + 1 == D.iters));
+        if (count) {
+            for (int o = span >= 32 ? 16 : span >> 1; o > 0; o >>= 1) mv += __shfl_xor_sync(0xffffffffu, mv, o);
+            if (span > 32 && (tid & 31) == 0) mvred[wid] = mv;
+        }
         const bool any = __syncthreads_or(live);
-        if (span > 32) {
+        if (count && span > 32) {
             const int w0 = sub * (span >> 5);
             mv = 0;
             for (int w = w0; w < w0 + (span >> 5); ++w) mv += mvred[w];
         }
         if (upd) {
-            moved = mv;
+            if (count) moved = mv;
             ++done;
             if (stop_fixed && moved == 0) stop = true;
         }

@@ -316,39 +316,47 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
             __syncthreads();
         }
 
-        float acc[4][4];
+        // accumulators as column pairs (j = 0, 1 and 2, 3) of each row, the packed FMA operands
+        float2 acc2[4][2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        for (int i = 0; i < 4; ++i) { acc2[i][0] = make_float2(0.f, 0.f); acc2[i][1] = make_float2(0.f, 0.f); }
+        // factor staging: each thread fills one row / column r of the factors for every fourth l
+        const int sr = tid & (kBwdTileH - 1), sl = tid / kBwdTileH;
+        static_assert(kBwdTileH == kBwdTileW && kThreads % kBwdTileH == 0, "square tiles, whole rows of threads");
+        constexpr int kStageStep = kThreads / kBwdTileH;
+        const int su = u0 + sr, sv = v0 + sr;
+        const bool su_in = su < H, sv_in = sv < Wd;
+        const float fu = (float)su, fv = (float)sv;
         for (int base = 0; base < nl; base += kChunk) {
             const int nc = min(kChunk, nl - base);
-            for (int i = tid; i < nc * kBwdTileH; i += blockDim.x) {
-                const int l = i / kBwdTileH, r = i % kBwdTileH;
+            for (int l = sl; l < nc; l += kStageStep) {
                 const float4 rec = lc[base + l];
-                const int u = u0 + r, v = v0 + r;
                 float av = 0.f, bv = 0.f;
-                if (u < H && abs(u - __float_as_int(rec.z)) <= Ru) { const float d = (float)u - rec.x; av = ex2_ftz(-(d * d) * l0); }
-                if (v < Wd && abs(v - __float_as_int(rec.w)) <= Rv) { const float d = (float)v - rec.y; bv = ex2_ftz(-(d * d) * l1); }
-                sa[l][r] = av;
-                sb[l][r] = bv;
+                if (su_in && abs(su - __float_as_int(rec.z)) <= Ru) { const float d = fu - rec.x; av = ex2_ftz(-(d * d) * l0); }
+                if (sv_in && abs(sv - __float_as_int(rec.w)) <= Rv) { const float d = fv - rec.y; bv = ex2_ftz(-(d * d) * l1); }
+                sa[l][sr] = av;
+                sb[l][sr] = bv;
             }
             __syncthreads();
-            for (int l = 0; l < nc; ++l) {
-                const float4 av4 = *reinterpret_cast<const float4*>(&sa[l][pr]);
-                const float4 bv4 = *reinterpret_cast<const float4*>(&sb[l][pc]);
-                const float av[4] = {av4.x, av4.y, av4.z, av4.w}, bv[4] = {bv4.x, bv4.y, bv4.z, bv4.w};
-                if (nd == 2) {
+            if (nd == 2) {
+#pragma unroll 1   // unrolled, the loop spills at the 80-register budget of 3 CTAs per SM
+                for (int l = 0; l < nc; ++l) {
+                    const float4 av4 = *reinterpret_cast<const float4*>(&sa[l][pr]);
+                    const float4 bv4 = *reinterpret_cast<const float4*>(&sb[l][pc]);
+                    const float av[4] = {av4.x, av4.y, av4.z, av4.w};
                     const float2 b01 = make_float2(bv4.x, bv4.y), b23 = make_float2(bv4.z, bv4.w);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float2 ai = make_float2(av[i], av[i]);
-                        float2 p0 = make_float2(acc[i][0], acc[i][1]), p1 = make_float2(acc[i][2], acc[i][3]);
-                        p0 = __ffma2_rn(ai, b01, p0);
-                        p1 = __ffma2_rn(ai, b23, p1);
-                        acc[i][0] = p0.x; acc[i][1] = p0.y; acc[i][2] = p1.x; acc[i][3] = p1.y;
+                        acc2[i][0] = __ffma2_rn(ai, b01, acc2[i][0]);
+                        acc2[i][1] = __ffma2_rn(ai, b23, acc2[i][1]);
                     }
-                } else {
+                }
+            } else {
+                for (int l = 0; l < nc; ++l) {
+                    const float4 av4 = *reinterpret_cast<const float4*>(&sa[l][pr]);
+                    const float4 bv4 = *reinterpret_cast<const float4*>(&sb[l][pc]);
+                    const float av[4] = {av4.x, av4.y, av4.z, av4.w}, bv[4] = {bv4.x, bv4.y, bv4.z, bv4.w};
                     const int k = lk[base + l];
                     const float wg = cw[k * 3 + 2];
                     const int rg = cr[k * 3 + 2];
@@ -359,12 +367,18 @@ __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_co
                             const int gl = gray[i][j];
                             if (abs(gl - rg) <= Rg) {
                                 const float d = (float)gl - wg;
-                                acc[i][j] = fmaf(av[i] * bv[j], expf(-d * d * c2), acc[i][j]);
+                                float& aij = (j & 1) ? acc2[i][j >> 1].y : acc2[i][j >> 1].x;
+                                aij = fmaf(av[i] * bv[j], expf(-d * d * c2), aij);
                             }
                         }
                 }
             }
             __syncthreads();   // sa / sb are rewritten by the next chunk or tile
+        }
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            acc[i][0] = acc2[i][0].x; acc[i][1] = acc2[i][0].y; acc[i][2] = acc2[i][1].x; acc[i][3] = acc2[i][1].y;
         }
 
         if (nd == 2 && rows16) {

@@ -122,8 +122,8 @@ def test_fields_are_deterministic():
 def test_tma_tiles_equal_plain_tiles_bit_for_bit(sigma, dtype, absolute, pattern):
     """Rows on 16-byte boundaries take the TMA-staged tiles; an odd row pitch takes the plain
     staging.  Both accumulate the same products in the same order, so they agree exactly.
-    "solid" adds a disc and a band of ones touching the border: there the TMA tiles take the
-    constant sums of all-ones windows, which must equal the products they stand for."""
+    "solid" adds a disc and a band of ones touching the border: long runs of all-ones windows,
+    tiles with no zero row, and ones against the image edges."""
     import torch
     rng = np.random.default_rng(int(sigma * 10) + (dtype == "f32"))
     h = (rng.random((197, 203)) < 0.2)

@@ -29,7 +29,7 @@ def _gpu_chamfer(images, align=16):
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 40), (37, 1), (29, 31), (64, 64), (70, 129), (33, 257), (41, 513),
-                                   (17, 1024), (200, 300)])
+                                   (17, 1024), (200, 300), (7, 70), (3, 200), (2, 400), (1, 900), (5, 260)])
 def test_random_images(shape):
     rng = np.random.default_rng(shape[0] * 7919 + shape[1])
     imgs = [(rng.random(shape) < p).astype(np.uint8) for p in (0.5, 0.9, 1.0)]

@@ -206,6 +206,44 @@ def cpu_baseline(name, seconds):
                       f"FP64 C oracle, one thread, {dt:.1f} s"}
 
 
+def original_vs_lattice(name, seconds=8.0, max_images=4):
+    """Context for the paper's per-iteration speed-up of lattice ITC over original ITC (Sec. 4):
+    both updates in the FP64 oracle on one thread, on the first 2-D images of this workload.
+    The original update (Eq. origupdate) sums over every data point for every codebook vector;
+    the lattice step gathers the fields, computed once per image, and sums over codebook pairs."""
+    import oracle
+    images, Ms, params, W0s, ndims, Gs = make_workload(name, 0, n=min(WORKLOADS[name]["n"], max_images))
+    rows, t_start = [], time.perf_counter()
+    for im, M, p, W0, nd in zip(images, Ms, params, W0s, ndims):
+        if nd != 2 or time.perf_counter() - t_start > seconds:
+            continue
+        sigma = p["sigma"]
+        h = im.astype(np.float64)
+        X, hx = oracle.image_points(h)
+        t0 = time.perf_counter()
+        A, Fu, Fv = oracle.fields2d(h, sigma)
+        sxx = oracle.sxx(h, A)
+        t_fields = time.perf_counter() - t0
+        it = 20
+        t0 = time.perf_counter()
+        oracle.lattice_run(A, [Fu, Fv], sxx, sigma, W0, it)
+        t_lat = (time.perf_counter() - t0) / it
+        reps, t0 = 0, time.perf_counter()
+        while reps < 3 and (reps == 0 or time.perf_counter() - t0 < 1.0):
+            oracle.original_step(X, sigma, W0, hx)
+            reps += 1
+        t_orig = (time.perf_counter() - t0) / reps
+        rows.append({"shape": list(im.shape), "data_points": int(X.shape[0]), "M": int(M), "sigma": float(sigma),
+                     "original_ms_per_iter": 1e3 * t_orig, "lattice_ms_per_iter": 1e3 * t_lat,
+                     "fields_ms_once": 1e3 * t_fields, "speedup_per_iter": t_orig / t_lat,
+                     "speedup_run": p["iters"] * t_orig / (t_fields + p["iters"] * t_lat)})
+    if not rows:
+        return None
+    return {"images": rows, "iters": int(params[0]["iters"]), "cores": 1,
+            "note": "FP64 oracle, one thread; speedup_run includes the fields, computed once per image. "
+                    "The paper reports about 100x per iteration (Sec. 4) on its own machine: context only"}
+
+
 # ----------------------------------------------------------------------------------- our arm
 def segment_report(images, seg_ms, world, B, peaks, peak_src):
     """itc_segment over the batch: images/s and its bytes (input once, one int16 label per pixel)
@@ -645,6 +683,9 @@ def run_ours(args, rank, world, local_rank):
         res["batched_over_per_image"] = value / world / per_image["value"]
     if not args.no_cpu_baseline and world == 1:
         res["cpu_baseline"] = cpu_baseline(name, args.cpu_seconds)
+        ovl = original_vs_lattice(name)
+        if ovl:
+            res["cpu_baseline"]["original_vs_lattice"] = ovl
     return res
 
 

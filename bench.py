@@ -77,8 +77,7 @@ def make_workload(name, rank, n=None):
     n = n or w["n"]
     if name == "c3":
         images, Ms, sig = synth.c3_batch(n, start=rank * n)
-        W0s = [synth.init_codebook(synth.rng_for(3, 500_000 + rank * n + i), im.astype(np.float32), int(m))
-               for i, (im, m) in enumerate(zip(images, Ms))]
+        W0s = [synth.c3_codebook(rank * n + i, im, m) for i, (im, m) in enumerate(zip(images, Ms))]
         params = [dict(sigma=float(s), iters=w["iters"]) for s in sig]
         return images, [int(m) for m in Ms], params, W0s, [2] * n, [1] * n
     if name == "c4":
@@ -190,20 +189,61 @@ def oracle_image(im, M, p, W0, ndim, G):
     return W
 
 
+def host_cpu():
+    """(cores, model) of this host: os.cpu_count() and lscpu's model name."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_images_per_s(images, Ms, params, W0s, ndims, Gs, seconds, threads):
+    """The oracle on images taken in order until about `seconds` have passed, on `threads` host
+    threads (one image per thread at a time; the C oracle releases the interpreter lock, so the
+    threads run on separate cores).  Returns (images done, seconds, pixels)."""
+    import concurrent.futures as cf
+    t0 = time.perf_counter()
+    done = 0
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        futs, nxt = set(), 0
+        while nxt < len(images) and len(futs) < threads:
+            futs.add(ex.submit(oracle_image, images[nxt], Ms[nxt], params[nxt], W0s[nxt], ndims[nxt], Gs[nxt]))
+            nxt += 1
+        while futs:
+            fin, futs = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
+            for f in fin:
+                f.result()
+                done += 1
+            if nxt < len(images) and time.perf_counter() - t0 < seconds:
+                while nxt < len(images) and len(futs) < threads:
+                    futs.add(ex.submit(oracle_image, images[nxt], Ms[nxt], params[nxt], W0s[nxt], ndims[nxt],
+                                       Gs[nxt]))
+                    nxt += 1
+    dt = time.perf_counter() - t0
+    return done, dt, sum(images[i].size for i in range(done))
+
+
 def cpu_baseline(name, seconds):
-    """Oracle images/s on the first images of this workload, single thread, ~`seconds` of work."""
+    """Oracle images/s on the first images of this workload: on one thread and on every host core
+    (one image per core), each for about `seconds` of work."""
     import oracle
     oracle.build()
-    images, Ms, params, W0s, ndims, Gs = make_workload(name, 0, n=min(WORKLOADS[name]["n"], 400))
-    done, t0 = 0, time.perf_counter()
-    while done < len(images) and (time.perf_counter() - t0) < seconds:
-        oracle_image(images[done], Ms[done], params[done], W0s[done], ndims[done], Gs[done])
-        done += 1
-    dt = time.perf_counter() - t0
-    px = sum(images[i].size for i in range(done))
-    return {"value": done / dt, "unit": "images/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {done} images of the workload ({px} pixels), fields + iterations + gradient, "
-                      f"FP64 C oracle, one thread, {dt:.1f} s"}
+    oracle.lib()   # loaded once before the threads start
+    cores, model = host_cpu()
+    images, Ms, params, W0s, ndims, Gs = make_workload(name, 0, n=min(WORKLOADS[name]["n"], 1200))
+    d1, t1, px1 = oracle_images_per_s(images, Ms, params, W0s, ndims, Gs, seconds, 1)
+    dn, tn, pxn = oracle_images_per_s(images, Ms, params, W0s, ndims, Gs, seconds, cores)
+    return {"value": dn / tn, "unit": "images/s", "cores": cores, "kind": "oracle", "cpu_model": model,
+            "sample": f"first {dn} images of the workload ({pxn} pixels), fields + iterations + gradient, FP64 C "
+                      f"oracle, one image per thread on {cores} threads, {tn:.1f} s",
+            "single_thread": {"value": d1 / t1, "unit": "images/s", "cores": 1,
+                              "sample": f"first {d1} images ({px1} pixels), one thread, {t1:.1f} s"}}
 
 
 def original_vs_lattice(name, seconds=8.0, max_images=4):
@@ -242,6 +282,91 @@ def original_vs_lattice(name, seconds=8.0, max_images=4):
     return {"images": rows, "iters": int(params[0]["iters"]), "cores": 1,
             "note": "FP64 oracle, one thread; speedup_run includes the fields, computed once per image. "
                     "The paper reports about 100x per iteration (Sec. 4) on its own machine: context only"}
+
+
+# ------------------------------------------------------------------------------- parity sample
+def parity_sample(images, Ms, pk, n=16):
+    """Indices of the timed batch checked against the oracle: its largest image, its costliest
+    image (most pair work, then most pixels), and evenly spaced others."""
+    B = len(images)
+    size = [im.size for im in images]
+    cost = [(Ms[b] * Ms[b], size[b]) for b in range(B)]
+    pick = [int(np.argmax(size)), max(range(B), key=lambda b: cost[b])]
+    for b in np.linspace(0, B - 1, n, dtype=int):
+        if int(b) not in pick and len(pick) < n:
+            pick.append(int(b))
+    return sorted(set(pick))
+
+
+def parity_report(images, Ms, pk, W0s, ndims, Gs, snap, idx):
+    """The timed batch's results on the sampled images against the FP64 oracle, with the tests'
+    bars: fields element-wise (A within 1e-5 relative, centred moments within 1e-5 R A); final
+    codebooks equal where the oracle trajectory has no rounding tie (within 1e-4 of a half-integer);
+    D_cs within 4e-5; the gradient at the returned codebooks normwise (1e-4), and dD/dh
+    element-wise within 3e-5 of its two terms.  2-D images only (3-D: codebooks and D_cs)."""
+    import concurrent.futures as cf
+
+    import oracle
+    oracle.lib()
+
+    def one(b):
+        p, nd = pk[b], ndims[b]
+        sigma, iters = p["sigma"], p["iters"]
+        Wg = snap["W"][b]
+        r = {}
+        if nd == 2:
+            h = images[b].astype(np.float64)
+            A, Fu, Fv = oracle.fields2d(h, sigma)
+            R = oracle.radius(sigma)
+            F = snap["fields"][b]
+            pos = A > 0
+            r["zeros_equal"] = bool(np.array_equal(F[0] == 0, A == 0))
+            r["A_rel"] = float(np.max(np.abs(F[0][pos] - A[pos]) / A[pos])) if pos.any() else 0.0
+            r["F_ratio"] = float(max(np.max(np.abs(F[1 + i][pos] - f[pos]) / (1e-5 * R * A[pos])) if pos.any() else 0.0
+                                     for i, f in enumerate((Fu, Fv))))
+            sxx = oracle.sxx(h, A)
+            Wo, dcs, tie, _ = oracle.lattice_run(A, [Fu, Fv], sxx, sigma, W0s[b], iters)
+            gref, ghref, sums = oracle.dcs_grad2d_dense(h, sigma, Wg.astype(np.float64), A=A)
+            r["gW_rel"] = float(np.linalg.norm(snap["gW"][b] - gref) / max(np.linalg.norm(gref), 1e-300))
+            gh = snap["gh"][b].astype(np.float64)
+            r["gh_rel"] = float(np.linalg.norm(gh - ghref) / max(np.linalg.norm(ghref), 1e-300))
+            t1 = 2.0 * A / sums[2]
+            tol = 3e-5 * (np.abs(t1) + np.abs(t1 - ghref))
+            err = np.abs(gh - ghref)
+            r["gh_ratio"] = float(np.max(np.where(tol > 0, err / np.where(tol > 0, tol, 1.0), np.where(err > 0, np.inf, 0.0))))
+        else:
+            A, Fu, Fv, Fg = oracle.fields3d(images[b], Gs[b], sigma)
+            occ = np.zeros((Gs[b],) + images[b].shape)
+            uu, vv = np.meshgrid(np.arange(images[b].shape[0]), np.arange(images[b].shape[1]), indexing="ij")
+            occ[images[b], uu, vv] = 1.0
+            Wo, dcs, tie, _ = oracle.lattice_run(A, [Fu, Fv, Fg], float((occ * A).sum()), sigma, W0s[b], iters)
+        r["tied"] = bool(len(tie) and tie.min() <= 1e-4)
+        r["equal"] = bool(np.array_equal(Wg, Wo))
+        r["dcs_err"] = None if r["tied"] else float(abs(snap["stats"][b]["dcs"] - dcs[-1]))
+        return r
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        rows = list(ex.map(one, idx))
+    two = [r for r in rows if "A_rel" in r]
+    untied = [r for r in rows if not r["tied"]]
+    out = {"images": len(idx), "indices": idx,
+           "codebooks_equal": sum(r["equal"] for r in rows),
+           "codebooks_tied": sum(r["tied"] for r in rows),
+           "codebooks_differ_untied": sum((not r["equal"]) for r in untied),
+           "dcs_max_abs_err": max([r["dcs_err"] for r in untied], default=None)}
+    if two:
+        out.update({"fields_A_max_rel_err": max(r["A_rel"] for r in two),
+                    "fields_moment_max_over_bound": max(r["F_ratio"] for r in two),
+                    "fields_zero_pattern_equal": all(r["zeros_equal"] for r in two),
+                    "grad_W_max_rel": max(r["gW_rel"] for r in two),
+                    "grad_h_max_rel": max(r["gh_rel"] for r in two),
+                    "grad_h_max_over_elementwise_bound": max(r["gh_ratio"] for r in two)})
+    out["bars"] = ("A 1e-5 relative; moments 1e-5 R A (ratio <= 1); codebooks equal unless the oracle "
+                   "trajectory has a tie within 1e-4 of a half-integer; D_cs 4e-5; gradients normwise 1e-4, "
+                   "dD/dh element-wise 3e-5 of its two terms (ratio <= 1)")
+    out["note"] = ("results of the timed step on a sample of the timed batch (its largest and costliest "
+                   "images and evenly spaced others), checked after the timed region")
+    return out
 
 
 # ----------------------------------------------------------------------------------- our arm
@@ -377,6 +502,51 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ms = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
     ms_step = ms / args.steps
+
+    # the timed batch's results on a sample of its images, for the parity report (checked against
+    # the oracle after every timing is done)
+    snap = None
+    if rank == 0 and not args.no_parity:
+        pidx = parity_sample(images, Ms, pk)
+        Wn, gWn, ghn = plan.unpack_W(W), plan.unpack_W(gW), plan.unpack_pixels(gh)
+        snap = {"idx": pidx, "W": {b: Wn[b].copy() for b in pidx}, "gW": {b: gWn[b].copy() for b in pidx},
+                "gh": {b: ghn[b].copy() for b in pidx}, "stats": itc.stats_to_numpy(stats),
+                "fields": {b: plan.fields_of(b)[:, 0, :, :images[b].shape[1]].cpu().numpy().copy()
+                           for b in pidx if ndims[b] == 2}}
+
+    # the same step with the fields recomputed under a memory budget (itc_run_budget +
+    # itc_backward_budget in a workspace of an eighth of the stored fields), results compared
+    # with the stored-fields step bit for bit
+    budget = None
+    if not args.no_budget:
+        ref = (W.clone(), gW.clone(), gh.clone())
+        bws = itc.budget_workspace(plan, plan.ws_bytes // 8)
+        bW, bgW, bgh = torch.empty_like(W), torch.empty_like(gW), torch.empty_like(gh)
+        bst = itc.new_stats(B, dev)
+
+        def budget_step():
+            bW.copy_(W0)
+            itc.run_budget(plan, bW, bws, bst)
+            itc.backward_budget(plan, bW, bws, grad_W=bgW, grad_h=bgh)
+
+        for _ in range(args.warmup):
+            budget_step()
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.steps):
+            budget_step()
+        q1.record(stream)
+        torch.cuda.synchronize()
+        bms = q0.elapsed_time(q1) / args.steps
+        same = bool(torch.equal(bW, ref[0]) and torch.equal(bgW, ref[1]) and torch.equal(bgh, ref[2]))
+        budget = {"value": world * B / (bms / 1000.0), "unit": "images/s", "ms_per_step": bms,
+                  "workspace_bytes": int(bws.numel()), "stored_workspace_bytes": int(plan.ws_bytes),
+                  "time_over_stored_step": bms / ms_step, "equal_to_stored_fields_bit_for_bit": same,
+                  "note": "itc_run_budget + itc_backward_budget: the fields of each image range recomputed in "
+                          "a window (an eighth of the batch's fields) in the forward and again in the backward; "
+                          "iterations one image per CTA per range"}
+        del bws, bW, bgW, bgh, bst, ref
     f_ms = [e[0].elapsed_time(e[1]) for e in ev]
     i_ms = [e[1].elapsed_time(e[2]) for e in ev]
     b_ms = [e[2].elapsed_time(e[3]) for e in ev]
@@ -694,6 +864,10 @@ def run_ours(args, rank, world, local_rank):
     if per_image:
         res["per_image_launch"] = per_image
         res["batched_over_per_image"] = value / world / per_image["value"]
+    if budget:
+        res["budget"] = budget
+    if snap is not None:
+        res["parity"] = parity_report(images, Ms, pk, W0s, ndims, Gs, snap, snap["idx"])
     if not args.no_cpu_baseline and world == 1:
         res["cpu_baseline"] = cpu_baseline(name, args.cpu_seconds)
         ovl = original_vs_lattice(name)
@@ -708,15 +882,19 @@ def run_reference(args, rank):
     workload (the first --ref-images images)."""
     if rank != 0:
         return None
+    import concurrent.futures as cf
+
     import oracle
     oracle.build()
+    oracle.lib()
     name = args.workload
-    n = min(args.ref_images, WORKLOADS[name]["n"])
+    cores, model = host_cpu()
+    n = min(args.ref_images or 2 * cores, WORKLOADS[name]["n"])
     images, Ms, pk, W0s, ndims, Gs = make_workload(name, 0, n=max(n, 1))
+    pool = cf.ThreadPoolExecutor(max_workers=cores)
 
-    def step():
-        for b in range(n):
-            oracle_image(images[b], Ms[b], pk[b], W0s[b], ndims[b], Gs[b])
+    def step():   # one image per host thread at a time (the C oracle releases the interpreter lock)
+        list(pool.map(lambda b: oracle_image(images[b], Ms[b], pk[b], W0s[b], ndims[b], Gs[b]), range(n)))
 
     for _ in range(args.warmup):
         step()
@@ -724,14 +902,16 @@ def run_reference(args, rank):
     for _ in range(args.steps):
         step()
     dt = (time.perf_counter() - t0) / args.steps
+    pool.shutdown()
     v = n / dt
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "images/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000.0, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{name}: {WORKLOADS[name]['desc']}", "images_per_step": n},
-        "cpu_baseline": {"value": v, "unit": "images/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {n} images of the workload per step, FP64 C oracle, one thread"},
+        "cpu_baseline": {"value": v, "unit": "images/s", "cores": cores, "kind": "oracle", "cpu_model": model,
+                         "sample": f"first {n} images of the workload per step, FP64 C oracle, one image per "
+                                   f"thread on {cores} threads"},
         "e2e": {"value": v, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -747,14 +927,16 @@ def main():
     ap.add_argument("--per-image-n", type=int, default=512)
     ap.add_argument("--no-per-image", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-images", type=int, default=8)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--ref-images", type=int, default=None, help="images per reference step (default 2 x cores)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default fields configuration")
     ap.add_argument("--e2e-chunks", type=int, default=4, help="image ranges of the staged end-to-end step")
     ap.add_argument("--no-schedule", action="store_true", help="skip the Sec. 4 width-schedule timing")
     ap.add_argument("--fields-ctas", type=int, default=None,
                     help="persistent fields CTAs per SM after tuning (room for overlapping iterations)")
     ap.add_argument("--chunks", type=int, default=1, help="image ranges of the pipelined fields/iterations")
+    ap.add_argument("--no-parity", action="store_true", help="skip the oracle check of a sample of the timed batch")
+    ap.add_argument("--no-budget", action="store_true", help="skip the step with the fields recomputed under a budget")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else max(args.warmup, 1)
 

@@ -68,10 +68,14 @@ extern "C" {
                                   two damped sinusoids, untruncated, cost independent of sigma;
                                   no radius limit.  itc_fields rejects it (ITC_ERR_UNSUPPORTED);
                                   itc_backward rejects plans that use it */
-#define ITC_TEST_STALL_WAIT 256 /* test hook (itc_fields, tensor-tile path only): the first tile
-                                  copy of the first CTA is never started, so that CTA's bounded
-                                  wait (about one second) runs out; the call then reports
-                                  S_XX = NaN and nothing else is affected.  Never set otherwise. */
+#define ITC_TEST_STALL_WAIT 256 /* test hook (tensor-tile fields path only): the first tile copy
+                                  of the first CTA of the fields launch is never started, so that
+                                  CTA's bounded wait (about one second) runs out.  itc_fields then
+                                  reports ITC_ERR_TIMEOUT in its workspace status word and
+                                  S_XX = NaN; in a plan (any image of a fields launch carrying the
+                                  flag arms it) the images of that CTA's tiles get the status
+                                  ITC_ERR_TIMEOUT in itc_stats.  Nothing else is affected and the
+                                  GPU stays usable.  Never set otherwise. */
 
 /* Limits of this build. */
 #define ITC_MAX_RADIUS_UV 32   /* R_u, R_v */
@@ -119,7 +123,9 @@ typedef struct {
     int empty;           /* codebooks with no data in their window in the last evaluation */
     int moved;           /* codebooks moved by the last update */
     int iters_done;      /* updates applied */
-    int status;          /* ITC_OK, ITC_WARN_EMPTY_SUPPORT or ITC_ERR_NONFINITE */
+    int status;          /* ITC_OK, ITC_WARN_EMPTY_SUPPORT, ITC_ERR_NONFINITE, or ITC_ERR_TIMEOUT
+                            when a bounded wait of the image's fields pass gave up (its fields are
+                            then incomplete and S_XX is NaN) */
 } itc_stats;
 
 /* --------------------------------------------------------------- parameters from xi, omega */
@@ -149,7 +155,8 @@ int itc_field_pitch(int W);
  * 0 if img is invalid. */
 size_t itc_fields_bytes(const itc_image* img);
 
-/* Scratch bytes itc_fields needs for `img` (per-tile S_XX partial sums); 0 if invalid. */
+/* Scratch bytes itc_fields needs for `img` (a 256-byte status slot, then per-tile S_XX partial
+ * sums); 0 if invalid. */
 size_t itc_fields_workspace_bytes(const itc_image* img);
 
 /* Message for a status code (static string). */
@@ -164,7 +171,11 @@ const char* itc_status_string(int code);
  *   p      : sigma, trunc and ITC_FIELDS_ABSOLUTE are used
  *   fields : device, itc_fields_bytes(img) bytes, 16-byte aligned; written
  *   sxx    : device double, written (may be NULL)
- *   ws     : device scratch of itc_fields_workspace_bytes(img) bytes, 16-byte aligned
+ *   ws     : device scratch of itc_fields_workspace_bytes(img) bytes, 16-byte aligned.  Its first
+ *            int is the call's device status, written on the stream: ITC_OK, or ITC_ERR_TIMEOUT
+ *            when a bounded wait of the fields pass gave up (the fields of the tiles its CTA still
+ *            owned are then not written, and S_XX is NaN).  It is the only signal when sxx is
+ *            NULL; read it after the stream has reached the call.
  * Errors: ITC_ERR_INVALID_ARG (bad image/params/pointer), ITC_ERR_WORKSPACE, ITC_ERR_CUDA.
  */
 int itc_fields(const itc_image* img, const itc_params* p, float* fields, double* sxx,
@@ -175,15 +186,17 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
  * has no counterpart: this is a deployment variant.  Some hosts give a library only the input
  * and output buffers and forbid any allocation while they run (plugin and real-time hosts with
  * a fixed memory budget, or code that must not call cudaMalloc while it records work); they
- * cannot provide itc_fields' scratch.  This entry point keeps that scratch (one double per
- * fields tile) in a fixed device array inside the library, ITC_NOALLOC_MAX_TILES doubles
- * (512 KiB), which every GPU that loads the library holds until the process exits.
+ * cannot provide itc_fields' scratch.  This entry point keeps that scratch (a status slot and
+ * one double per fields tile) in a fixed device array inside the library, 256 bytes plus
+ * ITC_NOALLOC_MAX_TILES doubles (512 KiB), which every GPU that loads the library holds until
+ * the process exits.  A bounded wait that gives up shows here only as S_XX = NaN (pass sxx).
  *   Same arguments and results as itc_fields, without ws / ws_bytes.  Allocates nothing.
  *   The first call on each device looks up the array's device address (cudaGetSymbolAddress,
  *   with that device current); make that first call before any stream capture.
  *   All calls share the one array: calls whose work overlaps on a GPU (other streams, other
  *   host threads) race on it and must be serialised by the caller.  The array keeps the last
- *   call's partial sums; each call overwrites every entry it reads, so nothing is cleared.
+ *   call's partial sums; each call sets its status word to ITC_OK first and overwrites every
+ *   partial it reads, so nothing else is cleared.
  * Errors: ITC_ERR_UNSUPPORTED if the image needs more than ITC_NOALLOC_MAX_TILES tiles (2-D:
  * ceil(H/64) ceil(W/64); 3-D: ceil(H/32) ceil(W/64) ceil(G/8)); otherwise as itc_fields.
  */
@@ -418,6 +431,48 @@ int itc_segment(const void* plan_host, const void* plan_dev, const float* W, sho
 int itc_backward(const void* plan_host, const void* plan_dev, const float* W,
                  const float* grad_dcs, float* grad_W, float* grad_h, itc_stats* stats, void* ws,
                  size_t ws_bytes, void* stream);
+
+/* ----------------------------------------------------- fields recomputed under a memory budget */
+/*
+ * When the fields of a whole batch do not fit in device memory (every image's ndim+1 FP32 planes:
+ * 12 bytes per pixel of a 2-D batch, e.g. about 4 GB for 4096 images of up to 512 x 512), the
+ * budgeted calls keep no fields between calls.  Their workspace holds the batch's S_XX partials,
+ * per-image scalars and status words (a few bytes per image and per tile) plus a window of any
+ * size that holds the fields of at least the largest image; the batch is cut into consecutive
+ * image ranges whose fields fit the window, and each range's fields (step 2 of Algorithm 1,
+ * Sec. 3.1) are computed into the window just before they are used.  The results are those of
+ * the stored-fields calls bit for bit: the same fields kernels, tile configuration and
+ * summation order, range by range.
+ */
+
+/* Workspace bytes for the budgeted calls within a total of budget_bytes: budget_bytes rounded
+ * down to a multiple of 256, raised to the smallest workspace they accept (the batch's partials,
+ * scalars and status words plus the fields of its largest image); 0 gives that smallest
+ * workspace.  The window is what the workspace holds beyond that fixed part: the larger it is,
+ * the fewer and larger the ranges.  0 if the plan is invalid. */
+size_t itc_plan_budget_bytes(const void* plan_host, size_t budget_bytes);
+
+/*
+ * itc_run_budget -- itc_run with the fields recomputed range by range in the window: per range,
+ * the fields pass and then the iterations of its images (one image per CTA).  Same arguments
+ * and results as itc_run; ws of ws_bytes >= itc_plan_budget_bytes(plan, 0), 256-byte aligned.
+ * The fields are not left in ws: follow it with itc_backward_budget, not itc_backward.
+ * Errors: ITC_ERR_INVALID_ARG, ITC_ERR_WORKSPACE (smaller than the smallest budget), ITC_ERR_CUDA.
+ */
+int itc_run_budget(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
+                   size_t ws_bytes, void* stream);
+
+/*
+ * itc_backward_budget -- itc_backward (the gradient of Eq. (1), weighted ITC of Sec. 5) with A
+ * and S_XX recomputed range by range in the window instead of read from a stored fields pass:
+ * per range, the fields pass, then the codebook and pixel kernels of the backward for its
+ * images.  Same arguments and results as itc_backward (bit for bit); ws as for itc_run_budget.
+ * It needs no earlier call: everything it reads is computed inside it.
+ * Errors: as itc_run_budget; ITC_ERR_UNSUPPORTED for plans with recursive fields.
+ */
+int itc_backward_budget(const void* plan_host, const void* plan_dev, const float* W,
+                        const float* grad_dcs, float* grad_W, float* grad_h, itc_stats* stats,
+                        void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,7 @@ using namespace itc;
 namespace {
 
 constexpr int kGridTileH2 = 64;   // fields tile height, 2-D
+constexpr size_t kFieldsStatusBytes = 256;   // itc_fields scratch: the status word's slot
 constexpr int kGridTileH3 = 32;   // fields tile height, 3-D
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.f; }
@@ -310,6 +311,44 @@ const PlanHeader* plan_of(const void* plan_host) {
     return h;
 }
 
+// Where a plan's kernels find their scratch: the base from which every image's field_off (and
+// self_off) counts, the S_XX partials, the backward scalars and the per-image status words.
+struct WsView {
+    float* fields;
+    double* partials;
+    double* scal;
+    int* status;
+};
+
+// The full workspace: [fields of every image][partials][scalars][status words].
+WsView full_view(const PlanHeader* h, void* ws) {
+    unsigned char* w = reinterpret_cast<unsigned char*>(ws);
+    return {reinterpret_cast<float*>(w + h->ws_fields_off), reinterpret_cast<double*>(w + h->ws_partials_off),
+            reinterpret_cast<double*>(w + h->ws_scal_off), reinterpret_cast<int*>(w + h->ws_status_off)};
+}
+
+// The budgeted workspace: the tail of the full layout ([partials][scalars][status words], for the
+// whole batch) and then a window that holds the fields of one image range at a time.
+size_t budget_tail_bytes(const PlanHeader* h) { return (size_t)(h->ws_bytes - h->ws_partials_off); }
+
+// Floats of image b's fields span (its planes, scratch planes and A_s plane).
+long long field_span(const PlanHeader* h, const ImageDesc* d, int b) {
+    return (b + 1 < h->B ? d[b + 1].field_off : h->fields_floats) - d[b].field_off;
+}
+
+// The view of a budgeted workspace while the window holds the fields of the images from b0 on:
+// the fields base is the window moved back by image b0's offset, so that base + field_off of
+// those images lands inside the window (integer arithmetic; the kernels add the offsets back).
+WsView budget_view(const PlanHeader* h, void* ws, const ImageDesc* hdescs, int b0) {
+    unsigned char* w = reinterpret_cast<unsigned char*>(ws);
+    const size_t tail = budget_tail_bytes(h);
+    const uintptr_t window = reinterpret_cast<uintptr_t>(w + tail);
+    const uintptr_t shift = (uintptr_t)hdescs[b0].field_off * sizeof(float);
+    return {reinterpret_cast<float*>(window - shift), reinterpret_cast<double*>(w),
+            reinterpret_cast<double*>(w + (h->ws_scal_off - h->ws_partials_off)),
+            reinterpret_cast<int*>(w + (h->ws_status_off - h->ws_partials_off))};
+}
+
 }  // namespace
 
 extern "C" {
@@ -330,7 +369,8 @@ size_t itc_fields_workspace_bytes(const itc_image* img) {
     p.trunc = 1.f;
     ImageDesc d;
     fill_desc(img, &p, 1, &d);
-    return align_up((size_t)tiles_of(d) * sizeof(double), 256);
+    // the call's device status word (first 256 bytes), then one S_XX partial per tile
+    return kFieldsStatusBytes + align_up((size_t)tiles_of(d) * sizeof(double), 256);
 }
 
 const char* itc_status_string(int code) {
@@ -361,7 +401,8 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
     make_taps(p, img->ndim, &L.taps);
     fill_desc(img, p, 1, &L.one);
     L.fields = fields;
-    L.partials = reinterpret_cast<double*>(ws);
+    L.status = reinterpret_cast<int*>(ws);
+    L.partials = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(ws) + kFieldsStatusBytes);
     L.tile_h = tile_h_of(img->ndim);
     L.absolute = (p->flags & ITC_FIELDS_ABSOLUTE) ? 1 : 0;
     L.test_stall = (p->flags & ITC_TEST_STALL_WAIT) ? 1 : 0;
@@ -370,6 +411,8 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool tma = fields_tma_supported(img->ndim, L.taps.R[0], L.taps.R[1]) &&
                      encode_input_map(img, L.taps.R[0], &L.tmap_one);
+    rc = cuda_status(cudaMemsetAsync(L.status, 0, sizeof(int), s));   // ITC_OK unless a wait gives up
+    if (rc) return rc;
     rc = cuda_status(launch_fields_any(L, tma, 0, (int)nt, L.taps.R[0], L.taps.R[1], img->ndim, img->dtype, s));
     if (rc) return rc;
     if (sxx && has_self_pass(p, img->ndim)) {
@@ -495,6 +538,13 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         const bool rec = (d.flags & ITC_RECURSIVE) != 0;
         foff += (long long)align_up((size_t)(d.ndim + 1 + (rec ? 2 : 0)) * d.plane_floats, 64);
         if (rec) h->has_recursive = 1;
+        // then the A_s plane of an image with a self-overlap pass (plus one scratch plane for
+        // recursive fields): every image's scratch is one contiguous span, so the spans of an
+        // image range are contiguous too (the budgeted calls recompute them range by range)
+        if (d.self_cls >= 0) {
+            d.self_off = foff;
+            foff += (long long)align_up((size_t)(rec ? 2 : 1) * d.plane_floats, 64);
+        }
         d.w_off = woff;
         woff += (long long)d.M * d.ndim;
         d.gh_off = ghoff;
@@ -507,13 +557,6 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
         h->max_dim[1] = d.W > h->max_dim[1] ? d.W : h->max_dim[1];
         h->max_dim[2] = d.G > h->max_dim[2] ? d.G : h->max_dim[2];
         h->ndim_mask |= 1 << d.ndim;
-    }
-    // A_s planes of the images with a self-overlap pass
-    for (int b = 0; b < B; ++b) {
-        ImageDesc& d = descs[b];
-        if (d.self_cls < 0) continue;
-        d.self_off = foff;   // A_s (plus one scratch plane for recursive fields)
-        foff += (long long)align_up((size_t)((d.flags & ITC_RECURSIVE) ? 2 : 1) * d.plane_floats, 64);
     }
     h->fields_floats = foff;
     h->total_pixels = ghoff;
@@ -592,7 +635,7 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     h->run_groups_off = run_off;
     h->bwd_tiles = bwd;
 
-    // workspace: [fields][S_XX partials][per-image backward scalars]
+    // workspace: [fields][S_XX partials][per-image backward scalars][per-image status words]
     size_t off = 0;
     h->ws_fields_off = 0;
     off = align_up((size_t)foff * sizeof(float), 256);
@@ -600,6 +643,8 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     off = align_up(off + (size_t)pbase * sizeof(double), 256);
     h->ws_scal_off = (long long)off;
     off = align_up(off + (size_t)B * 4 * sizeof(double), 256);
+    h->ws_status_off = (long long)off;
+    off = align_up(off + (size_t)B * sizeof(int), 256);
     h->ws_bytes = (long long)off;
     if (ws_bytes_out) *ws_bytes_out = off;
     memcpy(plan, buf.data(), need);
@@ -621,23 +666,26 @@ int itc_plan_offsets(const void* plan_host, int b, size_t* field_off, size_t* w_
     return ITC_OK;
 }
 
-int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, int b1, void* ws, size_t ws_bytes,
-                         void* stream) {
-    const PlanHeader* h = plan_of(plan_host);
-    if (!h || !plan_dev || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
-    if (b0 < 0 || b1 > h->B || b0 > b1) return ITC_ERR_INVALID_ARG;
-    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+// The fields pass (every class) of images [b0, b1) into the scratch of view v.
+static int fields_range(const PlanHeader* h, const void* plan_host, const void* plan_dev, int b0, int b1,
+                        const WsView& v, cudaStream_t s) {
     const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
     const int* hints = reinterpret_cast<const int*>(reinterpret_cast<const unsigned char*>(plan_host) + h->ints_off);
     const ImageDesc* descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
     const int* ints = reinterpret_cast<const int*>(pd + h->ints_off);
-    unsigned char* w = reinterpret_cast<unsigned char*>(ws);
+    const ImageDesc* hdescs = reinterpret_cast<const ImageDesc*>(reinterpret_cast<const unsigned char*>(plan_host) +
+                                                                 h->desc_off);
+    // the images' status words start at ITC_OK; a fields CTA whose bounded wait gives up sets them
+    if (b1 > b0 && cudaMemsetAsync(v.status + b0, 0, (size_t)(b1 - b0) * sizeof(int), s) != cudaSuccess)
+        return ITC_ERR_CUDA;
     for (int c = 0; c < h->ncls; ++c) {
         const ClassInfo& ci = h->cls[c];
         const int p0 = lower_pos(hints + ci.list_off, ci.nimg, b0), p1 = lower_pos(hints + ci.list_off, ci.nimg, b1);
         const int t0 = hints[ci.prefix_off + p0], t1 = hints[ci.prefix_off + p1];
         if (t1 <= t0) continue;
+        // test hook: an image of the launch asks for the stalled first copy (tensor tiles only)
+        int stall = 0;
+        for (int q = p0; q < p1 && !stall; ++q) stall = (hdescs[hints[ci.list_off + q]].flags & ITC_TEST_STALL_WAIT) != 0;
         FieldsLaunch L;
         memset(&L, 0, sizeof(L));
         L.taps = ci.taps;
@@ -645,13 +693,15 @@ int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, in
         L.img_list = ints + ci.list_off;
         L.tile_prefix = ints + ci.prefix_off;
         L.nimg = ci.nimg;
-        L.fields = reinterpret_cast<float*>(w + h->ws_fields_off);
-        L.partials = reinterpret_cast<double*>(w + h->ws_partials_off);
+        L.fields = v.fields;
+        L.partials = v.partials;
         L.tile_h = ci.tile_h;
         L.absolute = 0;
         L.tmaps = reinterpret_cast<const CUtensorMap*>(pd + h->tmap_off);
         L.grid_per_sm = ci.grid_per_sm;
         L.mode = ci.self ? 1 : 0;
+        L.status = v.status;
+        L.test_stall = stall;
         int rc;
         if (ci.recursive) {
             RecursiveLaunch R;
@@ -669,6 +719,15 @@ int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, in
         if (rc) return rc;
     }
     return ITC_OK;
+}
+
+int itc_run_fields_range(const void* plan_host, const void* plan_dev, int b0, int b1, void* ws, size_t ws_bytes,
+                         void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (b0 < 0 || b1 > h->B || b0 > b1) return ITC_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    return fields_range(h, plan_host, plan_dev, b0, b1, full_view(h, ws), reinterpret_cast<cudaStream_t>(stream));
 }
 
 int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int reps, void* stream) {
@@ -706,6 +765,7 @@ int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int
         L.tmaps = reinterpret_cast<const CUtensorMap*>(pd + h->tmap_off);
         L.grid_per_sm = ci.grid_per_sm;
         L.mode = ci.self ? 1 : 0;
+        L.status = reinterpret_cast<int*>(w + h->ws_status_off);
         const bool tma = ci.tma && !ci.use_plain;
         for (int i = 0; i <= reps; ++i) {   // the first launch warms caches and is not timed
             if (i == 1 && cudaEventRecord(e0, s) != cudaSuccess) return ITC_ERR_CUDA;
@@ -885,27 +945,24 @@ int itc_run_iterate_range(const void* plan_host, const void* plan_dev, int b0, i
     return run_iterate_images(plan_host, plan_dev, b0, b1, false, W, stats, ws, ws_bytes, stream);
 }
 
-// images [b0, b1) in order, or (whole) every image of the plan in the plan's iteration order
-static int run_iterate_images(const void* plan_host, const void* plan_dev, int b0, int b1, bool whole, float* W,
-                              itc_stats* stats, void* ws, size_t ws_bytes, void* stream) {
-    const PlanHeader* h = plan_of(plan_host);
-    if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
-    if (b0 < 0 || b1 > h->B || b0 > b1) return ITC_ERR_INVALID_ARG;
-    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+// The iterations of images [b0, b1) in order (one image per CTA), or (whole) of every image of the
+// plan in the plan's iteration order (grouped CTAs), on the fields of view v.
+static int iterate_images(const PlanHeader* h, const void* plan_dev, int b0, int b1, bool whole, float* W,
+                          itc_stats* stats, const WsView& v, cudaStream_t s) {
     if (b1 == b0) return ITC_OK;
     const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
-    unsigned char* w = reinterpret_cast<unsigned char*>(ws);
     RunLaunch R;
     memset(&R, 0, sizeof(R));
     R.descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
-    R.fields = reinterpret_cast<const float*>(w + h->ws_fields_off);
-    R.partials = reinterpret_cast<const double*>(w + h->ws_partials_off);
+    R.fields = v.fields;
+    R.partials = v.partials;
     R.W_in = W;
     R.W_out = W;
     R.stats = stats;
     R.absolute = 0;
     R.final_eval = 1;
     R.img_base = b0;
+    R.img_status = v.status;
     const bool grouped = whole && b0 == 0 && b1 == h->B;
     const int* groups = reinterpret_cast<const int*>(pd + h->ints_off) + h->run_groups_off;
     for (int nd = 2; nd <= 3; ++nd) {
@@ -916,10 +973,19 @@ static int run_iterate_images(const void* plan_host, const void* plan_dev, int b
             R.groups = groups + (nd == 3 ? (size_t)h->run_ngroups[0] * kGroupInts : 0);
             ctas = h->run_ngroups[nd - 2];
         }
-        const int rc = cuda_status(launch_run(R, ctas, h->max_M, h->max_dim, reinterpret_cast<cudaStream_t>(stream), nd));
+        const int rc = cuda_status(launch_run(R, ctas, h->max_M, h->max_dim, s, nd));
         if (rc) return rc;
     }
     return ITC_OK;
+}
+
+static int run_iterate_images(const void* plan_host, const void* plan_dev, int b0, int b1, bool whole, float* W,
+                              itc_stats* stats, void* ws, size_t ws_bytes, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (b0 < 0 || b1 > h->B || b0 > b1) return ITC_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    return iterate_images(h, plan_dev, b0, b1, whole, W, stats, full_view(h, ws), reinterpret_cast<cudaStream_t>(stream));
 }
 
 int itc_run_fields(const void* plan_host, const void* plan_dev, void* ws, size_t ws_bytes, void* stream) {
@@ -1037,6 +1103,46 @@ int itc_run(const void* plan_host, const void* plan_dev, float* W, itc_stats* st
     return itc_run_iterate(plan_host, plan_dev, W, stats, ws, ws_bytes, stream);
 }
 
+// The backward of images [b0, b1) (whole: every image, in the plan's backward order) on the
+// fields and S_XX partials of view v.
+static int backward_images(const PlanHeader* h, const void* plan_host, const void* plan_dev, int b0, int b1,
+                           bool whole, const float* W, const float* grad_dcs, float* grad_W, float* grad_h,
+                           itc_stats* stats, const WsView& v, cudaStream_t s) {
+    if (b1 == b0) return ITC_OK;
+    const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
+    BackwardLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
+    L.fields = v.fields;
+    L.partials = v.partials;
+    L.W = W;
+    L.grad_dcs = grad_dcs;
+    L.grad_W = grad_W;
+    L.grad_h = grad_h;
+    L.stats = stats;
+    L.scal = v.scal;
+    L.B = h->B;
+    L.img_status = v.status;
+    if (whole) {
+        L.bwd_order = reinterpret_cast<const int*>(pd + h->ints_off) + h->bwd_order_off;
+        return cuda_status(launch_backward(L, h->B, h->max_M, h->bwd_tiles, h->max_bwd_tiles, s));
+    }
+    // an image range: its CTAs in image order
+    const ImageDesc* hd = reinterpret_cast<const ImageDesc*>(reinterpret_cast<const unsigned char*>(plan_host) +
+                                                             h->desc_off);
+    long long tiles = 0;
+    int max_tiles = 0, max_M = 0;
+    for (int b = b0; b < b1; ++b) {
+        const int t = hd[b].bwd_tiles_u * hd[b].bwd_tiles_v;
+        tiles += t;
+        max_tiles = std::max(max_tiles, t);
+        max_M = std::max(max_M, hd[b].M);
+    }
+    L.bwd_order = nullptr;
+    L.img_base = b0;
+    return cuda_status(launch_backward(L, b1 - b0, max_M, tiles, max_tiles, s));
+}
+
 int itc_backward(const void* plan_host, const void* plan_dev, const float* W, const float* grad_dcs,
                  float* grad_W, float* grad_h, itc_stats* stats, void* ws, size_t ws_bytes, void* stream) {
     const PlanHeader* h = plan_of(plan_host);
@@ -1044,23 +1150,83 @@ int itc_backward(const void* plan_host, const void* plan_dev, const float* W, co
     if (!ws || ws_bytes < (size_t)h->ws_bytes || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
     // the adjoint stamps truncated kernel boxes; recursive fields have none
     if (h->has_recursive) return ITC_ERR_UNSUPPORTED;
-    const unsigned char* pd = reinterpret_cast<const unsigned char*>(plan_dev);
-    unsigned char* w = reinterpret_cast<unsigned char*>(ws);
-    BackwardLaunch L;
-    memset(&L, 0, sizeof(L));
-    L.descs = reinterpret_cast<const ImageDesc*>(pd + h->desc_off);
-    L.fields = reinterpret_cast<const float*>(w + h->ws_fields_off);
-    L.partials = reinterpret_cast<const double*>(w + h->ws_partials_off);
-    L.W = W;
-    L.grad_dcs = grad_dcs;
-    L.grad_W = grad_W;
-    L.grad_h = grad_h;
-    L.stats = stats;
-    L.scal = reinterpret_cast<double*>(w + h->ws_scal_off);
-    L.bwd_order = reinterpret_cast<const int*>(pd + h->ints_off) + h->bwd_order_off;
-    L.B = h->B;
-    return cuda_status(launch_backward(L, h->B, h->max_M, h->bwd_tiles, h->max_bwd_tiles,
-                                       reinterpret_cast<cudaStream_t>(stream)));
+    return backward_images(h, plan_host, plan_dev, 0, h->B, true, W, grad_dcs, grad_W, grad_h, stats,
+                           full_view(h, ws), reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------------ budgeted (recomputing) calls
+
+size_t itc_plan_budget_bytes(const void* plan_host, size_t budget_bytes) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h) return 0;
+    const ImageDesc* d = reinterpret_cast<const ImageDesc*>(reinterpret_cast<const unsigned char*>(plan_host) +
+                                                            h->desc_off);
+    long long largest = 0;
+    for (int b = 0; b < h->B; ++b) largest = std::max(largest, field_span(h, d, b));
+    const size_t least = budget_tail_bytes(h) + align_up((size_t)largest * sizeof(float), 256);
+    return std::max(budget_bytes / 256 * 256, least);
+}
+
+// Cuts the plan into image ranges whose fields fit the window of a budgeted workspace of
+// ws_bytes; ITC_ERR_WORKSPACE if it is smaller than itc_plan_budget_bytes(plan, 0).
+static int budget_ranges(const PlanHeader* h, const ImageDesc* d, size_t ws_bytes, std::vector<int>* cuts) {
+    const size_t tail = budget_tail_bytes(h);
+    if (ws_bytes < tail) return ITC_ERR_WORKSPACE;
+    const long long window = (long long)((ws_bytes - tail) / sizeof(float));
+    cuts->assign(1, 0);
+    long long used = 0;
+    for (int b = 0; b < h->B; ++b) {
+        const long long span = field_span(h, d, b);
+        if (span > window) return ITC_ERR_WORKSPACE;
+        if (used + span > window) {
+            cuts->push_back(b);
+            used = 0;
+        }
+        used += span;
+    }
+    cuts->push_back(h->B);
+    return ITC_OK;
+}
+
+int itc_run_budget(const void* plan_host, const void* plan_dev, float* W, itc_stats* stats, void* ws,
+                   size_t ws_bytes, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (!ws || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    const ImageDesc* hd = reinterpret_cast<const ImageDesc*>(reinterpret_cast<const unsigned char*>(plan_host) +
+                                                             h->desc_off);
+    std::vector<int> cuts;
+    int rc = budget_ranges(h, hd, ws_bytes, &cuts);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (size_t r = 0; r + 1 < cuts.size() && !rc; ++r) {
+        const WsView v = budget_view(h, ws, hd, cuts[r]);
+        rc = fields_range(h, plan_host, plan_dev, cuts[r], cuts[r + 1], v, s);
+        if (!rc) rc = iterate_images(h, plan_dev, cuts[r], cuts[r + 1], false, W, stats, v, s);
+    }
+    return rc;
+}
+
+int itc_backward_budget(const void* plan_host, const void* plan_dev, const float* W, const float* grad_dcs,
+                        float* grad_W, float* grad_h, itc_stats* stats, void* ws, size_t ws_bytes, void* stream) {
+    const PlanHeader* h = plan_of(plan_host);
+    if (!h || !plan_dev || !W || !aligned(plan_dev, 16)) return ITC_ERR_INVALID_ARG;
+    if (!ws || !aligned(ws, 256)) return ITC_ERR_WORKSPACE;
+    if (h->has_recursive) return ITC_ERR_UNSUPPORTED;
+    const ImageDesc* hd = reinterpret_cast<const ImageDesc*>(reinterpret_cast<const unsigned char*>(plan_host) +
+                                                             h->desc_off);
+    std::vector<int> cuts;
+    int rc = budget_ranges(h, hd, ws_bytes, &cuts);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (size_t r = 0; r + 1 < cuts.size() && !rc; ++r) {
+        const WsView v = budget_view(h, ws, hd, cuts[r]);
+        rc = fields_range(h, plan_host, plan_dev, cuts[r], cuts[r + 1], v, s);
+        if (!rc)
+            rc = backward_images(h, plan_host, plan_dev, cuts[r], cuts[r + 1], false, W, grad_dcs, grad_W, grad_h,
+                                 stats, v, s);
+    }
+    return rc;
 }
 
 }  // extern "C"

@@ -50,7 +50,8 @@ __device__ __forceinline__ int pixel_gray(const ImageDesc& D, int u, int v) {
 }
 
 __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_constant__ BackwardLaunch L) {
-    const ImageDesc& D = L.descs[blockIdx.x];
+    const int img = L.img_base + blockIdx.x;
+    const ImageDesc& D = L.descs[img];
     const int M = D.M, nd = D.ndim, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nw = blockDim.x >> 5;
     extern __shared__ __align__(16) float sm[];
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
     }
     __syncthreads();
     const double sxw = red[0], sww = red[1];
-    const double gD = L.grad_dcs ? (double)L.grad_dcs[blockIdx.x] : 1.0;
+    const double gD = L.grad_dcs ? (double)L.grad_dcs[img] : 1.0;
     if (L.grad_W) {
         float* gW = L.grad_W + D.w_off;
         for (int k = tid; k < M; k += blockDim.x)
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
             }
     }
     if (tid == 0) {
-        L.scal[blockIdx.x * 4 + 0] = 2.0 * gD / sxx;
-        L.scal[blockIdx.x * 4 + 1] = 2.0 * gD / sxw;
+        L.scal[img * 4 + 0] = 2.0 * gD / sxx;
+        L.scal[img * 4 + 1] = 2.0 * gD / sxw;
         if (L.stats) {
             itc_stats r;
             r.sxw = sxw;
@@ -198,9 +199,11 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
             r.empty = (int)red[2];
             r.moved = 0;
             r.iters_done = 0;
-            r.status = !(sxw > 0) || !isfinite(r.dcs) ? ITC_ERR_NONFINITE
-                       : (r.empty > 0 ? ITC_WARN_EMPTY_SUPPORT : ITC_OK);
-            L.stats[blockIdx.x] = r;
+            const int dev_status = L.img_status ? L.img_status[img] : ITC_OK;
+            r.status = dev_status == ITC_ERR_TIMEOUT ? ITC_ERR_TIMEOUT
+                       : (!(sxw > 0) || !isfinite(r.dcs) ? ITC_ERR_NONFINITE
+                          : (r.empty > 0 ? ITC_WARN_EMPTY_SUPPORT : ITC_OK));
+            L.stats[img] = r;
         }
     }
 }
@@ -219,7 +222,8 @@ constexpr int kChunk = 64;   // codebooks staged per round in the pixel kernel
 __global__ void __launch_bounds__(kThreads, 3) bwd_pixels_kernel(const __grid_constant__ BackwardLaunch L) {
     // split CTAs per image (few large images): CTA s of an image takes its tiles s, s + split, ...
     const int split = L.split;
-    const int img = __ldg(L.bwd_order + blockIdx.x / split), part = blockIdx.x % split;
+    const int img = L.bwd_order ? __ldg(L.bwd_order + blockIdx.x / split) : L.img_base + (int)(blockIdx.x / split);
+    const int part = blockIdx.x % split;
     const ImageDesc& D = L.descs[img];
     const int M = D.M, nd = D.ndim, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int H = D.H, Wd = D.W, G = D.G, fpitch = D.fpitch, tiles_v = D.bwd_tiles_v;

@@ -271,14 +271,18 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
         __syncthreads();   // the staged tile has landed; the previous tile's passes are done
         if (tid == 0) flush();
         if (s_abort) {
-            // every tile this CTA still owns gets a NaN S_XX share, so each affected image
-            // reports a non-finite status; then the copies still in flight land (bounded waits)
+            // every tile this CTA still owns gets a NaN S_XX share and its image the status
+            // ITC_ERR_TIMEOUT (its fields stay unwritten); then the copies still in flight land
+            // (bounded waits)
             if (tid < 32) {
                 for (int tt = t; tt < t_hi; ++tt) {
                     int im, lc;
                     locate_warp(L, tt, im, lc);
                     const ImageDesc* d2 = L.descs ? L.descs + im : &L.one;
-                    if (tid == 0) L.partials[d2->partial_off + lc] = __longlong_as_double(0x7ff8000000000000LL);
+                    if (tid == 0) {
+                        L.partials[d2->partial_off + lc] = __longlong_as_double(0x7ff8000000000000LL);
+                        if (L.status) L.status[L.descs ? im : 0] = ITC_ERR_TIMEOUT;
+                    }
                 }
                 if (tid == 0)
                     for (int b = 0; b < NST; ++b)

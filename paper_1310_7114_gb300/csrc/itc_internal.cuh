@@ -111,6 +111,7 @@ struct PlanHeader {
     long long ints_off;         // bytes from plan start to the int area
     long long nints;
     long long ws_scal_off;      // bytes: per-image backward scalars (4 doubles each)
+    long long ws_status_off;    // bytes: per-image device status words of the fields pass (B ints)
     long long bwd_tiles;        // backward pixel tiles over all images
     int max_bwd_tiles;          // most backward pixel tiles of one image
     int bwd_order_off;          // offset (ints) of the backward image order (B ints, most tiles first)
@@ -151,6 +152,9 @@ struct FieldsLaunch {
     int grid_per_sm;            // persistent CTAs per SM (0: as many as fit)
     int mode;                   // 0: every field plane; 1: A only, into the A_s plane, S_XX
                                 // partials at sxx_off (self-overlap pass); 2: S_XX partials only
+    int* status;                // device status words: one per image of the plan (batched) or one
+                                // for the call (single image); a CTA whose bounded wait gives up
+                                // writes ITC_ERR_TIMEOUT for every image it still owned tiles of
 };
 
 struct RunLaunch {
@@ -168,6 +172,7 @@ struct RunLaunch {
     int img_base;               // image of blockIdx.x == 0 (image sub-ranges)
     const int* groups;          // whole batch: the images of each CTA (kGroupInts ints a CTA), else
                                 // one image a CTA, img_base + blockIdx.x
+    const int* img_status;      // per-image status words of the fields pass (plans) or nullptr
 };
 
 struct BackwardLaunch {
@@ -180,9 +185,12 @@ struct BackwardLaunch {
     float* grad_h;
     itc_stats* stats;
     double* scal;               // per-image scalars in workspace: S_XW, S_WW, S_XX, gD
-    const int* bwd_order;       // image of each backward pixel CTA (B ints, most tiles first)
+    const int* bwd_order;       // image of each backward pixel CTA (B ints, most tiles first), or
+                                // nullptr: images img_base, img_base + 1, ... in order
     int B;
     int split;                  // pixel-pass CTAs per image (set at launch)
+    int img_base;               // image of the first CTA (image ranges)
+    const int* img_status;      // per-image status words of the fields pass, or nullptr
 };
 
 constexpr int kChamferMaxW = 1024;   // chamfer rows: 32 lanes x 4 columns x 8 chunks

@@ -12,9 +12,10 @@
 
 namespace {
 
-// Scratch of itc_fields_noalloc: one double per fields tile (ITC_NOALLOC_MAX_TILES doubles,
-// 512 KiB).  Every device that loads the library keeps it until the process exits.
-static __device__ __align__(256) double g_noalloc_partials[ITC_NOALLOC_MAX_TILES];
+// Scratch of itc_fields_noalloc, laid out as itc_fields' workspace: the call's status word in
+// the first 256 bytes, then one double per fields tile (ITC_NOALLOC_MAX_TILES doubles, 512 KiB).
+// Every device that loads the library keeps it until the process exits.
+static __device__ __align__(256) double g_noalloc_partials[32 + ITC_NOALLOC_MAX_TILES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
@@ -39,13 +40,13 @@ int scratch_address(void** out) {
 
 extern "C" int itc_fields_noalloc(const itc_image* img, const itc_params* p, float* fields, double* sxx,
                                   void* stream) {
-    const size_t need = itc_fields_workspace_bytes(img);   // one double per tile, 0 if invalid
+    const size_t need = itc_fields_workspace_bytes(img);   // status slot + one double per tile, 0 if invalid
     if (need == 0) return ITC_ERR_INVALID_ARG;
     if (need > sizeof(g_noalloc_partials)) return ITC_ERR_UNSUPPORTED;   // beyond the fixed scratch
     void* scratch = nullptr;
     const int rc = scratch_address(&scratch);
     if (rc) return rc;
-    // The fields pass overwrites one partial per tile before the reduction reads them, so
-    // nothing in the shared array needs clearing between calls.
+    // The fields pass overwrites one partial per tile before the reduction reads them, and the
+    // call clears the status word itself, so nothing else in the shared array needs clearing.
     return itc_fields(img, p, fields, sxx, scratch, sizeof(g_noalloc_partials), stream);
 }

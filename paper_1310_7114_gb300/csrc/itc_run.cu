@@ -13,9 +13,10 @@
 //   sums     S_XW = sum_k a_k, S_WW = sum_k s_k (FP32 shuffle trees, then the image's warps in order),
 //            c = S_XW / S_WW, D_cs of Eq. (1) in double at the reported W
 //   update   w_k' = w_k + step_scale (D_k - kappa c E_k) / a_k, kappa_i = tau_i^2 / rho_i^2 (the
-//            factor differentiating Eq. (1) gives the pair term; 1 when tau = rho), rounded unless
-//            ITC_CONTINUOUS (on the lattice w_k is an integer, so w_k + round(delta) is exact in
-//            FP32); a_k = 0 keeps w_k.  Jacobi: every k reads the old W.
+//            factor differentiating Eq. (1) gives the pair term; 1 when tau = rho), rounded to the
+//            lattice unless ITC_CONTINUOUS (floor(w) + round(w - floor(w) + delta), exact in FP32
+//            up to the one sum of the fraction and delta; a real-valued W lands on the lattice
+//            after its first update); a_k = 0 keeps w_k.  Jacobi: every k reads the old W.
 #include <math.h>
 
 #include <type_traits>
@@ -50,8 +51,10 @@ struct Sums {
     int empty;
 };
 
+// dev_status: the image's status word from the fields pass (ITC_ERR_TIMEOUT when a bounded wait
+// there gave up; its S_XX is then NaN)
 __device__ void write_stats(itc_stats* st, const Sums& s, double sxx, int moved, int iters_done,
-                            double dcs_const) {
+                            double dcs_const, int dev_status) {
     itc_stats r;
     r.sxw = s.sxw;
     r.sww = s.sww;
@@ -61,8 +64,9 @@ __device__ void write_stats(itc_stats* st, const Sums& s, double sxx, int moved,
     r.empty = s.empty;
     r.moved = moved;
     r.iters_done = iters_done;
-    r.status = !(s.sxw > 0) || !isfinite(r.dcs) ? ITC_ERR_NONFINITE
-               : (s.empty > 0 ? ITC_WARN_EMPTY_SUPPORT : ITC_OK);
+    r.status = dev_status == ITC_ERR_TIMEOUT ? ITC_ERR_TIMEOUT
+               : (!(s.sxw > 0) || !isfinite(r.dcs) ? ITC_ERR_NONFINITE
+                  : (s.empty > 0 ? ITC_WARN_EMPTY_SUPPORT : ITC_OK));
     *st = r;
 }
 
@@ -295,7 +299,8 @@ __global__ void __launch_bounds__(kRunThreads, ND == 3 ? 6 : 7) run_kernel(const
         Sums r;
         group_sums(pa, ps, pe, span, warp_has, red, &r);
         if (live) s = r;
-        if (live && !L.final_eval && t == 0 && L.stats && kl == 0) write_stats(L.stats + img, s, s_sxx[sub], 0, 0, Dg.dcs_const);
+        if (live && !L.final_eval && t == 0 && L.stats && kl == 0)
+            write_stats(L.stats + img, s, s_sxx[sub], 0, 0, Dg.dcs_const, L.img_status ? L.img_status[img] : ITC_OK);
         const bool upd = live && t != D.iters && !stop;
         if (!upd) live = false;
         // update (Jacobi: every k above read the old W; the barrier in group_sums, or the image's
@@ -323,8 +328,13 @@ __global__ void __launch_bounds__(kRunThreads, ND == 3 ? 6 : 7) run_kernel(const
                 const float delta = D.step * (Dm[q][i] - (c * kap[i]) * Ek[q][i]) / a[q];
                 float nv;
                 if (snap) {
-                    // w is integral: round(w + delta) = w + round(delta), exact in FP32
-                    nv = fminf(fmaxf(nw[i] + floorf(delta + 0.5f), 0.f), (float)(ni - 1));
+                    // round(w + delta) = fl + round(fr + delta) with w = fl + fr, fl = floor(w):
+                    // fl and fr are exact in FP32, and on the lattice (fr = 0, the state after
+                    // the first update) this is w + round(delta) with the one rounding of delta
+                    // + 0.5.  A real-valued initial W (from a continuous run, or optimised by
+                    // gradients) is rounded onto the lattice by its first update.
+                    const float fl = floorf(nw[i]);
+                    nv = fminf(fmaxf(fl + floorf((nw[i] - fl) + delta + 0.5f), 0.f), (float)(ni - 1));
                 } else {
                     nv = fminf(fmaxf(nw[i] + delta, 0.f), (float)(ni - 1));
                 }
@@ -361,7 +371,8 @@ __global__ void __launch_bounds__(kRunThreads, ND == 3 ? 6 : 7) run_kernel(const
         }
         if (!any) break;
     }
-    if (has && L.final_eval && L.stats && kl == 0) write_stats(L.stats + img, s, s_sxx[sub], moved, done, Dg.dcs_const);
+    if (has && L.final_eval && L.stats && kl == 0)
+        write_stats(L.stats + img, s, s_sxx[sub], moved, done, Dg.dcs_const, L.img_status ? L.img_status[img] : ITC_OK);
     if (has && !L.final_eval && L.stats && kl == 0) {
         L.stats[img].moved = moved;
         L.stats[img].iters_done = done;

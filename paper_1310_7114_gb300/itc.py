@@ -39,7 +39,8 @@ EXPORTS = (
     "itc_run", "itc_run_fields", "itc_run_iterate", "itc_run_fields_range", "itc_run_iterate_range",
     "itc_run_pipelined", "itc_backward", "itc_fields_noalloc", "itc_autotune", "itc_plan_classes",
     "itc_plan_class", "itc_plan_configure", "itc_params_parzen", "itc_segment",
-    "itc_plan_padded_offset", "itc_chamfer", "itc_run_staged",
+    "itc_plan_padded_offset", "itc_chamfer", "itc_run_staged", "itc_plan_budget_bytes", "itc_run_budget",
+    "itc_backward_budget",
 )
 
 
@@ -149,6 +150,12 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
         L.itc_plan_class.argtypes = [_P, ctypes.c_int, _I, _F, _I, _I, _I, _I, _F]
         L.itc_backward.restype = ctypes.c_int
         L.itc_backward.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]
+        L.itc_plan_budget_bytes.restype = _SZ
+        L.itc_plan_budget_bytes.argtypes = [_P, _SZ]
+        L.itc_run_budget.restype = ctypes.c_int
+        L.itc_run_budget.argtypes = [_P, _P, _P, _P, _P, _SZ, _P]
+        L.itc_backward_budget.restype = ctypes.c_int
+        L.itc_backward_budget.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]
         _lib = L
     return _lib
 
@@ -299,7 +306,7 @@ class Plan:
     """
 
     def __init__(self, images: Sequence, M: Sequence[int], params, ndims=None, Gs=None, weights=None,
-                 device=None):
+                 device=None, allocate_ws: bool = True):
         torch = _torch()
         B = len(images)
         ndims = list(ndims) if ndims is not None else [2] * B
@@ -325,7 +332,8 @@ class Plan:
         blob = np.frombuffer(self.host.raw, dtype=np.uint8)
         self.dev = torch.from_numpy(blob.copy()).to(dev)
         self.ws_bytes = int(ws.value)
-        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        # the whole batch's fields; a plan used only through the budgeted calls needs none of it
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev) if allocate_ws else None
         self.pixels = int(lib().itc_plan_pixels(ctypes.cast(self.host, _P)))
         self.w_offsets = np.concatenate([[0], np.cumsum([m * d for m, d in zip(self.M, ndims)])]).astype(np.int64)
         self.gh_offsets = np.concatenate([[0], np.cumsum([h * w for h, w in self.shapes])]).astype(np.int64)
@@ -334,6 +342,11 @@ class Plan:
     @property
     def host_ptr(self):
         return ctypes.cast(self.host, _P)
+
+    def budget_bytes(self, budget_bytes: int = 0) -> int:
+        """itc_plan_budget_bytes: workspace of the budgeted calls within ``budget_bytes`` in all
+        (raised to the smallest they accept; 0 gives that smallest)."""
+        return int(lib().itc_plan_budget_bytes(self.host_ptr, int(budget_bytes)))
 
     def offsets(self, b: int):
         """(field byte offset in ws, W float offset, grad_h float offset) of image b (itc_plan_offsets)."""
@@ -467,6 +480,26 @@ def backward(plan: Plan, W, grad_dcs=None, grad_W=None, grad_h=None, stats=None,
     _check(itc_backward(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), _ptr(grad_dcs), _ptr(grad_W),
                         _ptr(grad_h), _ptr(stats), plan.ws.data_ptr(), plan.ws.numel(), _stream(stream)),
            "itc_backward")
+    return grad_W, grad_h
+
+
+def budget_workspace(plan: Plan, budget_bytes: int = 0):
+    """A device workspace for the budgeted calls, of itc_plan_budget_bytes(plan, budget_bytes)."""
+    return _torch().empty(plan.budget_bytes(budget_bytes), dtype=_torch().uint8, device=plan.dev.device)
+
+
+def run_budget(plan: Plan, W, ws, stats=None, stream=None):
+    """itc_run_budget: itc_run with the fields recomputed range by range inside ``ws``."""
+    _check(lib().itc_run_budget(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), _ptr(stats), ws.data_ptr(),
+                                ws.numel(), _stream(stream)), "itc_run_budget")
+    return W
+
+
+def backward_budget(plan: Plan, W, ws, grad_dcs=None, grad_W=None, grad_h=None, stats=None, stream=None):
+    """itc_backward_budget: the gradient with A and S_XX recomputed range by range inside ``ws``."""
+    _check(lib().itc_backward_budget(plan.host_ptr, plan.dev.data_ptr(), W.data_ptr(), _ptr(grad_dcs),
+                                     _ptr(grad_W), _ptr(grad_h), _ptr(stats), ws.data_ptr(), ws.numel(),
+                                     _stream(stream)), "itc_backward_budget")
     return grad_W, grad_h
 
 

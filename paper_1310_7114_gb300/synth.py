@@ -26,7 +26,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "rng_for", "draw_ellipse", "draw_polyline", "c1_image", "c2_image", "c3_batch",
+    "rng_for", "draw_ellipse", "draw_polyline", "c1_image", "c2_image", "c3_batch", "c3_shape", "c3_codebook",
     "c4_weights", "c5_gray", "init_codebook", "init_codebook_gray", "blob_silhouette",
 ]
 
@@ -119,23 +119,40 @@ def blob_silhouette(rng: np.random.Generator, H: int, W: int, target: float) -> 
     return img
 
 
-def c3_batch(n: int = 4096, start: int = 0):
-    """Ragged batch of binary silhouettes.
+def _c3_draw(i: int):
+    rng = rng_for(3, i)
+    H, W = int(rng.integers(64, 513)), int(rng.integers(64, 513))
+    target = rng.uniform(0.05, 0.40)
+    M = int(rng.choice([16, 32, 64, 128]))
+    s = float(rng.choice([2.0, 3.0, 4.0]))
+    return rng, H, W, target, M, s
+
+
+def c3_shape(i: int):
+    """``(H, W, M, sigma)`` of image ``i`` of the ragged batch, without drawing its pixels."""
+    _, H, W, _, M, s = _c3_draw(i)
+    return H, W, M, s
+
+
+def c3_batch(n: int = 4096, start: int = 0, indices=None):
+    """Ragged batch of binary silhouettes (images ``start .. start+n-1``, or the listed ``indices``).
 
     Returns ``(images, M, sigma)``: a list of uint8 arrays with sides drawn from U{64..512},
     per-image codebook sizes from {16, 32, 64, 128} and kernel widths from {2, 3, 4}.
     """
     images, Ms, sigmas = [], [], []
-    for i in range(start, start + n):
-        rng = rng_for(3, i)
-        H, W = int(rng.integers(64, 513)), int(rng.integers(64, 513))
-        target = rng.uniform(0.05, 0.40)
-        M = int(rng.choice([16, 32, 64, 128]))
-        s = float(rng.choice([2.0, 3.0, 4.0]))
+    for i in (range(start, start + n) if indices is None else indices):
+        rng, H, W, target, M, s = _c3_draw(int(i))
         images.append(blob_silhouette(rng, H, W, target))
         Ms.append(M)
         sigmas.append(s)
     return images, np.array(Ms, np.int32), np.array(sigmas, np.float32)
+
+
+def c3_codebook(i: int, img: np.ndarray, M: int) -> np.ndarray:
+    """Initial codebook of image ``i`` of the ragged batch as the benchmark draws it: M distinct
+    foreground pixels (PCG64 seed 3 * 1000 + 500000 + i)."""
+    return init_codebook(rng_for(3, 500_000 + i), img.astype(np.float32), int(M))
 
 
 def _smooth_noise(rng: np.random.Generator, shape, sigma: float) -> np.ndarray:

@@ -50,6 +50,69 @@ def assert_lattice_equal_except_ties(Wg, Wref, raw, eps=1e-4, what=""):
     return int(ties.sum())
 
 
+def assert_grad_h_close(gh, h, A_s, sums, gh_ref, gD=1.0, c=3e-5, what=""):
+    """Element-wise bound on dD/dh(x) = s1 A_s(x) - s2 S(x), s1 = 2 gD / S_XX, s2 = 2 gD / S_XW,
+    S(x) = sum_k g(x - w_k) over the boxes that hold x (the transposed stamp of the codebook).
+
+    The GPU value is the FP32 combination of FP32 terms: A_s within 1e-5 relative (the fields
+    bound), S_XX and S_XW within 1e-5 relative (sums of those fields), and the stamp a sum of at
+    most M non-negative products of two ex2.approx factors (2^-22 each, plus the rounding of the
+    exponent and of each product and partial sum: below (M + 4) 2^-23 < 2e-5 for M <= 128).  So
+    |delta| <= c (|s1 A_s| + |s2 S|) with c = 3e-5, where both terms are taken from the oracle:
+    s1 A_s from A_s and S_XX, and s2 S = s1 A_s - dD/dh.  Exact zeros (pixels whose windows
+    hold no data and that no box covers) must be zero."""
+    gh = np.asarray(gh, np.float64)
+    t1 = 2.0 * gD * np.asarray(A_s, np.float64) / sums[2]
+    t2 = t1 - np.asarray(gh_ref, np.float64)
+    tol = c * (np.abs(t1) + np.abs(t2))
+    err = np.abs(gh - gh_ref)
+    bad = err > tol
+    assert not bad.any(), (f"{what}: {bad.sum()} pixels of dD/dh outside the element-wise bound, worst "
+                           f"{(err[bad] / np.maximum(tol[bad], 1e-300)).max():.2f}x at {np.argwhere(bad)[:4].tolist()}")
+
+
 # D = log S_WW + log S_XX - 2 log S_XW; each sum carries at most 1e-5 relative error, which is an
 # absolute error of at most 1e-5 in its log, so |dD| <= (1 + 1 + 2) 1e-5.
 DCS_ATOL = 4e-5
+
+
+def one_iteration(p):
+    """A copy of itc_params ``p`` with a single iteration (for lockstep plans)."""
+    import ctypes
+    from paper_1310_7114_gb300 import itc
+    q = itc.ItcParams()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
+    q.iters = 1
+    return q
+
+
+def plan_lockstep(images, Ms, params, W0s, iters, oracle_step, ndims=None, Gs=None, weights=None, what="lockstep"):
+    """Lockstep through the batched plan itself (not through itc_step): a plan over the same
+    images with one iteration per call, its fields computed once.  Every call starts each image
+    from the oracle's codebooks of that iteration and must give the oracle's next codebooks
+    except coordinates within 1e-4 of a half-integer.  The iteration CTAs are grouped as in the
+    full run (the groups depend on M and, through the launch order, only on the images'
+    relative cost, which is unchanged when every image has one iteration).
+    ``oracle_step(b, W) -> (W_next, W_raw)``; ``params`` one ItcParams or one per image.
+    Returns the tie count."""
+    import torch
+    from paper_1310_7114_gb300 import itc
+    B = len(images)
+    ps = [params] * B if not isinstance(params, (list, tuple)) else list(params)
+    ts = [to_dev(im) for im in images]
+    ws = [None if w is None else to_dev(np.asarray(w, np.float32)) for w in (weights or [None] * B)]
+    plan = itc.Plan(ts, Ms, [one_iteration(p) for p in ps], ndims=ndims, Gs=Gs, weights=ws)
+    itc.run_fields(plan)
+    Wc = [np.asarray(w, np.float64) for w in W0s]
+    ties = 0
+    for t in range(iters):
+        W = plan.pack_W([w.astype(np.float32) for w in Wc])
+        st = itc.new_stats(B, W.device)
+        itc.run_iterate(plan, W, st)
+        torch.cuda.synchronize()
+        got = plan.unpack_W(W)
+        for b in range(B):
+            Wn, raw = oracle_step(b, Wc[b])
+            ties += assert_lattice_equal_except_ties(got[b], Wn, raw, what=f"{what}: image {b} iteration {t}")
+            Wc[b] = Wn
+    return ties

@@ -282,3 +282,27 @@ def test_staged_run_checks_the_image_buffer(L):
     assert L.itc_run_staged(hp, 0x100000, 0x1000, 0x10000, 0x8000, 0x2000, None, 0x4000, ws, 2, None, None) == itc.ITC_ERR_INVALID_ARG
     assert L.itc_run_staged(hp, 0x100000, 0x1000, 0x10000, 0x20000, 0x2000, None, 0x4000, ws, 0, None, None) == itc.ITC_ERR_INVALID_ARG
     assert L.itc_run_staged(hp, 0x100000, None, 0x10000, 0x20000, 0x2000, None, 0x4000, ws, 2, None, None) == itc.ITC_ERR_INVALID_ARG
+
+
+def test_budget_workspace_query_and_checks(L):
+    """itc_plan_budget_bytes: the smallest budgeted workspace holds the batch's per-tile and
+    per-image words plus the fields of its largest image (here the 300 x 513 one: 3 planes of
+    rows of 516 floats), far less than the whole batch's fields; larger budgets are rounded down
+    to 256 bytes; the budgeted calls reject workspaces below the smallest before any launch."""
+    shapes = [(64, 64), (100, 70), (300, 513), (17, 9), (200, 200)]
+    rc, buf, ws = _plan(L, shapes, [8, 16, 128, 3, 32], [_p(2.0), _p(3.0), _p(2.0), _p(4.0), _p(3.0)])
+    assert rc == 0
+    plan = ctypes.cast(buf, ctypes.c_void_p)
+    least = L.itc_plan_budget_bytes(plan, 0)
+    largest = 3 * 300 * 516 * 4
+    assert largest <= least < largest + (ws - sum(3 * h * ((w + 3) // 4 * 4) * 4 for h, w in shapes)) + 4096
+    assert least < ws and least % 256 == 0
+    assert L.itc_plan_budget_bytes(plan, least + 1000) == (least + 1000) // 256 * 256
+    assert L.itc_plan_budget_bytes(plan, 10) == least
+    bogus = ctypes.create_string_buffer(len(buf.raw))
+    assert L.itc_plan_budget_bytes(ctypes.cast(bogus, ctypes.c_void_p), 0) == 0
+    for fn in (lambda w, n: L.itc_run_budget(plan, 0x1000, 0x2000, None, w, n, None),
+               lambda w, n: L.itc_backward_budget(plan, 0x1000, 0x2000, None, None, None, None, w, n, None)):
+        assert fn(0x4000, least - 256) == itc.ITC_ERR_WORKSPACE
+        assert fn(0x4010, least) == itc.ITC_ERR_WORKSPACE
+        assert fn(None, least) == itc.ITC_ERR_WORKSPACE

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpuhelp import DCS_ATOL, assert_fields_close, assert_lattice_equal_except_ties, radii, to_dev
+from gpuhelp import DCS_ATOL, assert_fields_close, plan_lockstep, radii, to_dev
 from paper_1310_7114_gb300 import build, itc, synth
 
 pytestmark = pytest.mark.gpu
@@ -89,18 +89,13 @@ def _check_run3d(gray, G, sigma, M, iters, W0, Wg, st, hw=None):
         assert np.array_equal(Wg, Wo)
         assert abs(st["dcs"] - dcs[-1]) <= DCS_ATOL
     else:
-        # lockstep with GPU steps from the oracle's W
-        import torch
-        t = to_dev(gray)
-        F, s = itc.fields(t, sigma, 3.0, ndim=3, G=G, weight=to_dev(hw.astype(np.float32)) if hw is not None else None)
-        W = np.asarray(W0, np.float64)
-        for _ in range(iters):
+        # the plan in lockstep with the oracle's steps
+        def ostep(b, W):
             Wn, raw, _ = oracle.lattice_step(A, [Fu, Fv, Fg], sigma, W)
-            Wo2, _, _ = itc.step(t, F, s, to_dev(W.astype(np.float32)), sigma, ndim=3, G=G,
-                                 weight=to_dev(hw.astype(np.float32)) if hw is not None else None)
-            torch.cuda.synchronize()
-            assert_lattice_equal_except_ties(Wo2.cpu().numpy(), Wn, raw, what="3-D lockstep")
-            W = Wn
+            return Wn, raw
+
+        plan_lockstep([gray], [M], itc.make_params(sigma, 3.0, 1), [W0], iters, ostep, ndims=[3], Gs=[G],
+                      weights=[hw] if hw is not None else None, what="3-D lockstep")
 
 
 def test_run3d_small():

@@ -1,13 +1,14 @@
 """GPU parity of the hand-written adjoint of Eq. (1): itc_backward's dD/dW and dD/dh (weighted
 ITC, Sec. 5) vs the oracle's analytic gradient, and vs FP64 central differences (h = 1e-4) on 64
-random entries of W and of h of a full-size 512x512 weight image.  Bar: normwise relative error
+random entries of W and of h of a full-size 512x512 weight image.  Bars: normwise relative error
 <= 1e-4 (FP32 sums of ~1e-6 relative error, with the cancellation between the two terms of
-dD/dh bounded by their magnitudes)."""
+dD/dh bounded by their magnitudes), and for dD/dh also element-wise, every pixel within 3e-5 of
+the magnitudes of its two terms (gpuhelp.assert_grad_h_close)."""
 import numpy as np
 import pytest
 
 import oracle
-from gpuhelp import to_dev
+from gpuhelp import assert_grad_h_close, to_dev
 from paper_1310_7114_gb300 import build, itc, synth
 
 pytestmark = pytest.mark.gpu
@@ -50,6 +51,8 @@ def test_backward_matches_oracle_gradient_weighted_and_binary():
         scale = [1.0, 2.5, -0.5, 1.0][b]
         assert _nrel(gW[b], scale * gref) <= 1e-4, (b, _nrel(gW[b], scale * gref))
         assert _nrel(gh[b], scale * ghref) <= 1e-4, (b, _nrel(gh[b], scale * ghref))
+        A = oracle.fields2d(im.astype(np.float64), 3.0)[0]
+        assert_grad_h_close(gh[b], im, A, sums, scale * ghref, gD=scale, what=f"image {b}")
         d_ref = np.log(sums[1]) + np.log(sums[2]) - 2 * np.log(sums[0])
         assert abs(st[b]["dcs"] - d_ref) <= 4e-5 and abs(st2[b]["dcs"] - d_ref) <= 4e-5
 
@@ -58,8 +61,9 @@ def test_backward_uint8_binary_image():
     img = synth.c1_image(2)
     W0 = synth.init_codebook(synth.rng_for(1, 2), img.astype(np.float32), 8)
     _, gW, gh, _, _ = gpu_forward_backward([img], [8], [W0], 2.0)
-    gref, ghref, _ = oracle.dcs_grad2d_dense(img.astype(np.float64), 2.0, W0.astype(np.float64))
+    gref, ghref, sums = oracle.dcs_grad2d_dense(img.astype(np.float64), 2.0, W0.astype(np.float64))
     assert _nrel(gW[0], gref) <= 1e-4 and _nrel(gh[0], ghref) <= 1e-4
+    assert_grad_h_close(gh[0], img, oracle.fields2d(img.astype(np.float64), 2.0)[0], sums, ghref, what="binary")
 
 
 def test_backward_at_real_valued_codebook():
@@ -68,8 +72,9 @@ def test_backward_at_real_valued_codebook():
     rng = np.random.default_rng(9)
     W0 = (synth.init_codebook(synth.rng_for(4, 7), img, 12, 0.5) + rng.uniform(-0.45, 0.45, (12, 2))).astype(np.float32)
     _, gW, gh, _, _ = gpu_forward_backward([img], [12], [W0], 3.0)
-    gref, ghref, _ = oracle.dcs_grad2d_dense(img.astype(np.float64), 3.0, W0.astype(np.float64))
+    gref, ghref, sums = oracle.dcs_grad2d_dense(img.astype(np.float64), 3.0, W0.astype(np.float64))
     assert _nrel(gW[0], gref) <= 1e-4 and _nrel(gh[0], ghref) <= 1e-4
+    assert_grad_h_close(gh[0], img, oracle.fields2d(img.astype(np.float64), 3.0)[0], sums, ghref, what="real W")
 
 
 def test_backward_full_size_c4_against_central_differences():
@@ -81,6 +86,9 @@ def test_backward_full_size_c4_against_central_differences():
     rng = np.random.default_rng(11)
     eps = 1e-4
     A = oracle.fields2d(h, 3.0)[0]
+    # every pixel of the full image against the oracle's analytic gradient, element-wise
+    _, ghref, sums = oracle.dcs_grad2d_dense(h, 3.0, W0, A=A)
+    assert_grad_h_close(gh[0], h, A, sums, ghref, what="C4 full size")
     kw = rng.choice(64, 64, replace=True)
     fd_w, an_w = [], []
     for q in kw:
@@ -132,6 +140,8 @@ def test_backward_rows_not_16_byte_aligned():
     W0s = [synth.init_codebook(synth.rng_for(4, 70 + i), im, m, 0.5) for i, (im, m) in enumerate(zip(images, Ms))]
     plan, gW, gh, _, _ = gpu_forward_backward(images, Ms, W0s, 3.0)
     for b in range(len(images)):
-        gref, ghref, _ = oracle.dcs_grad2d_dense(images[b].astype(np.float64), 3.0, W0s[b].astype(np.float64))
+        gref, ghref, sums = oracle.dcs_grad2d_dense(images[b].astype(np.float64), 3.0, W0s[b].astype(np.float64))
         assert _nrel(gW[b], gref) <= 1e-4, (b, _nrel(gW[b], gref))
         assert _nrel(gh[b], ghref) <= 1e-4, (b, _nrel(gh[b], ghref))
+        assert_grad_h_close(gh[b], images[b], oracle.fields2d(images[b].astype(np.float64), 3.0)[0], sums, ghref,
+                            what=f"image {b}")

@@ -148,19 +148,71 @@ def test_tma_tiles_equal_plain_tiles_bit_for_bit(sigma, dtype, absolute, pattern
 
 def test_bounded_tile_wait_reports_instead_of_hanging():
     """The TMA tile wait is bounded: with the test hook one CTA waits for a copy phase that never
-    completes, gives up after about a second, and the call reports S_XX = NaN; the GPU context
-    stays usable and the next call is correct."""
+    completes and gives up after about a second.  The call reports ITC_ERR_TIMEOUT in the status
+    word at the start of its workspace, with sxx given (S_XX = NaN) and with sxx NULL; a call
+    without the hook reports ITC_OK there; the GPU context stays usable and the next call is
+    correct."""
+    import ctypes
     import torch
     h = (np.random.default_rng(0).random((256, 256)) < 0.3).astype(np.uint8)
     buf, (t,) = itc.pack_images([h], "cuda", align=16)   # aligned rows: the TMA path
     img = itc.make_image(t)
-    p = itc.make_params(2.0, 3.0, flags=itc.ITC_TEST_STALL_WAIT)
-    out = torch.empty(itc.lib().itc_fields_bytes(__import__("ctypes").byref(img)) // 4, device="cuda")
+    out = torch.empty(itc.lib().itc_fields_bytes(ctypes.byref(img)) // 4, device="cuda")
     ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
-    sxx = torch.zeros(1, dtype=torch.float64, device="cuda")
-    rc = itc.itc_fields(img, p, out.data_ptr(), sxx.data_ptr(), ws.data_ptr(), ws.numel(),
-                        torch.cuda.current_stream().cuda_stream)
-    assert rc == itc.ITC_OK
-    torch.cuda.synchronize()
-    assert np.isnan(sxx.item())
+    assert itc.lib().itc_fields_workspace_bytes(ctypes.byref(img)) <= ws.numel()
+    stream = torch.cuda.current_stream().cuda_stream
+    for with_sxx in (True, False):
+        ws.fill_(0x5A)
+        sxx = torch.zeros(1, dtype=torch.float64, device="cuda")
+        p = itc.make_params(2.0, 3.0, flags=itc.ITC_TEST_STALL_WAIT)
+        rc = itc.itc_fields(img, p, out.data_ptr(), sxx.data_ptr() if with_sxx else None, ws.data_ptr(),
+                            ws.numel(), stream)
+        assert rc == itc.ITC_OK
+        torch.cuda.synchronize()
+        assert int(ws[:4].view(torch.int32).item()) == itc.ITC_ERR_TIMEOUT, with_sxx
+        if with_sxx:
+            assert np.isnan(sxx.item())
+        else:
+            assert sxx.item() == 0.0   # untouched
+        rc = itc.itc_fields(img, itc.make_params(2.0), out.data_ptr(), None, ws.data_ptr(), ws.numel(), stream)
+        assert rc == itc.ITC_OK
+        torch.cuda.synchronize()
+        assert int(ws[:4].view(torch.int32).item()) == itc.ITC_OK
     check(h, 2.0, what="after a stalled call")
+
+
+def test_bounded_tile_wait_in_a_plan_sets_the_image_status():
+    """The same hook in a batch plan: the images whose tiles the stalled CTA owned report
+    ITC_ERR_TIMEOUT in itc_stats (from itc_run and from itc_backward), every other image of the
+    plan runs as in a plan without the hook, and the next run of the same plan is clean."""
+    import torch
+    images, Ms, sig = synth.c3_batch(12, start=300)
+    W0s = [synth.init_codebook(synth.rng_for(3, 90_000 + i), im.astype(np.float32), int(m))
+           for i, (im, m) in enumerate(zip(images, Ms))]
+    buf, views = itc.pack_images(images, "cuda")
+    outs = []
+    for stall in (True, False):
+        params = [itc.make_params(float(s), 3.0, 5, flags=itc.ITC_TEST_STALL_WAIT if stall else 0) for s in sig]
+        plan = itc.Plan(views, [int(m) for m in Ms], params)
+        assert any(c["staging"] == "tma" for c in plan.classes())
+        W = plan.pack_W(W0s)
+        st = itc.new_stats(len(images), W.device)
+        itc.run(plan, W, st)
+        gW = torch.empty_like(W)
+        st2 = itc.new_stats(len(images), W.device)
+        itc.backward(plan, W, grad_W=gW, stats=st2)
+        torch.cuda.synchronize()
+        outs.append((plan.unpack_W(W), itc.stats_to_numpy(st), itc.stats_to_numpy(st2)))
+    (Ws, s1, b1), (Wc, s0, b0) = outs
+    timed_out = [b for b in range(len(images)) if s1[b]["status"] == itc.ITC_ERR_TIMEOUT]
+    assert timed_out, "no image reported the timeout"
+    assert len(timed_out) < len(images)
+    for b in range(len(images)):
+        if b in timed_out:
+            assert np.isnan(s1[b]["sxx"]) and b1[b]["status"] == itc.ITC_ERR_TIMEOUT
+        else:
+            assert s1[b]["status"] == s0[b]["status"] != itc.ITC_ERR_TIMEOUT
+            assert np.array_equal(Ws[b], Wc[b]) and s1[b]["dcs"] == s0[b]["dcs"]
+            assert b1[b]["status"] != itc.ITC_ERR_TIMEOUT
+    assert all(s0[b]["status"] != itc.ITC_ERR_TIMEOUT for b in range(len(images)))
+    check(synth.c1_image(5), 2.0, what="after a stalled plan")

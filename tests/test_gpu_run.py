@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+import gpuhelp
 from gpuhelp import DCS_ATOL, assert_lattice_equal_except_ties, to_dev
 from paper_1310_7114_gb300 import build, itc, synth
 
@@ -34,20 +35,6 @@ def gpu_step(h, sigma, W, step_scale=1.0, flags=0, F=None):
     Wo, Wl, st = itc.step(t, F[0], F[1], to_dev(np.asarray(W, np.float32)), sigma, 3.0, step_scale, flags)
     torch.cuda.synchronize()
     return Wo.cpu().numpy(), Wl.cpu().numpy(), itc.stats_to_numpy(st)[0], F
-
-
-def lockstep(h, sigma, W0, iters, F_ref):
-    """Every iteration: GPU step from the oracle's W must match the oracle's next W (ties aside)."""
-    A, F, sxx = F_ref
-    W = np.asarray(W0, np.float64)
-    Fg = None
-    ties = 0
-    for _ in range(iters):
-        Wn, raw, _ = oracle.lattice_step(A, F, sigma, W)
-        Wg, _, _, Fg = gpu_step(h, sigma, W, F=Fg)
-        ties += assert_lattice_equal_except_ties(Wg, Wn, raw, what="lockstep")
-        W = Wn
-    return ties
 
 
 def run_plan(images, Ms, W0s, params, ndims=None, Gs=None, weights=None):
@@ -105,14 +92,30 @@ def test_step_with_absolute_fields_matches():
     assert_lattice_equal_except_ties(Wo.cpu().numpy(), Wn, raw, what="absolute")
 
 
-def _check_run(img, sigma, M, iters, W0, plan_W, stats, what):
+def plan_lockstep(images, Ms, sigmas, W0s, iters, what="plan lockstep"):
+    """The batched plan in lockstep with the oracle (see gpuhelp.plan_lockstep)."""
+    ref = [_oracle_fields(im, float(s)) for im, s in zip(images, sigmas)]
+
+    def ostep(b, W):
+        Wn, raw, _ = oracle.lattice_step(ref[b][0], ref[b][1], float(sigmas[b]), W)
+        return Wn, raw
+
+    return gpuhelp.plan_lockstep(images, Ms, [itc.make_params(float(s), 3.0, 1) for s in sigmas], W0s, iters,
+                                 ostep, what=what)
+
+
+def _check_run(img, sigma, M, iters, W0, plan_W, stats, what, batch=None):
+    """Final codebooks equal the oracle's when its trajectory has no rounding tie; otherwise the
+    batched plan is run in lockstep with the oracle (``batch`` = (images, Ms, sigmas, W0s) of the
+    plan that produced ``plan_W``; the image alone when None)."""
     A, F, sxx = _oracle_fields(img, sigma)
     Wo, dcs, tie, t = oracle.lattice_run(A, F, sxx, sigma, W0, iters)
     if tie.min() > 1e-4:
         assert np.array_equal(plan_W, Wo), f"{what}: final codebooks differ"
         assert abs(stats["dcs"] - dcs[-1]) <= DCS_ATOL, (what, stats["dcs"], dcs[-1])
     else:
-        lockstep(img, sigma, W0, iters, (A, F, sxx))
+        imgs, ms, sg, ws = batch if batch is not None else ([img], [M], [sigma], [W0])
+        plan_lockstep(imgs, ms, sg, ws, iters, what=what)
     assert stats["iters_done"] == iters
 
 
@@ -140,8 +143,18 @@ def test_batched_run_matches_oracle_per_image_and_single_fields():
            for i, (im, m) in enumerate(zip(images, Ms))]
     params = [itc.make_params(float(s), 3.0, 20) for s in sig]
     plan, Ws, st = run_plan(images, Ms, W0s, params)
+    tied = []
     for b in range(len(images)):
-        _check_run(images[b], float(sig[b]), int(Ms[b]), 20, W0s[b], Ws[b], st[b], f"image {b}")
+        A, F, sxx = _oracle_fields(images[b], float(sig[b]))
+        Wo, dcs, tie, t = oracle.lattice_run(A, F, sxx, float(sig[b]), W0s[b], 20)
+        assert st[b]["iters_done"] == 20
+        if tie.min() > 1e-4:
+            assert np.array_equal(Ws[b], Wo), f"image {b}: final codebooks differ"
+            assert abs(st[b]["dcs"] - dcs[-1]) <= DCS_ATOL
+        else:
+            tied.append(b)
+    if tied:   # the whole batch, through the batched plan, in lockstep with the oracle
+        plan_lockstep(images, Ms, sig, W0s, 20)
     for b in (0, 5, 11):
         H, W = images[b].shape
         single, _ = itc.fields(to_dev(images[b]), float(sig[b]))
@@ -393,3 +406,56 @@ def test_grouped_images_stop_on_their_own():
         if tie.min() > 1e-4:
             assert done[b] == t
             assert np.array_equal(plan.unpack_W(W)[b], Wo)
+
+
+def _real_valued(W0, rng, nd=2):
+    """Lattice sites moved by up to 0.45 px per axis: real-valued initial codebooks (as left by a
+    continuous run, or by gradient steps on W)."""
+    return (np.asarray(W0, np.float64) + rng.uniform(-0.45, 0.45, np.shape(W0))).astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_single_step_real_valued_codebook_snaps_to_lattice(seed):
+    """Default (snap) mode from a real-valued W: one step rounds w_k + delta_k onto the lattice
+    (Sec. 3.2; rounding floor(x + 0.5)), exactly as the oracle does, ties aside."""
+    img = synth.c1_image(10 + seed)
+    rng = np.random.default_rng(100 + seed)
+    W0 = _real_valued(synth.init_codebook(synth.rng_for(1, 10 + seed), img.astype(np.float32), 8), rng)
+    assert np.any(W0 != np.round(W0))
+    A, F, _ = _oracle_fields(img, 2.0)
+    Wn, raw, st = oracle.lattice_step(A, F, 2.0, W0.astype(np.float64))
+    Wg, Wl, s, _ = gpu_step(img, 2.0, W0)
+    assert_lattice_equal_except_ties(Wg, Wn, raw, what=f"seed {seed}")
+    assert np.all(Wg == np.round(Wg)), "snap mode left the lattice"
+    assert np.array_equal(Wl, Wg.astype(np.int32))
+    assert s["moved"] == st["moved"]
+
+
+def test_batched_run_real_valued_codebooks_grouped_ctas():
+    """A batch whose images share iteration CTAs (M <= 16, 32, 64: 8, 4, 2 per CTA) and larger
+    ones, every W_0 real-valued, default snap mode: each image's run equals the oracle's (or the
+    batched plan passes the lockstep when the oracle trajectory has a tie)."""
+    Ms = [5, 12, 16, 9, 20, 32, 27, 31, 40, 64, 50, 100, 128, 16, 3, 64]
+    images, W0s, sig = [], [], []
+    rng = np.random.default_rng(2024)
+    for i, m in enumerate(Ms):
+        img = synth.c3_batch(1, start=900 + i)[0][0][:160, :200].copy()
+        if img.sum() < 2 * m:
+            img = synth.c1_image(200 + i)
+        images.append(img)
+        W0s.append(_real_valued(synth.init_codebook(synth.rng_for(3, 80_000 + i), img.astype(np.float32), m), rng))
+        sig.append((2.0, 3.0, 4.0)[i % 3])
+    params = [itc.make_params(s, 3.0, 12) for s in sig]
+    plan, Ws, st = run_plan(images, Ms, W0s, params)
+    tied = 0
+    for b in range(len(images)):
+        assert np.all(Ws[b] == np.round(Ws[b])), f"image {b} left the lattice"
+        A, F, sxx = _oracle_fields(images[b], sig[b])
+        Wo, dcs, tie, t = oracle.lattice_run(A, F, sxx, sig[b], W0s[b], 12)
+        if tie.min() > 1e-4:
+            assert np.array_equal(Ws[b], Wo), f"image {b}: final codebooks differ"
+            assert abs(st[b]["dcs"] - dcs[-1]) <= DCS_ATOL
+        else:
+            tied += 1
+    if tied:
+        plan_lockstep(images, Ms, sig, W0s, 12, what="real-valued W0")

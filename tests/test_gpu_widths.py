@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpuhelp import DCS_ATOL, assert_lattice_equal_except_ties, to_dev
+from gpuhelp import DCS_ATOL, plan_lockstep, to_dev
 from paper_1310_7114_gb300 import build, itc, synth
 
 pytestmark = pytest.mark.gpu
@@ -38,19 +38,15 @@ def _oracle_run(img, p, W0, iters):
 
 
 def _lockstep(img, p, W0, iters, ref):
-    import torch
+    """The plan (one image, its widths) in lockstep with the oracle's steps."""
     A, F, sxx, K = ref
     tau, rho, s = _widths(p)
-    t = to_dev(img)
-    Fg, sg = itc.fields(t, tuple(tau), p.trunc, sigma_self=tuple(s))
-    W = np.asarray(W0, np.float64)
-    for _ in range(iters):
+
+    def ostep(b, W):
         Wn, raw, _ = oracle.lattice_step(A, F, tau, W, step_scale=p.step_scale, rho=rho)
-        Wg, _, _ = itc.step(t, Fg, sg, to_dev(W.astype(np.float32)), tuple(tau), p.trunc, p.step_scale,
-                            sigma_pair=tuple(rho), sigma_self=tuple(s))
-        torch.cuda.synchronize()
-        assert_lattice_equal_except_ties(Wg.cpu().numpy(), Wn, raw, what="lockstep")
-        W = Wn
+        return Wn, raw
+
+    plan_lockstep([img], [len(W0)], p, [W0], iters, ostep, what="widths lockstep")
 
 
 def _run(images, Ms, W0s, params):

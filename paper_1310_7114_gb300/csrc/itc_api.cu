@@ -17,7 +17,8 @@ using namespace itc;
 namespace {
 
 constexpr int kGridTileH2 = 64;   // fields tile height, 2-D
-constexpr size_t kFieldsStatusBytes = 256;   // itc_fields scratch: the status word's slot
+constexpr size_t kFieldsStatusBytes = 256;   // itc_fields scratch: the status word and the tile
+                                             // counter of the fields launch
 constexpr int kGridTileH3 = 32;   // fields tile height, 3-D
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.f; }
@@ -318,13 +319,15 @@ struct WsView {
     double* partials;
     double* scal;
     int* status;
+    int* counters;
 };
 
 // The full workspace: [fields of every image][partials][scalars][status words].
 WsView full_view(const PlanHeader* h, void* ws) {
     unsigned char* w = reinterpret_cast<unsigned char*>(ws);
     return {reinterpret_cast<float*>(w + h->ws_fields_off), reinterpret_cast<double*>(w + h->ws_partials_off),
-            reinterpret_cast<double*>(w + h->ws_scal_off), reinterpret_cast<int*>(w + h->ws_status_off)};
+            reinterpret_cast<double*>(w + h->ws_scal_off), reinterpret_cast<int*>(w + h->ws_status_off),
+            reinterpret_cast<int*>(w + h->ws_count_off)};
 }
 
 // The budgeted workspace: the tail of the full layout ([partials][scalars][status words], for the
@@ -346,7 +349,8 @@ WsView budget_view(const PlanHeader* h, void* ws, const ImageDesc* hdescs, int b
     const uintptr_t shift = (uintptr_t)hdescs[b0].field_off * sizeof(float);
     return {reinterpret_cast<float*>(window - shift), reinterpret_cast<double*>(w),
             reinterpret_cast<double*>(w + (h->ws_scal_off - h->ws_partials_off)),
-            reinterpret_cast<int*>(w + (h->ws_status_off - h->ws_partials_off))};
+            reinterpret_cast<int*>(w + (h->ws_status_off - h->ws_partials_off)),
+            reinterpret_cast<int*>(w + (h->ws_count_off - h->ws_partials_off))};
 }
 
 }  // namespace
@@ -402,6 +406,7 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
     fill_desc(img, p, 1, &L.one);
     L.fields = fields;
     L.status = reinterpret_cast<int*>(ws);
+    L.counter = L.status + 1;
     L.partials = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(ws) + kFieldsStatusBytes);
     L.tile_h = tile_h_of(img->ndim);
     L.absolute = (p->flags & ITC_FIELDS_ABSOLUTE) ? 1 : 0;
@@ -411,7 +416,8 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool tma = fields_tma_supported(img->ndim, L.taps.R[0], L.taps.R[1]) &&
                      encode_input_map(img, L.taps.R[0], &L.tmap_one);
-    rc = cuda_status(cudaMemsetAsync(L.status, 0, sizeof(int), s));   // ITC_OK unless a wait gives up
+    // status ITC_OK unless a wait gives up; no tiles handed out yet
+    rc = cuda_status(cudaMemsetAsync(L.status, 0, 2 * sizeof(int), s));
     if (rc) return rc;
     rc = cuda_status(launch_fields_any(L, tma, 0, (int)nt, L.taps.R[0], L.taps.R[1], img->ndim, img->dtype, s));
     if (rc) return rc;
@@ -636,6 +642,7 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     h->bwd_tiles = bwd;
 
     // workspace: [fields][S_XX partials][per-image backward scalars][per-image status words]
+    // [tile counters]
     size_t off = 0;
     h->ws_fields_off = 0;
     off = align_up((size_t)foff * sizeof(float), 256);
@@ -645,6 +652,8 @@ int itc_plan(int B, const itc_image* imgs, const int* M, const itc_params* p, in
     off = align_up(off + (size_t)B * 4 * sizeof(double), 256);
     h->ws_status_off = (long long)off;
     off = align_up(off + (size_t)B * sizeof(int), 256);
+    h->ws_count_off = (long long)off;
+    off = align_up(off + (size_t)io * sizeof(int), 256);   // io: every class list position fits
     h->ws_bytes = (long long)off;
     if (ws_bytes_out) *ws_bytes_out = off;
     memcpy(plan, buf.data(), need);
@@ -702,6 +711,10 @@ static int fields_range(const PlanHeader* h, const void* plan_host, const void* 
         L.mode = ci.self ? 1 : 0;
         L.status = v.status;
         L.test_stall = stall;
+        // this launch's tile counter (unique per class and first image, so that range calls on
+        // other streams do not share it), zeroed first
+        L.counter = v.counters + ci.list_off + p0;
+        if (cudaMemsetAsync(L.counter, 0, sizeof(int), s) != cudaSuccess) return ITC_ERR_CUDA;
         int rc;
         if (ci.recursive) {
             RecursiveLaunch R;
@@ -766,9 +779,11 @@ int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int
         L.grid_per_sm = ci.grid_per_sm;
         L.mode = ci.self ? 1 : 0;
         L.status = reinterpret_cast<int*>(w + h->ws_status_off);
+        L.counter = reinterpret_cast<int*>(w + h->ws_count_off) + ci.list_off;
         const bool tma = ci.tma && !ci.use_plain;
         for (int i = 0; i <= reps; ++i) {   // the first launch warms caches and is not timed
             if (i == 1 && cudaEventRecord(e0, s) != cudaSuccess) return ITC_ERR_CUDA;
+            if (cudaMemsetAsync(L.counter, 0, sizeof(int), s) != cudaSuccess) return ITC_ERR_CUDA;
             r = cuda_status(launch_fields_any(L, tma, 0, ci.ntiles, ci.taps.R[0], ci.taps.R[1], ci.ndim, ci.dtype, s));
             if (r) return r;
         }

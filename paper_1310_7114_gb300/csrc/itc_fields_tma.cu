@@ -139,6 +139,13 @@ struct TileCursor {
     }
 };
 
+// Tiles a persistent CTA takes from the launch's counter at a time.
+constexpr int kFieldsChunk = 4;
+// Row-pass items start at (tid + kItemRotate) mod kThreads: the threads of warps 0 and 1 take the
+// last item numbers of each round, so when a tile's items do not fill the last round those warps
+// have one item fewer -- warp 0 also walks the tile cursor and takes the next chunk.
+constexpr int kItemRotate = kThreads - 64;
+
 // Bounded wait for a staged tile: gives up after about one second (2^31 SM clocks); false means
 // the copy never landed.
 __device__ __forceinline__ bool wait_stage(uint64_t* bar, uint32_t parity) {
@@ -195,48 +202,69 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
     if (tid < 64) colbits[tid >> 5][(tid >> 2) & 7][tid & 3] = 0u;
     __syncthreads();
 
-    // This CTA's tiles: the contiguous run [t_lo, t_hi) of the launch's tiles [tile_base, ntiles),
-    // split evenly over the grid, so that neighbouring tiles share their image lookups.
-    const long long count = ntiles - L.tile_base;
-    const int t_lo = L.tile_base + (int)(count * blockIdx.x / gridDim.x);
-    const int t_hi = L.tile_base + (int)(count * (blockIdx.x + 1) / gridDim.x);
-
+    // Tiles are handed out dynamically, kFieldsChunk consecutive tiles at a time, from the launch's
+    // counter (zero at launch), so that CTAs whose tiles hold more data do not finish last: a
+    // persistent CTA takes a new chunk whenever it has issued the copies of its last one.  Warp 0
+    // walks the chunk's tiles with a cursor (image lookups loaded ahead within the chunk) and
+    // takes the next chunk's index one chunk ahead, so the atomic's latency is hidden.
     // tile copies run up to NST - 1 tiles ahead: the n-th tile of this CTA lands in stage n % NST,
     // whose previous tile (n - NST) has finished both passes by the time the copy is started
-    // called by all of warp 0: remember the cursor's tile for its stage, lane 0 starts the copy
     uint32_t inflight = 0;   // (thread 0) bit b: a copy into stage b has been started, not yet waited for
     // the cursor lives in shared memory and is advanced by thread 0 alone (it costs the other
     // threads no registers)
     __shared__ TileCursor s_cur;
+    __shared__ int s_chunk_end;    // first tile past the cursor's chunk; -1 once the tiles are exhausted
+    __shared__ int s_valid[NST];   // the stage holds a tile of this CTA
+    int next_chunk = 0;            // (lane 0 of warp 0) index of the chunk after the current one
+    // called by all of warp 0: the next tile of this CTA goes to stage `buf` (or none is left)
     auto issue = [&](int buf, bool copy) {
-        if (tid == 0) {
-            const int tv = s_cur.local % s_cur.tv, tu = s_cur.local / s_cur.tv;
-            const CUtensorMap* map = L.descs ? L.tmaps + s_cur.img : &L.tmap_one;
-            s_img[buf] = s_cur.img;
-            s_local[buf] = s_cur.local;
-            if (copy) {
-                mbar_expect_tx(&bar[buf], BOX_BYTES);
-                tma_load_2d(stage0 + buf * STAGE_BYTES, map, tv * TW - RA, tu * TH - R, &bar[buf]);
-                inflight |= 1u << buf;
+        __syncwarp();
+        if (s_chunk_end >= 0 && s_cur.t >= s_chunk_end) {   // warp-uniform: start the next chunk
+            const int c = __shfl_sync(0xffffffffu, next_chunk, 0);
+            const long long t0 = (long long)L.tile_base + (long long)c * kFieldsChunk;
+            if (t0 >= ntiles) {
+                if (tid == 0) s_chunk_end = -1;
+            } else {
+                if (tid == 0) next_chunk = atomicAdd(L.counter, 1);   // consumed one chunk later
+                TileCursor c0 = {};
+                c0.start(L, (int)t0);   // the whole warp: a warp search
+                if (tid == 0) {
+                    s_cur = c0;
+                    s_chunk_end = (int)(t0 + kFieldsChunk < ntiles ? t0 + kFieldsChunk : ntiles);
+                }
             }
-            s_cur.advance(L);
+            __syncwarp();
+        }
+        if (tid == 0) {
+            s_valid[buf] = s_chunk_end >= 0;
+            if (s_chunk_end >= 0) {
+                const int tv = s_cur.local % s_cur.tv, tu = s_cur.local / s_cur.tv;
+                const CUtensorMap* map = L.descs ? L.tmaps + s_cur.img : &L.tmap_one;
+                s_img[buf] = s_cur.img;
+                s_local[buf] = s_cur.local;
+                if (copy) {
+                    mbar_expect_tx(&bar[buf], BOX_BYTES);
+                    tma_load_2d(stage0 + buf * STAGE_BYTES, map, tv * TW - RA, tu * TH - R, &bar[buf]);
+                    inflight |= 1u << buf;
+                }
+                s_cur.advance(L);
+            }
         }
     };
 
-    int t = t_lo;
-    if (tid < 32 && t_lo < t_hi) {
-        TileCursor c0 = {};
-        c0.start(L, t_lo);   // the whole warp: the first lookup is a warp search
-        if (tid == 0) s_cur = c0;
+    if (tid < 32) {
+        if (tid == 0) {
+            next_chunk = atomicAdd(L.counter, 1);
+            s_cur.t = 0;
+            s_chunk_end = 0;   // no chunk yet: the first issue takes one
+        }
         for (int b = 0; b < NST; ++b)
-            if (t + b < t_hi)
-                // the test hook starts no copy for the first tile of CTA 0: its wait cannot end
-                issue(b, !(L.test_stall && blockIdx.x == 0 && b == 0));
+            // the test hook starts no copy for the first tile of CTA 0: its wait cannot end
+            issue(b, !(L.test_stall && blockIdx.x == 0 && b == 0));
     }
+    __syncthreads();   // s_valid of the first stages
     uint32_t phase = 0;   // bit b: parity of the next completion of bar[b]
     int n = 0;            // tiles of this CTA so far
-    const int kb = tid >> 4, cg = tid & 15;
-    const int k0 = kb * K, c0 = cg * 4;
     // S_XX share of the previous tile: its warps leave their sums in red[]; thread 0 adds them
     // (warp order) after the next barrier, so no tile needs a barrier of its own for it
     long long pending = -1;
@@ -261,28 +289,153 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
         }
     };
 
-    for (; t < t_hi; ++t) {
+    // Byte inputs (binary images: most windows hold no data) with the widest masks compact the row
+    // pass per warp: each warp first lists those of its items whose windows hold data (the others
+    // store their zeros meanwhile), then runs the listed items on consecutive lanes, so that its
+    // packed FMAs run on full lanes (a warp whose lanes diverge keeps the FMA pipe busy for its
+    // idle lanes too).  An item computes the same products in the same order whichever lane takes
+    // it.  On the ragged binary batch this pays at R = 12 (0.58 against 0.62 ms for that class);
+    // at R = 6 and 9 the second load of the listed items' windows costs more than it saves.
+    constexpr bool COMPACT = DTYPE == ITC_U8 && R >= 12;
+    constexpr int NITEMS = ROWS * 8;                 // row-pass items of a tile (8 per staged row)
+    constexpr int NROUNDS = (NITEMS + kThreads - 1) / kThreads;
+    __shared__ short s_items[COMPACT ? kThreads / 32 : 1][COMPACT ? NROUNDS * 32 : 1];   // per warp
+    const int lane = tid & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    const int rot = (tid + kItemRotate) & (kThreads - 1);   // first item of this thread
+
+    // the column unit (K rows x 4 columns at rows k0.., columns c0..): A, F_u, F_v with packed FMAs
+    // over column pairs, stored; returns the unit's share of S_XX (h from the staged box)
+    auto column_unit = [&](const unsigned char* stage, int k0, int c0, int u0, int v0, int H, int W, int fpitch,
+                           float* fbase, long long plane) -> float {
+        float2 aA[K][2], aU[K][2], aV[K][2];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+            for (int p = 0; p < 2; ++p) { aA[kk][p] = f2(0.f, 0.f); aU[kk][p] = f2(0.f, 0.f); aV[kk][p] = f2(0.f, 0.f); }
+        const float* Tp = sT + k0 * TW + c0;
+        const float ub = (float)(u0 - R + k0);
+#pragma unroll
+        for (int i = 0; i < K + 2 * R; ++i) {
+            const float4 t4 = *reinterpret_cast<const float4*>(Tp + i * TW);
+            const float4 v4 = *reinterpret_cast<const float4*>(Tp + ROWS * TW + i * TW);
+            const float2 t01 = f2(t4.x, t4.y), t23 = f2(t4.z, t4.w);
+            const float2 v01 = f2(v4.x, v4.y), v23 = f2(v4.z, v4.w);
+            float2 tu01, tu23;
+            if constexpr (ABS) {
+                const float uc = ub + (float)i;
+                tu01 = f2(t4.x * uc, t4.y * uc);
+                tu23 = f2(t4.z * uc, t4.w * uc);
+            }
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int e = i - kk;
+                if (e >= 0 && e <= 2 * R) {
+                    const float2 g2 = f2(tp.gu[e], tp.gu[e]);
+                    aA[kk][0] = __ffma2_rn(g2, t01, aA[kk][0]);
+                    aA[kk][1] = __ffma2_rn(g2, t23, aA[kk][1]);
+                    if constexpr (ABS) {
+                        aU[kk][0] = __ffma2_rn(g2, tu01, aU[kk][0]);
+                        aU[kk][1] = __ffma2_rn(g2, tu23, aU[kk][1]);
+                    } else {
+                        const float2 dg2 = f2(tp.dgu[e], tp.dgu[e]);
+                        aU[kk][0] = __ffma2_rn(dg2, t01, aU[kk][0]);
+                        aU[kk][1] = __ffma2_rn(dg2, t23, aU[kk][1]);
+                    }
+                    aV[kk][0] = __ffma2_rn(g2, v01, aV[kk][0]);
+                    aV[kk][1] = __ffma2_rn(g2, v23, aV[kk][1]);
+                }
+            }
+        }
+        float ps = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int u = u0 + k0 + kk;
+            if (u < H) {
+                float* o = fbase + (long long)u * fpitch + v0 + c0;
+                st4(o, aA[kk][0].x, aA[kk][0].y, aA[kk][1].x, aA[kk][1].y);
+                st4(o + plane, aU[kk][0].x, aU[kk][0].y, aU[kk][1].x, aU[kk][1].y);
+                st4(o + 2 * plane, aV[kk][0].x, aV[kk][0].y, aV[kk][1].x, aV[kk][1].y);
+                // h at the four outputs, from the staged box (row k0 + kk + R, columns RA + c0 ..)
+                float h4[4];
+                if constexpr (DTYPE == ITC_U8) {
+                    const uint32_t hw = *reinterpret_cast<const uint32_t*>(stage + (k0 + kk + R) * BW + RA + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        h4[j] = __int_as_float((int)__byte_perm(hw, 0x4B000000u, 0x7540u | (unsigned)j)) - 8388608.f;
+                } else {
+                    const float4 hf = *reinterpret_cast<const float4*>(stage + ((size_t)(k0 + kk + R) * BW + RA + c0) * 4);
+                    h4[0] = hf.x; h4[1] = hf.y; h4[2] = hf.z; h4[3] = hf.w;
+                }
+                const float a4[4] = {aA[kk][0].x, aA[kk][0].y, aA[kk][1].x, aA[kk][1].y};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (v0 + c0 + j < W) ps = fmaf(h4[j], a4[j], ps);
+            }
+        }
+        return ps;
+    };
+    // the column unit of thread tid: inside the image, and any T row of its window nonzero
+    auto unit_state = [&](int k0, int c0, int cgb, int par, int u0, int v0, int H, int W, bool* active) -> bool {
+        const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
+        bool t_any = false;
+        if (col_active) {
+            const uint32_t* cb = colbits[par][cgb];
+            const int w0 = k0 >> 5;
+            const unsigned long long both = ((unsigned long long)cb[w0 + 1] << 32) | cb[w0];
+            const unsigned long long need = (K + 2 * R >= 64) ? ~0ull : ((1ull << (K + 2 * R)) - 1ull);
+            t_any = ((both >> (k0 & 31)) & need) != 0ull;
+        }
+        *active = col_active && t_any;
+        return col_active;
+    };
+    auto zero_unit = [&](int k0, int c0, int u0, int v0, int H, int fpitch, float* fbase, long long plane) {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int u = u0 + k0 + kk;
+            if (u >= H) break;
+            float* o = fbase + (long long)u * fpitch + v0 + c0;
+#pragma unroll
+            for (int ff = 0; ff < 3; ++ff) st4(o + ff * plane, 0.f, 0.f, 0.f, 0.f);
+        }
+    };
+
+    for (;;) {
         const int buf = n % NST;
         const unsigned char* stage = stage0 + buf * STAGE_BYTES;
-        if (tid == 0) {
+        if (tid == 0 && s_valid[buf]) {
             if (wait_stage(&bar[buf], (phase >> buf) & 1u)) inflight &= ~(1u << buf);
             else s_abort = 1;
         }
         __syncthreads();   // the staged tile has landed; the previous tile's passes are done
         if (tid == 0) flush();
+        if (!s_valid[buf]) break;   // no tiles left for this CTA (uniform: read after the barrier)
         if (s_abort) {
-            // every tile this CTA still owns gets a NaN S_XX share and its image the status
-            // ITC_ERR_TIMEOUT (its fields stay unwritten); then the copies still in flight land
-            // (bounded waits)
+            // every tile this CTA still owns -- this one, those staged ahead and the rest of its
+            // chunk -- gets a NaN S_XX share and its image the status ITC_ERR_TIMEOUT (their fields
+            // stay unwritten); then the copies still in flight land (bounded waits)
             if (tid < 32) {
-                for (int tt = t; tt < t_hi; ++tt) {
+                auto mark = [&](int im, int lc) {
+                    const ImageDesc* d2 = L.descs ? L.descs + im : &L.one;
+                    L.partials[d2->partial_off + lc] = __longlong_as_double(0x7ff8000000000000LL);
+                    if (L.status) L.status[L.descs ? im : 0] = ITC_ERR_TIMEOUT;
+                };
+                // staged: tiles n .. n + NST - 1 before the first tile's wait, n .. n + NST - 2 later
+                // (the last stage still holds tile n - 1, whose share is already written)
+                if (tid == 0)
+                    for (int b = 0; b < (n == 0 ? NST : NST - 1); ++b)
+                        if (s_valid[(buf + b) % NST]) mark(s_img[(buf + b) % NST], s_local[(buf + b) % NST]);
+                for (int tt = s_cur.t; s_chunk_end >= 0 && tt < s_chunk_end; ++tt) {
                     int im, lc;
                     locate_warp(L, tt, im, lc);
-                    const ImageDesc* d2 = L.descs ? L.descs + im : &L.one;
-                    if (tid == 0) {
-                        L.partials[d2->partial_off + lc] = __longlong_as_double(0x7ff8000000000000LL);
-                        if (L.status) L.status[L.descs ? im : 0] = ITC_ERR_TIMEOUT;
-                    }
+                    if (tid == 0) mark(im, lc);
+                }
+                // and the chunk taken ahead, which no other CTA will take
+                const long long tn = (long long)L.tile_base + (long long)__shfl_sync(0xffffffffu, next_chunk, 0) * kFieldsChunk;
+                for (long long tt = tn; s_chunk_end >= 0 && tt < tn + kFieldsChunk && tt < ntiles; ++tt) {
+                    int im, lc;
+                    locate_warp(L, (int)tt, im, lc);
+                    if (tid == 0) mark(im, lc);
                 }
                 if (tid == 0)
                     for (int b = 0; b < NST; ++b)
@@ -293,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
         }
         phase ^= 1u << buf;
         // the stage of the previous tile is free: start the copy NST - 1 tiles ahead into it
-        if (tid < 32 && n > 0 && t + NST - 1 < t_hi) issue((n - 1) % NST, true);
+        if (tid < 32 && n > 0) issue((n - 1) % NST, true);
         ++n;
         const int par = n & 1;
         if (tid < 32) colbits[par ^ 1][tid >> 2][tid & 3] = 0u;   // for the next tile
@@ -307,37 +460,28 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
         if constexpr (DTYPE == ITC_U8) {
             // ---- pass along v, read straight from the staged box.  An item is 4 outputs in each of
             // two neighbouring rows: the two rows' inputs are the halves of every packed operand, so
-            // the packed FMAs need no realigned pairs; windows without data store zeros
+            // the packed FMAs need no realigned pairs
             constexpr int NW4 = 4 + 2 * R;                   // inputs of 4 neighbouring outputs
             constexpr int NQ4 = (OFF + NW4 + 3) / 4;         // 4-element groups covering the window
-            for (int item = tid; item < ROWS * 8; item += kThreads) {
+            // the item's input words (box columns c - R + RA - OFF .., a multiple of 4) of its two
+            // rows; rows outside the image read as zero
+            auto load_item = [&](int item, uint32_t (&w0)[NQ4], uint32_t (&w1)[NQ4]) {
                 const int r0 = (item >> 4) * 2, c = (item & 15) * 4;
-                if (v0 + c >= W) continue;
                 const int gu0 = u0 - R + r0;
                 const bool in0 = gu0 >= 0 && gu0 < H, in1 = gu0 + 1 >= 0 && gu0 + 1 < H;
-                float* oT = sT + r0 * TW + c;
-                float* oV = oT + ROWS * TW;
-                // the window's 4-groups: box columns c - R + RA - OFF ... (a multiple of 4)
                 const int g0 = (c - R + RA - OFF) >> 2;
-                uint32_t w0[NQ4], w1[NQ4];
-                bool nz0 = false, nz1 = false;
                 const uint32_t* row0 = reinterpret_cast<const uint32_t*>(stage + r0 * BW);
                 const uint32_t* row1 = row0 + BW / 4;
 #pragma unroll
                 for (int q = 0; q < NQ4; ++q) {
                     w0[q] = in0 ? row0[g0 + q] : 0u;
                     w1[q] = in1 ? row1[g0 + q] : 0u;
-                    nz0 |= w0[q] != 0u;
-                    nz1 |= w1[q] != 0u;
                 }
-                if (!(nz0 | nz1)) {
-                    st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + TW, 0.f, 0.f, 0.f, 0.f);
-                    st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + TW, 0.f, 0.f, 0.f, 0.f);
-                    continue;
-                }
-                if (nz0) atomicOr(&colbits[par][c >> 3][r0 >> 5], 1u << (r0 & 31));
-                if (nz1) atomicOr(&colbits[par][c >> 3][(r0 + 1) >> 5], 1u << ((r0 + 1) & 31));
-                // inputs as (row r0, row r0 + 1) pairs; bytes -> floats exactly (2^23 + b, minus 2^23)
+            };
+            // one item from its input words: inputs as (row r0, row r0 + 1) pairs, bytes -> floats
+            // exactly (2^23 + b, minus 2^23), the two masks' FMAs, T and T_v stored
+            auto compute_item = [&](int item, const uint32_t (&w0)[NQ4], const uint32_t (&w1)[NQ4]) {
+                const int r0 = (item >> 4) * 2, c = (item & 15) * 4;
                 float2 X[NW4];
 #pragma unroll
                 for (int i = 0; i < NW4; ++i) {
@@ -357,27 +501,73 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
                 }
                 float2 aT[4], aV[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) { aT[j] = f2(0.f, 0.f); aV[j] = f2(0.f, 0.f); }
+                for (int jj = 0; jj < 4; ++jj) { aT[jj] = f2(0.f, 0.f); aV[jj] = f2(0.f, 0.f); }
 #pragma unroll
                 for (int d = 0; d <= 2 * R; ++d) {
                     const float2 g2 = f2(tp.gv[d], tp.gv[d]);
                     const float2 dg2 = f2(tp.dgv[d], tp.dgv[d]);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        aT[j] = __ffma2_rn(g2, X[j + d], aT[j]);
-                        if constexpr (ABS) aV[j] = __ffma2_rn(g2, XV[j + d], aV[j]);
-                        else aV[j] = __ffma2_rn(dg2, X[j + d], aV[j]);
+                    for (int jj = 0; jj < 4; ++jj) {
+                        aT[jj] = __ffma2_rn(g2, X[jj + d], aT[jj]);
+                        if constexpr (ABS) aV[jj] = __ffma2_rn(g2, XV[jj + d], aV[jj]);
+                        else aV[jj] = __ffma2_rn(dg2, X[jj + d], aV[jj]);
                     }
                 }
+                float* oT = sT + r0 * TW + c;
+                float* oV = oT + ROWS * TW;
                 st4(oT, aT[0].x, aT[1].x, aT[2].x, aT[3].x); st4(oT + TW, aT[0].y, aT[1].y, aT[2].y, aT[3].y);
                 st4(oV, aV[0].x, aV[1].x, aV[2].x, aV[3].x); st4(oV + TW, aV[0].y, aV[1].y, aV[2].y, aV[3].y);
+            };
+            // every item of this thread: windows without data store zeros; with COMPACT the items
+            // with data are listed per warp and run afterwards on consecutive lanes, otherwise
+            // they run in place
+            short* wl = s_items[COMPACT ? (tid >> 5) : 0];
+            int cnt = 0;   // warp-uniform
+#pragma unroll 1
+            for (int k = 0; k < NROUNDS; ++k) {
+                const int item = rot + k * kThreads;
+                const int r0 = (item >> 4) * 2, c = (item & 15) * 4;
+                bool nz0 = false, nz1 = false;
+                if (item < NITEMS && v0 + c < W) {
+                    uint32_t w0[NQ4], w1[NQ4];
+                    load_item(item, w0, w1);
+#pragma unroll
+                    for (int q = 0; q < NQ4; ++q) {
+                        nz0 |= w0[q] != 0u;
+                        nz1 |= w1[q] != 0u;
+                    }
+                    if (!(nz0 | nz1)) {
+                        float* oT = sT + r0 * TW + c;
+                        float* oV = oT + ROWS * TW;
+                        st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + TW, 0.f, 0.f, 0.f, 0.f);
+                        st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + TW, 0.f, 0.f, 0.f, 0.f);
+                    }
+                    if (nz0) atomicOr(&colbits[par][c >> 3][r0 >> 5], 1u << (r0 & 31));
+                    if (nz1) atomicOr(&colbits[par][c >> 3][(r0 + 1) >> 5], 1u << ((r0 + 1) & 31));
+                    if constexpr (!COMPACT)
+                        if (nz0 | nz1) compute_item(item, w0, w1);
+                }
+                if constexpr (COMPACT) {
+                    const unsigned ba = __ballot_sync(0xffffffffu, nz0 | nz1);
+                    if (nz0 | nz1) wl[cnt + __popc(ba & lanes_below)] = (short)item;
+                    cnt += __popc(ba);
+                }
+            }
+            if constexpr (COMPACT) {
+                __syncwarp();
+                for (int j = lane; j < cnt; j += 32) {
+                    const int item = wl[j];
+                    uint32_t w0[NQ4], w1[NQ4];
+                    load_item(item, w0, w1);
+                    compute_item(item, w0, w1);
+                }
             }
         } else {
             // 4-byte inputs: 8 outputs of one row per item, pairs of neighbouring columns per packed
             // FMA (the pairs of rows of byte inputs would need register moves here)
             // ---- pass along v, read straight from the staged box: 8 outputs per item, pairs of
             // neighbouring columns per packed FMA; windows without data store zeros
-            for (int item = tid; item < ROWS * 8; item += kThreads) {
+            for (int item = rot; item < ROWS * 8; item += kThreads) {
                 const int r = item >> 3, c = (item & 7) * 8;
                 const int gu = u0 - R + r;
                 if (v0 + c >= W) continue;
@@ -389,17 +579,11 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
                 float4 f[NQ];
                 bool nz = false;
                 if (gu >= 0 && gu < H) {
-                    if constexpr (DTYPE == ITC_U8) {
-                        const uint32_t* row = reinterpret_cast<const uint32_t*>(stage + r * BW);
+                    const float4* row = reinterpret_cast<const float4*>(stage + (size_t)r * BW * 4);
 #pragma unroll
-                        for (int q = 0; q < NQ; ++q) { w[q] = row[g0 + q]; nz |= w[q] != 0u; }
-                    } else {
-                        const float4* row = reinterpret_cast<const float4*>(stage + (size_t)r * BW * 4);
-#pragma unroll
-                        for (int q = 0; q < NQ; ++q) {
-                            f[q] = row[g0 + q];
-                            nz |= (f[q].x != 0.f) | (f[q].y != 0.f) | (f[q].z != 0.f) | (f[q].w != 0.f);
-                        }
+                    for (int q = 0; q < NQ; ++q) {
+                        f[q] = row[g0 + q];
+                        nz |= (f[q].x != 0.f) | (f[q].y != 0.f) | (f[q].z != 0.f) | (f[q].w != 0.f);
                     }
                 }
                 if (!nz) {
@@ -437,101 +621,15 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
             }
         }
         __syncthreads();
-
-        // ---- pass along u: K rows x 4 columns per thread, column pairs per packed FMA
-        // T rows k0 .. k0 + K + 2R - 1 of this thread's 8-column block all zero -> outputs are zero
-        const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
-        bool t_any = false;
-        if (col_active) {
-            const uint32_t* cb = colbits[par][cg >> 1];
-            const int rlo = k0, w0 = rlo >> 5;
-            const unsigned long long both = ((unsigned long long)cb[w0 + 1] << 32) | cb[w0];
-            const unsigned long long need = (K + 2 * R >= 64) ? ~0ull : ((1ull << (K + 2 * R)) - 1ull);
-            t_any = ((both >> (rlo & 31)) & need) != 0ull;
-            if (!t_any) {
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    const int u = u0 + k0 + kk;
-                    if (u >= H) break;
-                    float* o = fbase + (long long)u * fpitch + v0 + c0;
-#pragma unroll
-                    for (int ff = 0; ff < 3; ++ff) st4(o + ff * plane, 0.f, 0.f, 0.f, 0.f);
-                }
-            }
-        }
-        float part = 0.f;
-        if (col_active && t_any) {
-            float2 aA[K][2], aU[K][2], aV[K][2];
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk)
-#pragma unroll
-                for (int p = 0; p < 2; ++p) { aA[kk][p] = f2(0.f, 0.f); aU[kk][p] = f2(0.f, 0.f); aV[kk][p] = f2(0.f, 0.f); }
-            const float* Tp = sT + k0 * TW + c0;
-            const float ub = (float)(u0 - R + k0);
-#pragma unroll
-            for (int i = 0; i < K + 2 * R; ++i) {
-                const float4 t4 = *reinterpret_cast<const float4*>(Tp + i * TW);
-                const float4 v4 = *reinterpret_cast<const float4*>(Tp + ROWS * TW + i * TW);
-                const float2 t01 = f2(t4.x, t4.y), t23 = f2(t4.z, t4.w);
-                const float2 v01 = f2(v4.x, v4.y), v23 = f2(v4.z, v4.w);
-                float2 tu01, tu23;
-                if constexpr (ABS) {
-                    const float uc = ub + (float)i;
-                    tu01 = f2(t4.x * uc, t4.y * uc);
-                    tu23 = f2(t4.z * uc, t4.w * uc);
-                }
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    const int e = i - kk;
-                    if (e >= 0 && e <= 2 * R) {
-                        const float2 g2 = f2(tp.gu[e], tp.gu[e]);
-                        aA[kk][0] = __ffma2_rn(g2, t01, aA[kk][0]);
-                        aA[kk][1] = __ffma2_rn(g2, t23, aA[kk][1]);
-                        if constexpr (ABS) {
-                            aU[kk][0] = __ffma2_rn(g2, tu01, aU[kk][0]);
-                            aU[kk][1] = __ffma2_rn(g2, tu23, aU[kk][1]);
-                        } else {
-                            const float2 dg2 = f2(tp.dgu[e], tp.dgu[e]);
-                            aU[kk][0] = __ffma2_rn(dg2, t01, aU[kk][0]);
-                            aU[kk][1] = __ffma2_rn(dg2, t23, aU[kk][1]);
-                        }
-                        aV[kk][0] = __ffma2_rn(g2, v01, aV[kk][0]);
-                        aV[kk][1] = __ffma2_rn(g2, v23, aV[kk][1]);
-                    }
-                }
-            }
-            float ps = 0.f;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-                const int u = u0 + k0 + kk;
-                if (u < H) {
-                    float* o = fbase + (long long)u * fpitch + v0 + c0;
-                    st4(o, aA[kk][0].x, aA[kk][0].y, aA[kk][1].x, aA[kk][1].y);
-                    st4(o + plane, aU[kk][0].x, aU[kk][0].y, aU[kk][1].x, aU[kk][1].y);
-                    st4(o + 2 * plane, aV[kk][0].x, aV[kk][0].y, aV[kk][1].x, aV[kk][1].y);
-                    // h at the four outputs, from the staged box (row k0 + kk + R, columns RA + c0 ..)
-                    float h4[4];
-                    if constexpr (DTYPE == ITC_U8) {
-                        const uint32_t hw =
-                            *reinterpret_cast<const uint32_t*>(stage + (k0 + kk + R) * BW + RA + c0);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            h4[j] = __int_as_float((int)__byte_perm(hw, 0x4B000000u, 0x7540u | (unsigned)j)) - 8388608.f;
-                    } else {
-                        const float4 hf =
-                            *reinterpret_cast<const float4*>(stage + ((size_t)(k0 + kk + R) * BW + RA + c0) * 4);
-                        h4[0] = hf.x; h4[1] = hf.y; h4[2] = hf.z; h4[3] = hf.w;
-                    }
-                    const float a4[4] = {aA[kk][0].x, aA[kk][0].y, aA[kk][1].x, aA[kk][1].y};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (v0 + c0 + j < W) ps = fmaf(h4[j], a4[j], ps);
-                }
-            }
-            part = ps;
-        }
+        // ---- pass along u: K rows x 4 columns per thread, column pairs per packed FMA; a unit
+        // whose T rows k0 .. k0 + K + 2R - 1 of its 8-column block are all zero stores zeros
+        const int k0 = (tid >> 4) * K, c0 = (tid & 15) * 4;
+        bool active;
+        const bool inside = unit_state(k0, c0, (tid & 15) >> 1, par, u0, v0, H, W, &active);
+        if (inside && !active) zero_unit(k0, c0, u0, v0, H, fpitch, fbase, plane);
+        float part = active ? column_unit(stage, k0, c0, u0, v0, H, W, fpitch, fbase, plane) : 0.f;
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if ((tid & 31) == 0) red[tid >> 5] = (double)part;   // FP32 within a warp, FP64 across warps
+        if (lane == 0) red[tid >> 5] = (double)part;   // FP32 within a warp, FP64 across warps
         if (tid == 0) pending = dp->partial_off + local;
     }
     __syncthreads();
@@ -549,9 +647,9 @@ cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem)) != cudaSuccess) return e;
     if (L.grid_per_sm > 0 && L.grid_per_sm < per_sm) per_sm = L.grid_per_sm;   // tuned persistent grid
-    const int count = ntiles - L.tile_base;
-    const int grid = count < sms * (per_sm > 0 ? per_sm : 1) ? count : sms * (per_sm > 0 ? per_sm : 1);
-    k<<<grid, kThreads, smem, s>>>(L, ntiles);
+    const int chunks = (ntiles - L.tile_base + kFieldsChunk - 1) / kFieldsChunk;
+    const int cap = sms * (per_sm > 0 ? per_sm : 1);
+    k<<<chunks < cap ? chunks : cap, kThreads, smem, s>>>(L, ntiles);
     return cudaGetLastError();
 }
 
@@ -582,6 +680,7 @@ int fields_tma_box(int dtype, int R, int tile_h, int* box_w, int* box_h) {
 
 cudaError_t launch_fields_tma(const FieldsLaunch& L, int ntiles, int R, int dtype, cudaStream_t s) {
     if (ntiles - L.tile_base <= 0) return cudaSuccess;
+    if (!L.counter) return cudaErrorInvalidValue;   // the tile counter is required (zeroed by the caller)
     const bool abs_ = L.absolute != 0;
     if (dtype == ITC_U8) return abs_ ? dispatch<true, ITC_U8>(L, ntiles, R, s) : dispatch<false, ITC_U8>(L, ntiles, R, s);
     return abs_ ? dispatch<true, ITC_F32>(L, ntiles, R, s) : dispatch<false, ITC_F32>(L, ntiles, R, s);

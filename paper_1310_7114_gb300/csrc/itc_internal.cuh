@@ -112,6 +112,9 @@ struct PlanHeader {
     long long nints;
     long long ws_scal_off;      // bytes: per-image backward scalars (4 doubles each)
     long long ws_status_off;    // bytes: per-image device status words of the fields pass (B ints)
+    long long ws_count_off;     // bytes: tile counters of the fields launches, one per class list
+                                // position (the launch of class c from list position p uses
+                                // list_off(c) + p)
     long long bwd_tiles;        // backward pixel tiles over all images
     int max_bwd_tiles;          // most backward pixel tiles of one image
     int bwd_order_off;          // offset (ints) of the backward image order (B ints, most tiles first)
@@ -152,6 +155,7 @@ struct FieldsLaunch {
     int grid_per_sm;            // persistent CTAs per SM (0: as many as fit)
     int mode;                   // 0: every field plane; 1: A only, into the A_s plane, S_XX
                                 // partials at sxx_off (self-overlap pass); 2: S_XX partials only
+    int* counter;               // tensor-tile path: chunks of tiles handed out so far (0 at launch)
     int* status;                // device status words: one per image of the plan (batched) or one
                                 // for the call (single image); a CTA whose bounded wait gives up
                                 // writes ITC_ERR_TIMEOUT for every image it still owned tiles of

@@ -58,6 +58,7 @@ WORKLOADS = {
                n=1, iters=100),
     "c5": dict(desc="one 256x256 gray image as a 256^3 [u,v,g] lattice, sigma=(3,3,8), M=64, 100 iterations, "
                     "fwd+bwd", n=1, iters=100),
+    "c1": dict(desc="one 64x64 binary image (5 ellipses), M=8, sigma=2, 50 iterations, fwd+bwd", n=1, iters=50),
 }
 
 
@@ -88,6 +89,10 @@ def make_workload(name, rank, n=None):
         images = [synth.c2_image(rank)]
         W0s = [synth.init_codebook(synth.rng_for(2, rank), images[0].astype(np.float32), 64)]
         return images, [64], [dict(sigma=4.0, iters=100)], W0s, [2], [1]
+    if name == "c1":
+        images = [synth.c1_image(rank)]
+        W0s = [synth.init_codebook(synth.rng_for(1, rank), images[0].astype(np.float32), 8)]
+        return images, [8], [dict(sigma=2.0, iters=50)], W0s, [2], [1]
     if name == "c5":
         images = [synth.c5_gray(rank)]
         W0s = [synth.init_codebook_gray(synth.rng_for(5, rank), images[0], 64)]

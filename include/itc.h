@@ -335,8 +335,8 @@ int itc_run_staged(const void* plan_host, const void* plan_dev, const void* host
 
 /*
  * itc_autotune -- pick, per parameter class of a plan, the fields-pass configuration that runs
- * fastest on this GPU for this batch: the rows of output per tile (64 or 32, i.e. how much of
- * the R-wide halo the row pass recomputes), the number of persistent CTAs per SM (1 or as many
+ * fastest on this GPU for this batch: the rows of output per tile (128, 64 or 32, i.e. how much
+ * of the R-wide halo the row pass recomputes), the number of persistent CTAs per SM (1 or as many
  * as fit), and the input staging (tensor-memory-accelerator tiles, where the image rows are
  * 16-byte aligned, or plain loads).  Each candidate is timed with CUDA events over `reps`
  * launches (after one untimed launch) on `stream`; the choice is stored in the host plan and
@@ -349,7 +349,7 @@ int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int
 
 /*
  * itc_plan_configure -- set the fields-pass configuration of class c by hand (what itc_autotune
- * chooses): staging 1 = tensor tiles with tile_h 32 or 64 output rows, staging 0 = plain loads
+ * chooses): staging 1 = tensor tiles with tile_h 32, 64 or 128 output rows, staging 0 = plain loads
  * with the fixed tile height of the lattice dimension (64 in 2-D, 32 in 3-D; pass it);
  * grid_per_sm = persistent CTAs per SM (0 = as many as fit, else 1..64).  Updates the host
  * plan and copies it to plan_dev (synchronously on `stream`).  Errors: ITC_ERR_INVALID_ARG,

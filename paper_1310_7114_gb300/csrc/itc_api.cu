@@ -797,13 +797,14 @@ int itc_autotune(void* plan_host, void* plan_dev, void* ws, size_t ws_bytes, int
         ClassInfo& ci = h->cls[c];
         if (ci.ndim != 2 || ci.self || ci.recursive) continue;   // one configuration for these
         struct Cand { int plain, tile_h, grid; };
-        Cand cands[5];
+        Cand cands[6];
         int nc = 0;
         if (ci.tma) {
             cands[nc++] = {0, 64, 0};
             cands[nc++] = {0, 64, 1};
             cands[nc++] = {0, 32, 0};
             cands[nc++] = {0, 32, 1};
+            cands[nc++] = {0, 128, 0};
         }
         cands[nc++] = {1, 64, 0};
         float best = 3.4e38f;
@@ -852,7 +853,8 @@ int itc_plan_configure(void* plan_host, void* plan_dev, int c, int tile_h, int g
     ClassInfo& ci = h->cls[c];
     if (ci.self || ci.recursive) return ITC_ERR_UNSUPPORTED;   // one configuration for these
     if (staging == 1 && !ci.tma) return ITC_ERR_UNSUPPORTED;
-    if (staging == 1 ? (tile_h != 32 && tile_h != 64) : tile_h != tile_h_of(ci.ndim)) return ITC_ERR_INVALID_ARG;
+    if (staging == 1 ? (tile_h != 32 && tile_h != 64 && tile_h != 128) : tile_h != tile_h_of(ci.ndim))
+        return ITC_ERR_INVALID_ARG;
     ci.use_plain = staging ? 0 : 1;
     ci.tile_h = tile_h;
     ci.grid_per_sm = grid_per_sm;

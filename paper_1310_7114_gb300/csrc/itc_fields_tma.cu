@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
     __shared__ int s_abort;
     // colbits[p][b] (tile parity p): bits over staged rows whose T in 8-column block b is not
     // known to be zero; the buffer of the next tile is cleared while this one is read
-    __shared__ uint32_t colbits[2][TW / 8][4];
+    constexpr int CBW = (ROWS + 31) / 32 + 1;   // words per block and parity (one spare for 64-bit reads)
+    __shared__ uint32_t colbits[2][TW / 8][CBW];
     __shared__ int s_img[NST], s_local[NST];   // image and local tile of the copy in each stage
     const Taps& tp = L.taps;
     const int tid = threadIdx.x;
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
         mbar_init_fence();
         s_abort = 0;
     }
-    if (tid < 64) colbits[tid >> 5][(tid >> 2) & 7][tid & 3] = 0u;
+    for (int i = tid; i < 2 * (TW / 8) * CBW; i += kThreads) (&colbits[0][0][0])[i] = 0u;
     __syncthreads();
 
     // Tiles are handed out dynamically, kFieldsChunk consecutive tiles at a time, from the launch's
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
         if (tid < 32 && n > 0) issue((n - 1) % NST, true);
         ++n;
         const int par = n & 1;
-        if (tid < 32) colbits[par ^ 1][tid >> 2][tid & 3] = 0u;   // for the next tile
+        if (tid < (TW / 8) * CBW) (&colbits[par ^ 1][0][0])[tid] = 0u;   // for the next tile
         const int img = s_img[buf], local = s_local[buf];
         const ImageDesc* dp = L.descs ? L.descs + img : &L.one;
         const int H = dp->H, W = dp->W, fpitch = dp->fpitch;
@@ -655,6 +656,11 @@ cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
 
 template <bool ABS, int DTYPE>
 cudaError_t dispatch(const FieldsLaunch& L, int ntiles, int R, cudaStream_t s) {
+    if (L.tile_h == 128) {
+        if (R == 6) return launch_tma<6, ABS, DTYPE, 128>(L, ntiles, s);
+        if (R == 9) return launch_tma<9, ABS, DTYPE, 128>(L, ntiles, s);
+        return launch_tma<12, ABS, DTYPE, 128>(L, ntiles, s);
+    }
     if (L.tile_h == 32) {
         if (R == 6) return launch_tma<6, ABS, DTYPE, 32>(L, ntiles, s);
         if (R == 9) return launch_tma<9, ABS, DTYPE, 32>(L, ntiles, s);

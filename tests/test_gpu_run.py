@@ -305,7 +305,8 @@ def test_every_fields_configuration_gives_the_same_result():
     same amount through log S_XX."""
     plan, W0s = _c3_plan(48, 12)
     base = _fields_and_run(plan, W0s, 12)
-    configs = [(64, 0, "plain"), (64, 1, "tma"), (32, 0, "tma"), (32, 1, "tma"), (32, 2, "tma"), (64, 0, "tma")]
+    configs = [(64, 0, "plain"), (64, 1, "tma"), (32, 0, "tma"), (32, 1, "tma"), (32, 2, "tma"), (128, 0, "tma"),
+               (128, 1, "tma"), (64, 0, "tma")]
     classes = plan.classes()
     assert sum(info["staging"] == "tma" for info in classes) >= 2
     for c, info in enumerate(classes):
@@ -328,7 +329,7 @@ def test_autotuned_plan_keeps_results():
     info = plan.autotune(reps=2)
     assert len(info) >= 2
     for c in info:
-        assert c["tuned_ms"] > 0 and c["tile_h"] in (32, 64) and c["staging"] in ("tma", "plain")
+        assert c["tuned_ms"] > 0 and c["tile_h"] in (32, 64, 128) and c["staging"] in ("tma", "plain")
     F, W, st = _fields_and_run(plan, W0s, 10)
     assert all(np.array_equal(a, b) for a, b in zip(F, base[0]))
     assert np.array_equal(W, base[1])

@@ -828,7 +828,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (seeded stand-ins for the paper's MPEG-7 shapes; no dataset on the box)",
+        "data": "synthetic (seeded stand-ins for the paper's MPEG-7 shapes, which are not available)",
         "config": {"workload": f"{name}: {WORKLOADS[name]['desc']}", "images_per_gpu": B,
                    "pixels_per_gpu": int(sum(im.size for im in images)),
                    "l2": "inputs larger than L2 (packed images %.0f MB, fields %.0f MB per step)"

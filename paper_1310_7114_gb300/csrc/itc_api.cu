@@ -118,6 +118,13 @@ void make_taps(const itc_params* p, int ndim, Taps* t, bool self = false) {
     fill_taps(t->sigma[0], t->R[0], t->gu, t->dgu);
     fill_taps(t->sigma[1], t->R[1], t->gv, t->dgv);
     if (ndim == 3) fill_taps(t->sigma[2], t->R[2], t->gg, t->dgg);
+    float a = 0.f, b = 0.f;
+    for (int d = 0; d <= 2 * t->R[1]; ++d) {
+        a = fmaf(t->gv[d], 1.f, a);
+        b = fmaf(t->dgv[d], 1.f, b);
+    }
+    t->ones_gv = a;
+    t->ones_dgv = b;
 }
 
 int tile_h_of(int ndim) { return ndim == 3 ? kGridTileH3 : kGridTileH2; }

@@ -139,6 +139,17 @@ struct TileCursor {
     }
 };
 
+// Bytes of 4-byte word q that lie in the window [OFF, OFF + N) of a row pass item.
+template <int OFF, int N>
+__device__ __forceinline__ constexpr uint32_t window_mask(int q) {
+    uint32_t m = 0u;
+    for (int k = 0; k < 4; ++k) {
+        const int b = 4 * q + k;
+        if (b >= OFF && b < OFF + N) m |= 0xffu << (8 * k);
+    }
+    return m;
+}
+
 // Tiles a persistent CTA takes from the launch's counter at a time.
 constexpr int kFieldsChunk = 4;
 // Row-pass items start at (tid + kItemRotate) mod kThreads: the threads of warps 0 and 1 take the
@@ -295,9 +306,10 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
     // store their zeros meanwhile), then runs the listed items on consecutive lanes, so that its
     // packed FMAs run on full lanes (a warp whose lanes diverge keeps the FMA pipe busy for its
     // idle lanes too).  An item computes the same products in the same order whichever lane takes
-    // it.  On the ragged binary batch this pays at R = 12 (0.58 against 0.62 ms for that class);
-    // at R = 6 and 9 the second load of the listed items' windows costs more than it saves.
-    constexpr bool COMPACT = DTYPE == ITC_U8 && R >= 12;
+    // it.  Items whose two windows are all ones are not listed either (their outputs are
+    // constants).  On the ragged binary batch this pays at every radius: 0.382 / 0.499 / 0.570 ms
+    // at R = 6 / 9 / 12 against 0.384 / 0.509 / 0.571 ms with the items run in place.
+    constexpr bool COMPACT = DTYPE == ITC_U8;
     constexpr int NITEMS = ROWS * 8;                 // row-pass items of a tile (8 per staged row)
     constexpr int NROUNDS = (NITEMS + kThreads - 1) / kThreads;
     __shared__ short s_items[COMPACT ? kThreads / 32 : 1][COMPACT ? NROUNDS * 32 : 1];   // per warp
@@ -528,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
             for (int k = 0; k < NROUNDS; ++k) {
                 const int item = rot + k * kThreads;
                 const int r0 = (item >> 4) * 2, c = (item & 15) * 4;
-                bool nz0 = false, nz1 = false;
+                bool nz0 = false, nz1 = false, ones = false;
                 if (item < NITEMS && v0 + c < W) {
                     uint32_t w0[NQ4], w1[NQ4];
                     load_item(item, w0, w1);
@@ -545,12 +557,31 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
                     }
                     if (nz0) atomicOr(&colbits[par][c >> 3][r0 >> 5], 1u << (r0 & 31));
                     if (nz1) atomicOr(&colbits[par][c >> 3][(r0 + 1) >> 5], 1u << ((r0 + 1) & 31));
+                    // both windows all ones (shape interiors; centred moments): T and T_v are the
+                    // FMA chains of the taps, prepared on the host
+                    if constexpr (!ABS) {
+                        if (nz0 & nz1) {
+                            uint32_t diff = 0u;
+#pragma unroll
+                            for (int q = 0; q < NQ4; ++q)
+                                diff |= ((w0[q] ^ 0x01010101u) | (w1[q] ^ 0x01010101u)) & window_mask<OFF, NW4>(q);
+                            ones = diff == 0u;
+                        }
+                    }
+                    if (ones) {
+                        float* oT = sT + r0 * TW + c;
+                        float* oV = oT + ROWS * TW;
+                        const float a = tp.ones_gv, b = tp.ones_dgv;
+                        st4(oT, a, a, a, a); st4(oT + TW, a, a, a, a);
+                        st4(oV, b, b, b, b); st4(oV + TW, b, b, b, b);
+                    }
                     if constexpr (!COMPACT)
-                        if (nz0 | nz1) compute_item(item, w0, w1);
+                        if ((nz0 | nz1) && !ones) compute_item(item, w0, w1);
                 }
                 if constexpr (COMPACT) {
-                    const unsigned ba = __ballot_sync(0xffffffffu, nz0 | nz1);
-                    if (nz0 | nz1) wl[cnt + __popc(ba & lanes_below)] = (short)item;
+                    const bool mixed = (nz0 | nz1) && !ones;
+                    const unsigned ba = __ballot_sync(0xffffffffu, mixed);
+                    if (mixed) wl[cnt + __popc(ba & lanes_below)] = (short)item;
                     cnt += __popc(ba);
                 }
             }

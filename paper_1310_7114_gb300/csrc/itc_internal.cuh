@@ -33,6 +33,9 @@ struct Taps {
     float sigma[3];
     float inv2s2[3];   // 1 / (2 sigma_i^2)
     int R[3];
+    // the row pass of a window whose inputs are all 1: the FP32 FMA chains of the v taps in
+    // kernel order, acc = fma(g[d], 1, acc) for d = 0 .. 2R (the same value as the arithmetic)
+    float ones_gv, ones_dgv;
 };
 
 // Deriche's recursive Gaussian for one width: per axis (u, v) and term t the complex pole

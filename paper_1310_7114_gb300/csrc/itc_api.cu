@@ -16,10 +16,8 @@ using namespace itc;
 
 namespace {
 
-constexpr int kGridTileH2 = 64;   // fields tile height, 2-D
 constexpr size_t kFieldsStatusBytes = 256;   // itc_fields scratch: the status word and the tile
                                              // counter of the fields launch
-constexpr int kGridTileH3 = 32;   // fields tile height, 3-D
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.f; }
 
@@ -151,7 +149,7 @@ void fill_desc(const itc_image* img, const itc_params* p, int M, ImageDesc* d) {
         d->tiles_u = 1;
         d->tiles_v = (img->W + 31) / 32;
     }
-    d->tiles_g = img->ndim == 3 ? (d->G + kGSlices - 1) / kGSlices : 1;
+    d->tiles_g = img->ndim == 3 ? d->G : 1;   // 3-D tiles: one gray slice each
     d->plane_floats = (long long)d->G * img->H * d->fpitch;
     d->bwd_tiles_u = (img->H + kBwdTileH - 1) / kBwdTileH;
     d->bwd_tiles_v = (img->W + kBwdTileW - 1) / kBwdTileW;
@@ -300,6 +298,7 @@ cudaError_t launch_fields_any(FieldsLaunch& L, bool tma, int begin, int end, int
     L.tile_base = begin;
     if (end <= begin) return cudaSuccess;
     if (tma && fields_tma_supported(ndim, Ru, Rv)) return launch_fields_tma(L, end, Ru, dtype, s);
+    if (ndim == 3) return launch_fields3d(L, end, Ru, Rv, s);
     return launch_fields(L, end - begin, Ru, Rv, ndim, dtype, s);
 }
 

@@ -1,13 +1,14 @@
-// itc_fields.cu -- truncated separable Gaussian fields of lattice images (Sec. 3.1, Sec. 5;
-// gray images as [u, v, g] lattices, Sec. 1 (ii)).
+// itc_fields.cu -- truncated separable Gaussian fields of 2-D lattice images (Sec. 3.1, Sec. 5)
+// with plain staging (rows that are not on 16-byte boundaries, radii without a compiled TMA
+// kernel); gray images as [u, v, g] lattices are in itc_fields3d.cu.
 //
-// One CTA computes a TH x 64 tile of output sites (times up to kGSlices gray slices in 3-D):
+// One CTA computes a TH x 64 tile of output sites:
 //   1. the input tile plus an R-wide halo is staged in shared memory as float (zero outside the
 //      lattice: sites outside hold no data);
 //   2. pass along v (Sec. 3.1: two 1-D masks): T = g_v * X and T_v = (d g_v) * X (centred) or
-//      g_v * (v X) (absolute), plus T_g = g_v * (S_g) in 3-D, for every staged row;
+//      g_v * (v X) (absolute), for every staged row;
 //   3. pass along u over the staged rows: A = g_u * T, F_u = (d g_u) * T or g_u * (u T),
-//      F_v = g_u * T_v (, F_g = g_u * T_g), written with 128-bit stores;
+//      F_v = g_u * T_v, written with 128-bit stores;
 //   4. epilogue: the tile's share of S_XX = sum_x h(x) A(x) (V(X) of Eq. (1)) as one double.
 // Tiles whose staged input is all zero only write zeros.  For the radii the parameter sets use
 // (6, 9, 12) both passes are fully unrolled with the taps in the constant bank; other radii
@@ -63,13 +64,13 @@ __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d
     *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
 }
 
-template <int RU, int RV, int NDIM, bool ABS, int DTYPE, int TH>
+template <int RU, int RV, bool ABS, int DTYPE, int TH>
 __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_constant__ FieldsLaunch L)
 {
     constexpr int TW = kTileW;
     constexpr int K = TH / 16;                 // output rows per thread in the u pass
-    constexpr int NR = NDIM;                   // row-pass outputs: T, T_v (, T_g)
-    constexpr int NC = NDIM + 1;               // column-pass outputs: A, F_u, F_v (, F_g)
+    constexpr int NR = 2;                      // row-pass outputs: T, T_v
+    constexpr int NC = 3;                      // column-pass outputs: A, F_u, F_v
     const Taps& tp = L.taps;
     const int Ru = RU > 0 ? RU : tp.R[0];
     const int Rv = RV > 0 ? RV : tp.R[1];
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
     } else {
         dp = &L.one;
     }
-    const int H = dp->H, W = dp->W, pitch = dp->pitch, fpitch = dp->fpitch, G = dp->G;
+    const int H = dp->H, W = dp->W, pitch = dp->pitch, fpitch = dp->fpitch;
     // mode 0: every plane of the fields; 1: A only, into the A_s plane (self-overlap pass);
     // 2: the S_XX partials only
     const int mode = L.mode;
@@ -94,17 +95,13 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
     const int tiles_v = dp->tiles_v, tiles_u = mode ? dp->self_tiles_u : dp->tiles_u;
     const int tv = b % tiles_v;
     const int tu = (b / tiles_v) % tiles_u;
-    const int tg = b / (tiles_v * tiles_u);
     const int u0 = tu * TH, v0 = tv * TW;
     float* const fbase = L.fields + (mode == 1 ? dp->self_off : dp->field_off);
     const long long plane = dp->plane_floats;
 
     extern __shared__ __align__(16) float smem[];
-    float* s_in = smem;                                 // ROWS x SW: input (2-D) / S (3-D)
-    float* s_aux = s_in + ROWS * SW;                    // 3-D: S_g channel
-    float* s_gray = s_aux + (NDIM == 3 ? ROWS * SW : 0);  // 3-D: gray level (float)
-    float* s_w = s_gray + (NDIM == 3 ? ROWS * SW : 0);    // 3-D: pixel weight (0 outside)
-    float* sT = s_w + (NDIM == 3 ? ROWS * SW : 0);      // NR planes of ROWS x TW
+    float* s_in = smem;                                 // ROWS x SW: input
+    float* sT = s_in + ROWS * SW;                       // NR planes of ROWS x TW
     __shared__ double red[32];
     const int tid = threadIdx.x;
 
@@ -118,25 +115,15 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
             for (int c = lane; c < SW; c += 32) {
                 const int gv = v0 - Rv + c;
                 const bool in = row_in && gv >= 0 && gv < W && c < TW + 2 * Rv;
-                if (NDIM == 2) {
-                    float x = 0.f;
-                    if (in) {
-                        if (DTYPE == ITC_U8)
-                            x = (float)__ldg(reinterpret_cast<const unsigned char*>(dp->data) + (size_t)gu * pitch + gv);
-                        else
-                            x = __ldg(reinterpret_cast<const float*>(dp->data) + (size_t)gu * pitch + gv);
-                    }
-                    nonzero |= (x != 0.f);
-                    s_in[r * SW + c] = x;
-                } else {
-                    float gl = -1e6f, wt = 0.f;
-                    if (in) {
-                        gl = (float)__ldg(reinterpret_cast<const unsigned char*>(dp->data) + (size_t)gu * pitch + gv);
-                        wt = dp->weight ? __ldg(dp->weight + (size_t)gu * pitch + gv) : 1.f;
-                    }
-                    s_gray[r * SW + c] = gl;
-                    s_w[r * SW + c] = wt;
+                float x = 0.f;
+                if (in) {
+                    if (DTYPE == ITC_U8)
+                        x = (float)__ldg(reinterpret_cast<const unsigned char*>(dp->data) + (size_t)gu * pitch + gv);
+                    else
+                        x = __ldg(reinterpret_cast<const float*>(dp->data) + (size_t)gu * pitch + gv);
                 }
+                nonzero |= (x != 0.f);
+                s_in[r * SW + c] = x;
             }
         }
     }
@@ -146,43 +133,21 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
     const int k0 = kb * K, c0 = cg * 4;
     const bool col_active = (u0 + k0 < H) && (v0 + c0 < W);
 
-    const int nslices = (NDIM == 3) ? min(kGSlices, G - tg * kGSlices) : 1;
     float part = 0.f;
 
-    for (int sl = 0; sl < nslices; ++sl) {
-        const int yg = tg * kGSlices + sl;
-        long long slice_off = 0;
-        if (NDIM == 3) {
-            slice_off = (long long)yg * H * fpitch;
-            __syncthreads();   // previous slice's passes are done with s_in / s_aux
-            const int Rg = tp.R[2];
-            nonzero = 0;
-            for (int i = tid; i < ROWS * SW; i += kThreads) {
-                const float gl = s_gray[i];
-                const float dgl = gl - (float)yg;
-                float s = 0.f;
-                if (fabsf(dgl) <= (float)Rg) s = s_w[i] * tp.gg[(int)dgl + Rg];
-                s_in[i] = s;
-                s_aux[i] = ABS ? s * gl : s * dgl;
-                nonzero |= (s != 0.f);
+    if (!__syncthreads_or(nonzero)) {
+        if (col_active) {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int u = u0 + k0 + kk;
+                if (u >= H) break;
+                float* o = fbase + (long long)u * fpitch + v0 + c0;
+#pragma unroll
+                for (int f = 0; f < NC; ++f)
+                    if (f < nstore) st4(o + f * plane, 0.f, 0.f, 0.f, 0.f);
             }
         }
-        const int any = __syncthreads_or(nonzero);
-        if (!any) {
-            if (col_active) {
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    const int u = u0 + k0 + kk;
-                    if (u >= H) break;
-                    float* o = fbase + slice_off + (long long)u * fpitch + v0 + c0;
-#pragma unroll
-                    for (int f = 0; f < NC; ++f)
-                        if (f < nstore) st4(o + f * plane, 0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            continue;
-        }
-
+    } else {
         // ---- pass along v
         for (int item = tid; item < ROWS * 16; item += kThreads) {
             const int r = item >> 4, c = (item & 15) * 4;
@@ -200,7 +165,6 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
 #pragma unroll
                 for (int j = 0; j < 4; ++j) t[f][j] = 0.f;
             const float* src = s_in + r * SW + c;
-            const float* srca = s_aux + r * SW + c;
             const float vbase = (float)(v0 - Rv + c);
             if constexpr (RV > 0) {
                 constexpr int NWIN = ((4 + 2 * RV) + 3) & ~3;
@@ -209,14 +173,6 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
                 for (int q = 0; q < NWIN / 4; ++q) {
                     const float4 f4 = ld4(src + 4 * q);
                     x[4 * q] = f4.x; x[4 * q + 1] = f4.y; x[4 * q + 2] = f4.z; x[4 * q + 3] = f4.w;
-                }
-                float xa[NDIM == 3 ? NWIN : 1];
-                if constexpr (NDIM == 3) {
-#pragma unroll
-                    for (int q = 0; q < NWIN / 4; ++q) {
-                        const float4 f4 = ld4(srca + 4 * q);
-                        xa[4 * q] = f4.x; xa[4 * q + 1] = f4.y; xa[4 * q + 2] = f4.z; xa[4 * q + 3] = f4.w;
-                    }
                 }
                 float xv[ABS ? NWIN : 1];
                 if constexpr (ABS) {
@@ -231,7 +187,6 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
                         t[0][j] = fmaf(g, x[j + d], t[0][j]);
                         if constexpr (ABS) t[1][j] = fmaf(g, xv[j + d], t[1][j]);
                         else t[1][j] = fmaf(tp.dgv[d], x[j + d], t[1][j]);
-                        if constexpr (NDIM == 3) t[2][j] = fmaf(g, xa[j + d], t[2][j]);
                     }
                 }
             } else {
@@ -243,7 +198,6 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
                         t[0][j] = fmaf(g, x, t[0][j]);
                         if (ABS) t[1][j] = fmaf(g, x * (vbase + (float)(j + d)), t[1][j]);
                         else t[1][j] = fmaf(dg, x, t[1][j]);
-                        if (NDIM == 3) t[NR - 1][j] = fmaf(g, srca[j + d], t[NR - 1][j]);
                     }
                 }
             }
@@ -290,7 +244,6 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
                                 if constexpr (ABS) acc[1][kk][j] = fmaf(g, tu[j], acc[1][kk][j]);
                                 else acc[1][kk][j] = fmaf(tp.dgu[e], t[0][j], acc[1][kk][j]);
                                 acc[2][kk][j] = fmaf(g, t[1][j], acc[2][kk][j]);
-                                if constexpr (NDIM == 3) acc[3][kk][j] = fmaf(g, t[2][j], acc[3][kk][j]);
                             }
                         }
                     }
@@ -315,7 +268,6 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
                                 if (ABS) acc[1][kk][j] = fmaf(g, t[0][j] * (ubase + (float)i), acc[1][kk][j]);
                                 else acc[1][kk][j] = fmaf(dg, t[0][j], acc[1][kk][j]);
                                 acc[2][kk][j] = fmaf(g, t[1][j], acc[2][kk][j]);
-                                if (NDIM == 3) acc[NC - 1][kk][j] = fmaf(g, t[NR - 1][j], acc[NC - 1][kk][j]);
                             }
                         }
                     }
@@ -326,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
             for (int kk = 0; kk < K; ++kk) {
                 const int u = u0 + k0 + kk;
                 if (u < H) {
-                    float* o = fbase + slice_off + (long long)u * fpitch + v0 + c0;
+                    float* o = fbase + (long long)u * fpitch + v0 + c0;
 #pragma unroll
                     for (int f = 0; f < NC; ++f)
                         if (f < nstore) st4(o + f * plane, acc[f][kk][0], acc[f][kk][1], acc[f][kk][2], acc[f][kk][3]);
@@ -334,17 +286,13 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         if (v0 + c0 + j < W) {
-                            float hx;
-                            if (NDIM == 2) hx = s_in[si + j];
-                            else hx = (s_gray[si + j] == (float)yg) ? s_w[si + j] : 0.f;
-                            ps = fmaf(hx, acc[0][kk][j], ps);
+                            ps = fmaf(s_in[si + j], acc[0][kk][j], ps);
                         }
                     }
                 }
             }
             part += ps;
         }
-        __syncthreads();   // sT / s_in reuse by the next slice
     }
 
     const double tot = block_sum_tile(part, red);
@@ -352,27 +300,26 @@ __global__ void __launch_bounds__(kThreads, 2) fields_kernel(const __grid_consta
     if (tid == 0) L.partials[(mode ? dp->sxx_off : dp->partial_off) + b] = tot;
 }
 
-template <int RU, int RV, int NDIM, bool ABS, int DTYPE, int TH>
+template <int RU, int RV, bool ABS, int DTYPE, int TH>
 cudaError_t launch_one(const FieldsLaunch& L, int nblocks, int Ru, int Rv, cudaStream_t s) {
     const int rows = TH + 2 * Ru;
     const int SW = ((kTileW + 2 * Rv + 3) & ~3) + 4;
-    size_t smem = (size_t)rows * SW * sizeof(float) * (NDIM == 3 ? 4 : 1) +
-                  (size_t)NDIM * rows * kTileW * sizeof(float);
-    auto k = fields_kernel<RU, RV, NDIM, ABS, DTYPE, TH>;
+    const size_t smem = (size_t)rows * SW * sizeof(float) + (size_t)2 * rows * kTileW * sizeof(float);
+    auto k = fields_kernel<RU, RV, ABS, DTYPE, TH>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<nblocks, kThreads, smem, s>>>(L);
     return cudaGetLastError();
 }
 
-template <int NDIM, bool ABS, int DTYPE, int TH>
+template <bool ABS, int DTYPE, int TH>
 cudaError_t dispatch_radius(const FieldsLaunch& L, int nblocks, int Ru, int Rv, cudaStream_t s) {
     if (Ru == Rv) {
-        if (Ru == 6) return launch_one<6, 6, NDIM, ABS, DTYPE, TH>(L, nblocks, Ru, Rv, s);
-        if (Ru == 9) return launch_one<9, 9, NDIM, ABS, DTYPE, TH>(L, nblocks, Ru, Rv, s);
-        if (Ru == 12) return launch_one<12, 12, NDIM, ABS, DTYPE, TH>(L, nblocks, Ru, Rv, s);
+        if (Ru == 6) return launch_one<6, 6, ABS, DTYPE, TH>(L, nblocks, Ru, Rv, s);
+        if (Ru == 9) return launch_one<9, 9, ABS, DTYPE, TH>(L, nblocks, Ru, Rv, s);
+        if (Ru == 12) return launch_one<12, 12, ABS, DTYPE, TH>(L, nblocks, Ru, Rv, s);
     }
-    return launch_one<0, 0, NDIM, ABS, DTYPE, TH>(L, nblocks, Ru, Rv, s);
+    return launch_one<0, 0, ABS, DTYPE, TH>(L, nblocks, Ru, Rv, s);
 }
 
 __global__ void reduce_sxx_kernel(const double* __restrict__ partials, int n, double* out) {
@@ -389,15 +336,12 @@ cudaError_t launch_fields(const FieldsLaunch& L, int nblocks, int Ru, int Rv, in
                           cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
     const bool abs_ = L.absolute != 0;
-    if (ndim == 2) {
-        if (dtype == ITC_U8)
-            return abs_ ? dispatch_radius<2, true, ITC_U8, 64>(L, nblocks, Ru, Rv, s)
-                        : dispatch_radius<2, false, ITC_U8, 64>(L, nblocks, Ru, Rv, s);
-        return abs_ ? dispatch_radius<2, true, ITC_F32, 64>(L, nblocks, Ru, Rv, s)
-                    : dispatch_radius<2, false, ITC_F32, 64>(L, nblocks, Ru, Rv, s);
-    }
-    return abs_ ? dispatch_radius<3, true, ITC_U8, 32>(L, nblocks, Ru, Rv, s)
-                : dispatch_radius<3, false, ITC_U8, 32>(L, nblocks, Ru, Rv, s);
+    if (ndim == 3) return launch_fields3d(L, L.tile_base + nblocks, Ru, Rv, s);
+    if (dtype == ITC_U8)
+        return abs_ ? dispatch_radius<true, ITC_U8, kGridTileH2>(L, nblocks, Ru, Rv, s)
+                    : dispatch_radius<false, ITC_U8, kGridTileH2>(L, nblocks, Ru, Rv, s);
+    return abs_ ? dispatch_radius<true, ITC_F32, kGridTileH2>(L, nblocks, Ru, Rv, s)
+                : dispatch_radius<false, ITC_F32, kGridTileH2>(L, nblocks, Ru, Rv, s);
 }
 
 cudaError_t launch_reduce_sxx(const double* partials, int n, double* out, cudaStream_t s) {

@@ -2,10 +2,14 @@
 //
 // Same arithmetic as fields_kernel in itc_fields.cu (the results are bit for bit the same: every
 // output accumulates the same products in the same order), reorganised for throughput:
-//   * persistent CTAs each walk a contiguous run of the tile list, image lookups loaded ahead;
+//   * persistent CTAs take chunks of consecutive tiles from a per-launch counter, image lookups
+//     loaded ahead;
 //   * the input tile plus its halo arrives by one cp.async.bulk.tensor (TMA) per tile into one
-//     of three staging buffers (two for 4-byte inputs), so copies run ahead of the tile being
-//     computed;
+//     of three staging buffers (two for 4-byte inputs and for 64-row byte tiles at R = 12), so
+//     copies run ahead of the tile being computed;
+//   * byte inputs skip the arithmetic of windows without data, store precomputed chains for
+//     windows of ones, take windows that are one run of 0/1 inputs from a table of chains, and
+//     run the rest of the row pass warp-compacted;
 //   * the row pass reads its input windows straight from the staged box (bytes are turned into
 //     floats in registers), so a tile needs two barriers and no float copy of its input, and three
 //     CTAs fit on an SM for byte inputs;
@@ -14,7 +18,8 @@
 //     realigned), the row pass of float inputs and the column pass over pairs of neighbouring
 //     columns.
 // Used for 2-D images whose rows start on 16-byte boundaries (the tensor map needs it) and for
-// the compiled radii 6, 9 and 12; everything else goes through fields_kernel.
+// the compiled radii 6, 9 and 12; other 2-D images go through fields_kernel, gray images through
+// fields3d_kernel (itc_fields3d.cu).
 #include <cuda.h>
 
 #include "itc_internal.cuh"
@@ -167,7 +172,7 @@ __device__ __forceinline__ bool wait_stage(uint64_t* bar, uint32_t parity) {
 }
 
 // Compile-time shape of one tile (rows TH + 2R of the staged box, stages in flight).
-template <int R, int DTYPE, int TH>
+template <int R, bool ABS, int DTYPE, int TH>
 struct TmaTile {
     static constexpr int TW = kTileW, K = TH / 16;
     static constexpr int ROWS = TH + 2 * R;
@@ -176,15 +181,21 @@ struct TmaTile {
     static constexpr int BW = TW + 2 * RA;                              // box width in elements
     static constexpr int BOX_BYTES = BW * ROWS * ES;
     static constexpr int STAGE_BYTES = (BOX_BYTES + 127) & ~127;
-    static constexpr int NST = STAGE_BYTES <= 12288 ? 3 : 2;           // staging buffers
-    static constexpr size_t SMEM = 128 + (size_t)NST * STAGE_BYTES + 2 * (size_t)ROWS * TW * 4;
+    static constexpr int NST = STAGE_BYTES <= 8192 ? 3 : 2;            // staging buffers
+    // byte inputs with centred moments and R >= 9 take row windows that are one run of 0/1 inputs
+    // from a table (below); it does not fit beside 128-row tiles at R = 12
+    static constexpr bool RUNS = DTYPE == ITC_U8 && !ABS && R >= 9 && !(TH == 128 && R == 12);
+    static constexpr int NTAP = 2 * R + 1;
+    static constexpr int T2 = (NTAP + 1) * (NTAP + 2) / 2;             // runs [a, b), 0 <= a <= b <= NTAP
+    static constexpr size_t TAB_BYTES = RUNS ? 2 * (size_t)T2 * 8 : 0;
+    static constexpr size_t SMEM = 128 + (size_t)NST * STAGE_BYTES + 2 * (size_t)ROWS * TW * 4 + TAB_BYTES;
     static constexpr int MIN_CTAS = (DTYPE == ITC_U8 && TH == 64) ? 3 : 2;
 };
 
 template <int R, bool ABS, int DTYPE, int TH>
-__global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
+__global__ void __launch_bounds__(kThreads, (TmaTile<R, ABS, DTYPE, TH>::MIN_CTAS))
     fields_tma_kernel(const __grid_constant__ FieldsLaunch L, int ntiles) {
-    using TT = TmaTile<R, DTYPE, TH>;
+    using TT = TmaTile<R, ABS, DTYPE, TH>;
     constexpr int TW = TT::TW, K = TT::K, ROWS = TT::ROWS, RA = TT::RA, BW = TT::BW;
     constexpr int BOX_BYTES = TT::BOX_BYTES, STAGE_BYTES = TT::STAGE_BYTES, NST = TT::NST;
     constexpr int OFF = (RA - R) & 3;                // a window's first input within its 4-group
@@ -195,6 +206,9 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
     // the TMA destination must be 128-byte aligned: round the base up (128 spare bytes reserved)
     unsigned char* stage0 = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // NST stages
     float* sT = reinterpret_cast<float*>(stage0 + NST * STAGE_BYTES);   // T then T_v: ROWS x TW each
+    // (T, T_v) of every window of 0/1 inputs that is one run: ones on [a, b) at entry
+    // b (b + 1) / 2 + a, ones outside [a, b) at T2 + that entry
+    float2* s_run = reinterpret_cast<float2*>(sT + 2 * ROWS * TW);
     __shared__ __align__(8) uint64_t bar[NST];
     __shared__ double red[32];
     __shared__ int s_abort;
@@ -212,6 +226,25 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
         s_abort = 0;
     }
     for (int i = tid; i < 2 * (TW / 8) * CBW; i += kThreads) (&colbits[0][0][0])[i] = 0u;
+    if constexpr (TT::RUNS) {
+        // each entry is the row pass's own FMA chain over the taps with inputs 1 on the run and 0
+        // elsewhere, so a window that is such a run gets the bits the FMAs would give
+        for (int e = tid; e < 2 * TT::T2; e += kThreads) {
+            const bool outside = e >= TT::T2;
+            const int t = outside ? e - TT::T2 : e;
+            int b = 0;
+            while ((b + 1) * (b + 2) / 2 <= t) ++b;
+            const int a = t - b * (b + 1) / 2;
+            float accT = 0.f, accV = 0.f;
+#pragma unroll
+            for (int d = 0; d < TT::NTAP; ++d) {
+                const float x = ((d >= a && d < b) != outside) ? 1.f : 0.f;
+                accT = fmaf(tp.gv[d], x, accT);
+                accV = fmaf(tp.dgv[d], x, accV);
+            }
+            s_run[e] = make_float2(accT, accV);
+        }
+    }
     __syncthreads();
 
     // Tiles are handed out dynamically, kFieldsChunk consecutive tiles at a time, from the launch's
@@ -308,7 +341,10 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
     // idle lanes too).  An item computes the same products in the same order whichever lane takes
     // it.  Items whose two windows are all ones are not listed either (their outputs are
     // constants).  On the ragged binary batch this pays at every radius: 0.382 / 0.499 / 0.570 ms
-    // at R = 6 / 9 / 12 against 0.384 / 0.509 / 0.571 ms with the items run in place.
+    // at R = 6 / 9 / 12 against 0.384 / 0.509 / 0.571 ms with the items run in place.  A listed
+    // item of 0/1 inputs whose row windows are one run each (98-99 % of them on that batch) takes
+    // its outputs from the run table instead of the FMAs (R >= 9: 0.497 / 0.541 ms at R = 9 / 12
+    // with two stages at R = 12; at R = 6 the FMAs cost no more than the table's index arithmetic).
     constexpr bool COMPACT = DTYPE == ITC_U8;
     constexpr int NITEMS = ROWS * 8;                 // row-pass items of a tile (8 per staged row)
     constexpr int NROUNDS = (NITEMS + kThreads - 1) / kThreads;
@@ -531,6 +567,56 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
                 st4(oT, aT[0].x, aT[1].x, aT[2].x, aT[3].x); st4(oT + TW, aT[0].y, aT[1].y, aT[2].y, aT[3].y);
                 st4(oV, aV[0].x, aV[1].x, aV[2].x, aV[3].x); st4(oV + TW, aV[0].y, aV[1].y, aV[2].y, aV[3].y);
             };
+            // one item from the run table when both of its row windows (4 + 2R inputs) hold only 0
+            // and 1 with at most two changes along the row, i.e. one run of ones or one run of
+            // zeros; each output's window then holds that run clipped to its 2R + 1 taps.  False
+            // (nothing stored) for any other item.  Binary shapes give such windows almost always.
+            auto run_item = [&](int item, const uint32_t (&w0)[NQ4], const uint32_t (&w1)[NQ4]) -> bool {
+                if constexpr (!TT::RUNS) {
+                    return false;
+                } else {
+                    constexpr int N = TT::NTAP;
+                    constexpr uint32_t FULL = (1u << NW4) - 1u;     // NW4 <= 28
+                    constexpr uint32_t EDGES = (1u << (NW4 - 1)) - 1u;
+                    uint32_t high = 0u, m0 = 0u, m1 = 0u;
+#pragma unroll
+                    for (int q = 0; q < NQ4; ++q) {
+                        high |= (w0[q] | w1[q]) & (0xfefefefeu & window_mask<OFF, NW4>(q));
+                        // the low bits of the 4 bytes gathered into 4 bits (no carries: the 16
+                        // partial products land on distinct bits)
+                        m0 |= (((w0[q] & 0x01010101u) * 0x01020408u) >> 24) << (4 * q);
+                        m1 |= (((w1[q] & 0x01010101u) * 0x01020408u) >> 24) << (4 * q);
+                    }
+                    m0 = (m0 >> OFF) & FULL;   // bit i: input at column c - R + i
+                    m1 = (m1 >> OFF) & FULL;
+                    if (high != 0u || __popc((m0 ^ (m0 >> 1)) & EDGES) > 2 || __popc((m1 ^ (m1 >> 1)) & EDGES) > 2)
+                        return false;
+                    const int r0 = (item >> 4) * 2, c = (item & 15) * 4;
+                    float tv[2][2][4];   // [T or T_v][row][output]
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t m = h ? m1 : m0;
+                        const bool zeros = (m & 1u) != 0u;            // starts with a one: a run of zeros
+                        const uint32_t run = zeros ? (~m & FULL) : m;
+                        const int a = run ? __ffs((int)run) - 1 : 0, b = a + __popc(run);
+                        const int base = zeros ? TT::T2 : 0;
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int aa = min(max(a - jj, 0), N), bb = min(max(b - jj, 0), N);
+                            const float2 e = s_run[base + (bb * (bb + 1) >> 1) + aa];
+                            tv[0][h][jj] = e.x;
+                            tv[1][h][jj] = e.y;
+                        }
+                    }
+                    float* oT = sT + r0 * TW + c;
+                    float* oV = oT + ROWS * TW;
+                    st4(oT, tv[0][0][0], tv[0][0][1], tv[0][0][2], tv[0][0][3]);
+                    st4(oT + TW, tv[0][1][0], tv[0][1][1], tv[0][1][2], tv[0][1][3]);
+                    st4(oV, tv[1][0][0], tv[1][0][1], tv[1][0][2], tv[1][0][3]);
+                    st4(oV + TW, tv[1][1][0], tv[1][1][1], tv[1][1][2], tv[1][1][3]);
+                    return true;
+                }
+            };
             // every item of this thread: windows without data store zeros; with COMPACT the items
             // with data are listed per warp and run afterwards on consecutive lanes, otherwise
             // they run in place
@@ -591,7 +677,7 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
                     const int item = wl[j];
                     uint32_t w0[NQ4], w1[NQ4];
                     load_item(item, w0, w1);
-                    compute_item(item, w0, w1);
+                    if (!run_item(item, w0, w1)) compute_item(item, w0, w1);
                 }
             }
         } else {
@@ -670,7 +756,7 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, DTYPE, TH>::MIN_CTAS))
 
 template <int R, bool ABS, int DTYPE, int TH>
 cudaError_t launch_tma(const FieldsLaunch& L, int ntiles, cudaStream_t s) {
-    const size_t smem = TmaTile<R, DTYPE, TH>::SMEM;
+    const size_t smem = TmaTile<R, ABS, DTYPE, TH>::SMEM;
     auto k = fields_tma_kernel<R, ABS, DTYPE, TH>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -227,7 +227,8 @@ struct SegmentLaunch {
 
 constexpr int kBwdTileH = 64;   // backward pixel tile: 64 rows x 64 columns
 constexpr int kBwdTileW = 64;
-constexpr int kGSlices = 8;     // 3-D fields: gray slices per CTA
+constexpr int kGridTileH2 = 64;   // fields tile height, 2-D (plain staging)
+constexpr int kGridTileH3 = 32;   // fields tile height, 3-D (one gray slice per tile)
 
 }  // namespace itc
 
@@ -236,6 +237,8 @@ namespace itc {
 cudaError_t launch_fields(const FieldsLaunch& L, int nblocks, int R_u, int R_v, int ndim, int dtype,
                           cudaStream_t s);
 cudaError_t launch_reduce_sxx(const double* partials, int n, double* out, cudaStream_t s);
+// 3-D fields (itc_fields3d.cu): tiles [L.tile_base, ntiles) of the launch's images
+cudaError_t launch_fields3d(const FieldsLaunch& L, int ntiles, int R_u, int R_v, cudaStream_t s);
 // TMA-staged 2-D fields (itc_fields_tma.cu): the radii it is compiled for, its box per radius
 // and data type, and its launch.
 bool fields_tma_supported(int ndim, int Ru, int Rv);

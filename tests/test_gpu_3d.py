@@ -128,3 +128,46 @@ def test_backward3d_matches_oracle():
     assert np.linalg.norm(g1 - gref) <= 1e-4 * np.linalg.norm(gref)
     g2 = gh.cpu().numpy()
     assert np.linalg.norm(g2 - ghref) <= 1e-4 * np.linalg.norm(ghref)
+
+
+def test_fields3d_plan_of_several_images():
+    """The fields launch of a 3-D plan gives each persistent CTA a run of slice tiles that crosses
+    image boundaries (and windows, which it stages anew).  Every image's fields equal its own
+    single-image call bit for bit (the same products in the same order) and match the oracle;
+    its S_XX (one partial per slice tile) matches the oracle's."""
+    import torch
+    specs = [(37, 70, 48, False), (64, 33, 20, True), (20, 100, 64, False), (45, 45, 31, True), (9, 7, 5, False)]
+    sigma = (3.0, 3.0, 8.0)
+    grays, hws = [], []
+    for i, (H, W, G, weighted) in enumerate(specs):
+        grays.append(_smooth_gray(20 + i, H, W, G))
+        hws.append(np.random.default_rng(30 + i).random((H, W)) if weighted else None)
+    bufs, views = itc.pack_images(grays, "cuda")   # rows on 16-byte boundaries
+    wts = []
+    for v, h in zip(views, hws):   # weights share the image's row pitch
+        if h is None:
+            wts.append(None)
+            continue
+        wp = torch.zeros((v.shape[0], v.stride(0)), dtype=torch.float32, device="cuda")
+        wp[:, :v.shape[1]] = torch.from_numpy(h.astype(np.float32)).cuda()
+        wts.append(wp[:, :v.shape[1]])
+    plan = itc.Plan(views, [4] * len(specs), itc.make_params(sigma, 3.0, 0), ndims=[3] * len(specs),
+                    Gs=[s[2] for s in specs], weights=wts)
+    W0 = [synth.init_codebook_gray(synth.rng_for(5, 40 + i), g, 4) for i, g in enumerate(grays)]
+    W = plan.pack_W(W0)
+    st = itc.new_stats(len(specs), "cuda")
+    itc.run(plan, W, st)
+    torch.cuda.synchronize()
+    stats = itc.stats_to_numpy(st)
+    for b, (H, W_, G, _) in enumerate(specs):
+        mine = plan.fields_of(b)[..., :W_].cpu().numpy()
+        single, _ = itc.fields(views[b], sigma, 3.0, ndim=3, G=G, weight=wts[b])
+        torch.cuda.synchronize()
+        assert np.array_equal(mine, single[..., :W_].cpu().numpy()), f"image {b}: plan vs single call"
+        ref = oracle.fields3d(grays[b], G, sigma, hw=hws[b])
+        assert_fields_close(list(mine.astype(np.float64)), ref, radii(sigma, 3.0, 3), False, f"plan image {b}")
+        occ = np.zeros((G, H, W_))
+        uu, vv = np.meshgrid(np.arange(H), np.arange(W_), indexing="ij")
+        occ[grays[b], uu, vv] = 1.0 if hws[b] is None else hws[b]
+        ref_sxx = float((occ * ref[0]).sum())
+        assert abs(stats["sxx"][b] - ref_sxx) <= 1e-5 * ref_sxx, f"image {b}: S_XX"

@@ -118,12 +118,15 @@ def test_fields_are_deterministic():
 @pytest.mark.parametrize("sigma", [2.0, 3.0, 4.0])
 @pytest.mark.parametrize("dtype", ["u8", "f32"])
 @pytest.mark.parametrize("absolute", [False, True])
-@pytest.mark.parametrize("pattern", ["sparse", "solid"])
+@pytest.mark.parametrize("pattern", ["sparse", "solid", "levels"])
 def test_tma_tiles_equal_plain_tiles_bit_for_bit(sigma, dtype, absolute, pattern):
     """Rows on 16-byte boundaries take the TMA-staged tiles; an odd row pitch takes the plain
     staging.  Both accumulate the same products in the same order, so they agree exactly.
     "solid" adds a disc and a band of ones touching the border: long runs of all-ones windows,
-    tiles with no zero row, and ones against the image edges."""
+    tiles with no zero row, and ones against the image edges; its row windows are mostly single
+    runs of 0/1 inputs, which the TMA tiles take from their run table at R >= 9 (entries made by
+    the same FMA chains).  "levels" puts inputs 2 and 255 into runs of the solid shapes: windows
+    that are runs of nonzero inputs but not of ones, which must take the FMAs."""
     import torch
     rng = np.random.default_rng(int(sigma * 10) + (dtype == "f32"))
     h = (rng.random((197, 203)) < 0.2)
@@ -133,6 +136,12 @@ def test_tma_tiles_equal_plain_tiles_bit_for_bit(sigma, dtype, absolute, pattern
         uu, vv = np.mgrid[0:197, 0:203]
         one = ((uu - 90) ** 2 + (vv - 110) ** 2 < 70 ** 2) | (vv >= 180) | (uu < 20)
         h = np.where(one, 1, h)
+    if pattern == "levels":
+        uu, vv = np.mgrid[0:197, 0:203]
+        one = ((uu - 90) ** 2 + (vv - 110) ** 2 < 70 ** 2) | (vv >= 180)
+        h = np.where(one, 1, h).astype(np.float32)
+        h[100:104, 60:150] = 2          # a band of 2 inside the disc
+        h[30:150:7, 185:200] = 255      # rows of 255 inside the right band
     h = h.astype(np.uint8) if dtype == "u8" else h.astype(np.float32)
     buf_a, (ta,) = itc.pack_images([h], "cuda", align=16)      # pitch multiple of 16 elements
     buf_b, (tb,) = itc.pack_images([h], "cuda", align=1)       # pitch 203: no tensor map

@@ -198,7 +198,7 @@ int itc_fields(const itc_image* img, const itc_params* p, float* fields, double*
  *   call's partial sums; each call sets its status word to ITC_OK first and overwrites every
  *   partial it reads, so nothing else is cleared.
  * Errors: ITC_ERR_UNSUPPORTED if the image needs more than ITC_NOALLOC_MAX_TILES tiles (2-D:
- * ceil(H/64) ceil(W/64); 3-D: ceil(H/32) ceil(W/64) ceil(G/8)); otherwise as itc_fields.
+ * ceil(H/64) ceil(W/64); 3-D: ceil(H/32) ceil(W/64) G, one tile per gray slice); otherwise as itc_fields.
  */
 #define ITC_NOALLOC_MAX_TILES 65536
 int itc_fields_noalloc(const itc_image* img, const itc_params* p, float* fields, double* sxx,

@@ -62,18 +62,28 @@ __global__ void __launch_bounds__(kRunThreads) bwd_codebook_kernel(const __grid_
     float* sE = ss + M;
     __shared__ double red[4];
 
-    if (tid < 32) {
-        const long long nt = D.sxx_tiles;
-        double v = 0;
-        for (long long i = tid; i < nt; i += 32) v += L.partials[D.sxx_off + i];
-        v = warp_sum_d(v);
-        if (tid == 0) red[3] = v;
+    // S_XX from the image's tile partials: warp 0 alone, or for a gray image (a partial per
+    // slice tile) every warp a strided share with eight loads in flight per lane, the warp sums
+    // added in warp order
+    __shared__ double s_px[32];
+    const int nws = nd == 3 ? nw : 1;
+    if (wid < nws) {
+        const long long nt = D.sxx_tiles, step = 32LL * nws;
+        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        long long i = tid;
+        for (; i + 7 * step < nt; i += 8 * step)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] += L.partials[D.sxx_off + i + q * step];
+        for (; i < nt; i += step) v[0] += L.partials[D.sxx_off + i];
+        const double t = warp_sum_d(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+        if (lane == 0) s_px[wid] = t;
     }
     const float* Wk = L.W + D.w_off;
     for (int k = tid; k < M; k += blockDim.x)
         for (int i = 0; i < 3; ++i) sw[k * 3 + i] = i < nd ? Wk[k * nd + i] : 0.f;
     __syncthreads();
-    const double sxx = red[3];
+    double sxx = 0;
+    for (int q = 0; q < nws; ++q) sxx += s_px[q];
     const float c0 = D.inv2s2[0], c1 = D.inv2s2[1], c2 = D.inv2s2[2];
     const int Ru = D.R[0], Rv = D.R[1], Rg = D.R[2];
 

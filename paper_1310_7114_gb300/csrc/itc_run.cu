@@ -162,19 +162,41 @@ __global__ void __launch_bounds__(kRunThreads, ND == 3 ? 6 : 7) run_kernel(const
     __shared__ float red[3 * (kRunThreads / 32)];
     __shared__ int mvred[kRunThreads / 32];
     __shared__ double s_sxx[kGroupMax];
+    __shared__ double s_part[kRunThreads / 32];   // S_XX partial sums of the warps
     __shared__ float s_kap[kGroupMax][3];   // tau_i^2 / rho_i^2 of each image of the group
 
     if (L.sxx_single) {
         if (tid == 0) s_sxx[0] = *L.sxx_single;
     } else {
-        // S_XX of each image from its tile partials, one warp per image
-        for (int g = wid; g < n; g += kRunThreads / 32) {
+        // S_XX of each image from its tile partials, one warp per image; gray images (a partial
+        // per slice tile) split the warps evenly over the group's images, eight loads in flight
+        // per lane; a fixed order throughout
+        constexpr int NW = kRunThreads / 32;
+        const int wpi = (ND == 3 && n < NW) ? NW / n : 1;   // warps per image
+        const int lane = tid & 31;
+        for (int g = wid / wpi; g < n; g += NW / wpi) {
             const ImageDesc& ds = grp ? L.descs[__ldg(grp + 2 + g)] : Dg;
-            const long long nt = ds.sxx_tiles, po = ds.sxx_off;
-            double v = 0;
-            for (long long i = tid & 31; i < nt; i += 32) v += L.partials[po + i];
-            v = warp_sum_d(v);
-            if ((tid & 31) == 0) s_sxx[g] = v;
+            const long long nt = ds.sxx_tiles, po = ds.sxx_off, step = 32LL * wpi;
+            double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            long long i = (long long)(wid % wpi) * 32 + lane;
+            for (; i + 7 * step < nt; i += 8 * step)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] += L.partials[po + i + q * step];
+            for (; i < nt; i += step) v[0] += L.partials[po + i];
+            double t = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+            t = warp_sum_d(t);
+            if (lane == 0) {
+                if (wpi == 1) s_sxx[g] = t;
+                else s_part[wid] = t;
+            }
+        }
+        if (wpi > 1) {
+            __syncthreads();
+            if (tid < n) {
+                double t = 0;
+                for (int q = 0; q < wpi; ++q) t += s_part[tid * wpi + q];
+                s_sxx[tid] = t;
+            }
         }
     }
     if (has && kl == 0)

@@ -494,8 +494,6 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, ABS, DTYPE, TH>::MIN_CTA
             return;
         }
         phase ^= 1u << buf;
-        // the stage of the previous tile is free: start the copy NST - 1 tiles ahead into it
-        if (tid < 32 && n > 0) issue((n - 1) % NST, true);
         ++n;
         const int par = n & 1;
         if (tid < (TW / 8) * CBW) (&colbits[par ^ 1][0][0])[tid] = 0u;   // for the next tile
@@ -739,6 +737,10 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, ABS, DTYPE, TH>::MIN_CTA
             }
         }
         __syncthreads();
+        // the stage of the previous tile is free: start the copy NST - 1 tiles ahead into it.
+        // Warp 0 does this here rather than before its row items: every warp waits at the barrier
+        // above for the last one to finish its row items (1.386 against 1.408 ms on the C3 batch)
+        if (tid < 32 && n > 1) issue((n - 2) % NST, true);
         // ---- pass along u: K rows x 4 columns per thread, column pairs per packed FMA; a unit
         // whose T rows k0 .. k0 + K + 2R - 1 of its 8-column block are all zero stores zeros
         const int k0 = (tid >> 4) * K, c0 = (tid & 15) * 4;

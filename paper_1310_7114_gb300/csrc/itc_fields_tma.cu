@@ -511,18 +511,17 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, ABS, DTYPE, TH>::MIN_CTA
             constexpr int NW4 = 4 + 2 * R;                   // inputs of 4 neighbouring outputs
             constexpr int NQ4 = (OFF + NW4 + 3) / 4;         // 4-element groups covering the window
             // the item's input words (box columns c - R + RA - OFF .., a multiple of 4) of its two
-            // rows; rows outside the image read as zero
+            // rows; the staged box holds zeros outside the image (the copy's fill beyond the tensor
+            // map's bounds), so rows and columns outside need no test (1.385 -> 1.353 ms on C3)
             auto load_item = [&](int item, uint32_t (&w0)[NQ4], uint32_t (&w1)[NQ4]) {
                 const int r0 = (item >> 4) * 2, c = (item & 15) * 4;
-                const int gu0 = u0 - R + r0;
-                const bool in0 = gu0 >= 0 && gu0 < H, in1 = gu0 + 1 >= 0 && gu0 + 1 < H;
                 const int g0 = (c - R + RA - OFF) >> 2;
                 const uint32_t* row0 = reinterpret_cast<const uint32_t*>(stage + r0 * BW);
                 const uint32_t* row1 = row0 + BW / 4;
 #pragma unroll
                 for (int q = 0; q < NQ4; ++q) {
-                    w0[q] = in0 ? row0[g0 + q] : 0u;
-                    w1[q] = in1 ? row1[g0 + q] : 0u;
+                    w0[q] = row0[g0 + q];
+                    w1[q] = row1[g0 + q];
                 }
             };
             // one item from its input words: inputs as (row r0, row r0 + 1) pairs, bytes -> floats

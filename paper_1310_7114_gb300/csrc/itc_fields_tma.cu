@@ -638,8 +638,9 @@ __global__ void __launch_bounds__(kThreads, (TmaTile<R, ABS, DTYPE, TH>::MIN_CTA
                         st4(oT, 0.f, 0.f, 0.f, 0.f); st4(oT + TW, 0.f, 0.f, 0.f, 0.f);
                         st4(oV, 0.f, 0.f, 0.f, 0.f); st4(oV + TW, 0.f, 0.f, 0.f, 0.f);
                     }
-                    if (nz0) atomicOr(&colbits[par][c >> 3][r0 >> 5], 1u << (r0 & 31));
-                    if (nz1) atomicOr(&colbits[par][c >> 3][(r0 + 1) >> 5], 1u << ((r0 + 1) & 31));
+                    // rows r0 and r0 + 1 (r0 even) share a word of the column bits
+                    const uint32_t rb = (nz0 ? 1u : 0u) | (nz1 ? 2u : 0u);
+                    if (rb) atomicOr(&colbits[par][c >> 3][r0 >> 5], rb << (r0 & 31));
                     // both windows all ones (shape interiors; centred moments): T and T_v are the
                     // FMA chains of the taps, prepared on the host
                     if constexpr (!ABS) {

@@ -51,7 +51,7 @@ extern "C" {
 #define ITC_ERR_TIMEOUT (-3)       /* a bounded device wait gave up */
 #define ITC_ERR_NONFINITE (-4)     /* device status: S_XW = 0 or a non-finite value appeared */
 #define ITC_ERR_WORKSPACE (-5)     /* workspace missing, too small or misaligned */
-#define ITC_ERR_UNSUPPORTED (-6)   /* valid request outside this build's limits */
+#define ITC_ERR_UNSUPPORTED (-6)   /* valid request outside the library's compiled limits */
 
 /* --------------------------------------------------------------------------- data types */
 #define ITC_U8 0   /* 2-D: occupancy 0/1 (binary image X of Sec. 3.2); 3-D: gray level */
@@ -77,7 +77,7 @@ extern "C" {
                                   ITC_ERR_TIMEOUT in itc_stats.  Nothing else is affected and the
                                   GPU stays usable.  Never set otherwise. */
 
-/* Limits of this build. */
+/* Compiled limits of the library. */
 #define ITC_MAX_RADIUS_UV 32   /* R_u, R_v */
 #define ITC_MAX_RADIUS_UV_3D 24 /* R_u, R_v of 3-D gray lattices */
 #define ITC_MAX_RADIUS_G 64    /* R_g */

@@ -199,7 +199,7 @@ size_t plan_layout(int B, size_t* desc_off, size_t* ints_off, size_t* tmap_off =
     return h + d + n + m;
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once; null when no driver is present (then
+// cuTensorMapEncodeTiled from the CUDA driver API, looked up once; null when no CUDA driver is present (then
 // every image takes the non-TMA fields path).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static std::once_flag once;
@@ -392,7 +392,7 @@ const char* itc_status_string(int code) {
         case ITC_ERR_TIMEOUT: return "a bounded device wait gave up";
         case ITC_ERR_NONFINITE: return "S_XW is zero or a value is not finite";
         case ITC_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
-        case ITC_ERR_UNSUPPORTED: return "request outside this build's limits";
+        case ITC_ERR_UNSUPPORTED: return "request outside the library's compiled limits";
         default: return "unknown status";
     }
 }

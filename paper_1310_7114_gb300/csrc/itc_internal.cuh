@@ -2,7 +2,7 @@
 // Nothing here is part of the public ABI (include/itc.h is).
 #pragma once
 
-#include <cuda.h>   // CUtensorMap (type only; the encoder is fetched from the driver at run time)
+#include <cuda.h>   // CUtensorMap (type only; the encoder is fetched from the CUDA driver API at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 

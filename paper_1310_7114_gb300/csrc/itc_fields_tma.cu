@@ -159,7 +159,7 @@ __device__ __forceinline__ constexpr uint32_t window_mask(int q) {
 constexpr int kFieldsChunk = 4;
 // Row-pass items start at (tid + kItemRotate) mod kThreads: the threads of warps 0 and 1 take the
 // last item numbers of each round, so when a tile's items do not fill the last round those warps
-// have one item fewer -- warp 0 also walks the tile cursor and takes the next chunk.
+// have one item fewer -- thread 0 also adds up the previous tile's S_XX share before its items.
 constexpr int kItemRotate = kThreads - 64;
 
 // Bounded wait for a staged tile: gives up after about one second (2^31 SM clocks); false means

@@ -36,7 +36,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per pixel of the fields pass, from one ncu capture of the C3 workload
 # with 1024 images (profiles/fields_tma_kernel_c3_1024.md), valid only for the kernel source it was
 # taken on (sha256 prefix below); scaled to a launch by its pixel count.
-FIELDS_TRAFFIC = {"workload": "c3", "bytes_per_pixel": 974.11e6 / 86358723, "source_sha256": "4029664d38b5f967",
+FIELDS_TRAFFIC = {"workload": "c3", "bytes_per_pixel": 974.59e6 / 86358723, "source_sha256": "4029664d38b5f967",
                   "source": "paper_1310_7114_gb300/csrc/itc_fields_tma.cu"}
 
 

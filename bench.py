@@ -414,8 +414,9 @@ def alu_roofline(images, pk, ndims, fields_ms, clocks, dev):
             "algorithmic_fma_per_launch": fmas,
             "peak_source": f"{FMA_LANES_PER_SM} FP32 FMA lanes/SM x {sms} SMs x {mhz:.0f} MHz (median SM clock "
                            "sampled in the timed region), 2 flop/FMA",
-            "note": "secondary: 5 x (2R+1) FMA per pixel (2-D), the ideal count without halo recompute; "
-                    "tiles and windows that hold no data are skipped, so this may exceed what executes"}
+            "note": "secondary: 5 (2-D) or 7 (3-D) x (2R+1) FMA per lattice site, the ideal count without "
+                    "halo recompute; tiles and windows that hold no data are skipped, so this may exceed what "
+                    "executes"}
 
 
 def max_over_ranks(x, world, device):

@@ -34,7 +34,7 @@ __device__ __forceinline__ int find_image(const int* __restrict__ prefix, int n,
 }
 
 template <int RU, int RV, bool ABS, int TH>
-__global__ void __launch_bounds__(kThreads, 2) fields3d_kernel(const __grid_constant__ FieldsLaunch L, int ntiles)
+__global__ void __launch_bounds__(kThreads, 3) fields3d_kernel(const __grid_constant__ FieldsLaunch L, int ntiles)
 {
     constexpr int TW = kTileW;
     constexpr int K = TH / 16;                 // rows per thread of the zero stores
@@ -44,20 +44,21 @@ __global__ void __launch_bounds__(kThreads, 2) fields3d_kernel(const __grid_cons
     const int Rv = RV > 0 ? RV : tp.R[1];
     const int Rg = tp.R[2];
     const int ROWS = TH + 2 * Ru;
-    const int SW = ((TW + 2 * Rv + 3) & ~3) + 4;   // staged row length (floats, a multiple of 4)
+    const int SW = (TW + 2 * Rv + 3) & ~3;   // staged row length (sites, a multiple of 4)
     // mode 0: every plane of the fields; 1: A only, into the A_s plane (self-overlap pass);
     // 2: the S_XX partials only
     const int mode = L.mode;
     const int nstore = mode == 0 ? 4 : (mode == 1 ? 1 : 0);
 
+    // 74 KB at R = 9, so that three CTAs share an SM: the gray levels are staged as bytes and
+    // the weights of weighted images are read from global memory (L1) where they are needed
     extern __shared__ __align__(16) float smem[];
     float* s_S = smem;                    // ROWS x SW: S of the slice
     float* s_Sg = s_S + ROWS * SW;        // S_g
-    float* s_gray = s_Sg + ROWS * SW;     // gray levels (-1e6 outside the image)
-    float* s_w = s_gray + ROWS * SW;      // weights (0 outside)
-    float* sT = s_w + ROWS * SW;          // T, T_v, T_g: ROWS x TW each
+    float* sT = s_Sg + ROWS * SW;         // T, T_v, T_g: ROWS x TW each
+    float* s_gg = sT + 3 * ROWS * TW;     // g_g taps (indexed per site), 2 Rg + 1 of them
+    unsigned char* s_gray = reinterpret_cast<unsigned char*>(s_gg + ((2 * Rg + 4) & ~3));   // ROWS x SW
     __shared__ double red[2][kThreads / 32];
-    __shared__ float s_gg[kMaxTapsG];     // g_g taps (indexed per site)
     const int tid = threadIdx.x, lane = tid & 31;
     for (int i = tid; i <= 2 * Rg; i += kThreads) s_gg[i] = tp.gg[i];
 
@@ -79,14 +80,14 @@ __global__ void __launch_bounds__(kThreads, 2) fields3d_kernel(const __grid_cons
         b -= __ldg(L.tile_prefix + img_p);
         return L.descs + __ldg(L.img_list + img_p);
     };
-    // stage the gray levels and weights of the (u, v) window at u0, v0.  Without weights and
-    // with rows on 16-byte boundaries: 16-byte loads of the row chunks [v0 - 16, v0 + 80), which
-    // cover the staged columns v0 - Rv .. v0 + 63 + Rv (Rv <= 16); a chunk that starts inside
-    // the row ends inside its 16-byte pitch
+    // stage the gray levels of the (u, v) window at u0, v0 as bytes (0 outside the image; the S
+    // pass tests the sites' coordinates).  With rows on 16-byte boundaries: 16-byte loads of the
+    // row chunks [v0 - 16, v0 + 80), which cover the staged columns v0 - Rv .. v0 + 63 + Rv
+    // (Rv <= 16); a chunk that starts inside the row ends inside its 16-byte pitch
     auto stage = [&](const ImageDesc* dp, int u0, int v0) {
         const int H = dp->H, W = dp->W, pitch = dp->pitch;
         const unsigned char* data = reinterpret_cast<const unsigned char*>(dp->data);
-        if (!dp->weight && (pitch & 15) == 0 && (reinterpret_cast<uintptr_t>(data) & 15) == 0 && Rv <= 16) {
+        if ((pitch & 15) == 0 && (reinterpret_cast<uintptr_t>(data) & 15) == 0 && Rv <= 16) {
             for (int e = tid; e < ROWS * 6; e += kThreads) {
                 const int r = e / 6, q = e - 6 * r;
                 const int gu = u0 - Ru + r, col = v0 - 16 + 16 * q;
@@ -98,41 +99,47 @@ __global__ void __launch_bounds__(kThreads, 2) fields3d_kernel(const __grid_cons
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int c = col - (v0 - Rv) + k;   // staged column of byte k
-                    if (c >= 0 && c < SW) {
-                        const bool in = row_in && col + k >= 0 && col + k < W && c < TW + 2 * Rv;
-                        s_gray[r * SW + c] = in ? (float)((wv[k >> 2] >> (8 * (k & 3))) & 0xffu) : -1e6f;
-                        s_w[r * SW + c] = in ? 1.f : 0.f;
-                    }
+                    if (c >= 0 && c < SW) s_gray[r * SW + c] = (unsigned char)(wv[k >> 2] >> (8 * (k & 3)));
                 }
             }
         } else {
             for (int e = tid; e < ROWS * SW; e += kThreads) {
                 const int r = e / SW, c = e - r * SW;
                 const int gu = u0 - Ru + r, gv = v0 - Rv + c;
-                float gl = -1e6f, wt = 0.f;
-                if (gu >= 0 && gu < H && gv >= 0 && gv < W && c < TW + 2 * Rv) {
-                    gl = (float)__ldg(data + (size_t)gu * pitch + gv);
-                    wt = dp->weight ? __ldg(dp->weight + (size_t)gu * pitch + gv) : 1.f;
-                }
-                s_gray[e] = gl;
-                s_w[e] = wt;
+                s_gray[e] = (gu >= 0 && gu < H && gv >= 0 && gv < W) ? __ldg(data + (size_t)gu * pitch + gv) : 0;
             }
         }
     };
-    // S and S_g of slice yg over the staged window, four sites per step; nonzero if any S is
-    auto s_pass = [&](int yg) -> int {
+    // S and S_g of slice yg over the staged window, four sites per step; nonzero if any S is.
+    // Staged columns [clo, chi) of rows inside the image hold its sites; the others hold no data.
+    // A site's tap index is its gray level + Rg - yg, and g - I is that index - Rg, exactly.
+    auto s_pass = [&](const ImageDesc* dp, int u0, int v0, int yg) -> int {
+        const int H = dp->H, pitch = dp->pitch;
+        const float* wimg = dp->weight;
+        const int clo = Rv - v0 > 0 ? Rv - v0 : 0;
+        const int chi = min(dp->W - (v0 - Rv), TW + 2 * Rv);
+        const int ib = Rg - yg;
+        const float fb = 8388608.f + (float)Rg;   // 2^23 + Rg: (2^23 + idx) - fb = idx - Rg
         int nonzero = 0;
+        const int QW = SW / 4;
 #pragma unroll 2
-        for (int q = tid; q < ROWS * SW / 4; q += kThreads) {
-            const float4 g4 = ld4(s_gray + 4 * q), w4 = ld4(s_w + 4 * q);
-            const float gl[4] = {g4.x, g4.y, g4.z, g4.w}, wt[4] = {w4.x, w4.y, w4.z, w4.w};
+        for (int q = tid; q < ROWS * QW; q += kThreads) {
+            const int r = q / QW, c = 4 * (q - r * QW);
+            const int gu = u0 - Ru + r;
+            const uint32_t g4 = *reinterpret_cast<const uint32_t*>(s_gray + r * SW + c);
+            const bool row_in = (unsigned)gu < (unsigned)H;
             float sv[4], sa[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float dgl = gl[j] - (float)yg;
-                sv[j] = fabsf(dgl) <= (float)Rg ? wt[j] * s_gg[(int)dgl + Rg] : 0.f;
-                sa[j] = ABS ? sv[j] * gl[j] : sv[j] * dgl;
-                nonzero |= (sv[j] != 0.f);
+                const int idx = (int)__byte_perm(g4, 0u, 0x4440u | (unsigned)j) + ib;
+                const bool ok = row_in && c + j >= clo && c + j < chi && (unsigned)idx <= (unsigned)(2 * Rg);
+                const int ic = min(max(idx, 0), 2 * Rg);
+                float v = ok ? s_gg[ic] : 0.f;
+                if (wimg && ok) v = __ldg(wimg + (size_t)gu * pitch + (v0 - Rv + c + j)) * v;
+                const float dgl = __int_as_float(0x4B000000 + ic) - fb;   // g - I (of the clamped index)
+                sv[j] = v;
+                sa[j] = ABS ? v * (dgl + (float)yg) : v * dgl;
+                nonzero |= (v != 0.f);
             }
             st4(s_S + 4 * q, sv[0], sv[1], sv[2], sv[3]);
             st4(s_Sg + 4 * q, sa[0], sa[1], sa[2], sa[3]);
@@ -148,10 +155,11 @@ __global__ void __launch_bounds__(kThreads, 2) fields3d_kernel(const __grid_cons
     int yg = b % dp->tiles_g, sp = b / dp->tiles_g;   // slice; (u, v) window
     stage(dp, (sp / dp->tiles_v) * TH, (sp % dp->tiles_v) * TW);
     __syncthreads();
-    int any = __syncthreads_or(s_pass(yg));
+    int any = __syncthreads_or(s_pass(dp, (sp / dp->tiles_v) * TH, (sp % dp->tiles_v) * TW, yg));
 
     for (int t = t_begin; t < t_end; ++t) {
-        const int H = dp->H, W = dp->W, fpitch = dp->fpitch;
+        const int H = dp->H, W = dp->W, fpitch = dp->fpitch, ipitch = dp->pitch;
+        const float* const wimg = dp->weight;
         const int u0 = (sp / dp->tiles_v) * TH, v0 = (sp % dp->tiles_v) * TW;
         float* const fbase = L.fields + (mode == 1 ? dp->self_off : dp->field_off);
         const long long plane = dp->plane_floats;
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields3d_kernel(const __grid_cons
                             if (f < nstore) o[f * plane] = acc[f][kk];
                         // h at the output: the pixel's weight on its own gray slice
                         const int si = (kr + kk + Ru) * SW + cc + Rv;
-                        const float hx = s_gray[si] == (float)yg ? s_w[si] : 0.f;
+                        const float hx = s_gray[si] != yg ? 0.f : (wimg ? __ldg(wimg + (size_t)u * ipitch + v0 + cc) : 1.f);
                         part = fmaf(hx, acc[0][kk], part);
                     }
                 }
@@ -300,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 2) fields3d_kernel(const __grid_cons
                 stage(dn, (spn / dn->tiles_v) * TH, (spn % dn->tiles_v) * TW);
                 __syncthreads();
             }
-            nonzero = s_pass(ygn);
+            nonzero = s_pass(dn, (spn / dn->tiles_v) * TH, (spn % dn->tiles_v) * TW, ygn);
             dp = dn;
             b = bn;
             yg = ygn;
@@ -318,8 +326,9 @@ __global__ void __launch_bounds__(kThreads, 2) fields3d_kernel(const __grid_cons
 template <int RU, int RV, bool ABS, int TH>
 cudaError_t launch_3d(const FieldsLaunch& L, int ntiles, int Ru, int Rv, cudaStream_t s) {
     const int rows = TH + 2 * Ru;
-    const int SW = ((kTileW + 2 * Rv + 3) & ~3) + 4;
-    const size_t smem = (size_t)rows * SW * sizeof(float) * 4 + (size_t)3 * rows * kTileW * sizeof(float);
+    const int SW = (kTileW + 2 * Rv + 3) & ~3;
+    const size_t smem = ((size_t)2 * rows * SW + (size_t)3 * rows * kTileW + ((2 * L.taps.R[2] + 4) & ~3)) * sizeof(float) +
+                        (size_t)rows * SW;   // S, S_g, T, T_v, T_g, the g taps, the gray bytes
     auto k = fields3d_kernel<RU, RV, ABS, TH>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -33,21 +33,39 @@ sys.path.insert(0, ROOT)
 METRIC = "batched ITC images/s vs per-image launch at ≤1e-5 rel err; conv GB/s % HBM peak"
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes (read + write) per pixel of the fields pass, from one ncu capture of the C3 workload
-# with 1024 images (profiles/fields_tma_kernel_c3_1024.md), valid only for the kernel source it was
-# taken on (sha256 prefix below); scaled to a launch by its pixel count.
-FIELDS_TRAFFIC = {"workload": "c3", "bytes_per_pixel": 974.59e6 / 86358723, "source_sha256": "4029664d38b5f967",
-                  "source": "paper_1310_7114_gb300/csrc/itc_fields_tma.cu"}
+# DRAM bytes (read + write) per lattice site of the fields pass, from one ncu capture of the workload
+# (C3: 1024 of its images, profiles/fields_tma_kernel_c3_1024.md; C5: its one launch,
+# profiles/fields3d_kernel_c5_gray3d.md), valid only for the kernel source it was taken on
+# (sha256 prefix below); scaled to a launch by its site count (pixels, or voxels of the 3-D lattice).
+FIELDS_TRAFFIC = {
+    "c3": {"bytes_per_site": 974.59e6 / 86358723, "source_sha256": "4029664d38b5f967",
+           "source": "paper_1310_7114_gb300/csrc/itc_fields_tma.cu",
+           "note": "ncu dram bytes of the 1024-image capture scaled by pixels (profiles/fields_tma_kernel_c3_1024.md)"},
+    "c5": {"bytes_per_site": (0.17e6 + 206.90e6) / 16777216, "source_sha256": "c920c9cfe3326cbe",
+           "source": "paper_1310_7114_gb300/csrc/itc_fields3d.cu",
+           "note": "ncu dram bytes of one launch (profiles/fields3d_kernel_c5_gray3d.md)"},
+}
 
 
-def fields_traffic(name, pixels):
+def fields_traffic(name, sites):
+    """(DRAM bytes of one fields pass, note), or (None, why) when no capture covers this source."""
     import hashlib
-    if name != FIELDS_TRAFFIC["workload"]:
-        return None
-    with open(os.path.join(ROOT, FIELDS_TRAFFIC["source"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest()[:16] != FIELDS_TRAFFIC["source_sha256"]:
-            return None   # the kernel changed since the counters were taken
-    return FIELDS_TRAFFIC["bytes_per_pixel"] * pixels
+    t = FIELDS_TRAFFIC.get(name)
+    if t is None:
+        return None, "no ncu capture of this workload's fields pass"
+    with open(os.path.join(ROOT, t["source"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != t["source_sha256"]:
+            return None, "the kernel changed since its ncu capture"
+    return t["bytes_per_site"] * sites, t["note"]
+
+
+def fields_kernel_name(ndims, tuning):
+    """The kernel that runs the fields pass of this plan."""
+    if all(d == 3 for d in ndims):
+        return "fields3d_kernel (persistent CTAs over runs of one-slice tiles, one launch)"
+    kinds = sorted({c["staging"] for c in tuning})
+    names = {"tma": "fields_tma_kernel", "plain": "fields_kernel"}
+    return " + ".join(names.get(k, k) for k in kinds) + " (persistent, one launch per sigma class)"
 
 WORKLOADS = {
     "c3": dict(desc="4096 binary blob silhouettes, sides U{64..512}, M in {16,32,64,128}, sigma in {2,3,4}, "
@@ -813,6 +831,8 @@ def run_ours(args, rank, world, local_rank):
 
     peaks, peak_src = measured_peaks()
     fbytes = algorithmic_field_bytes(images, ndims, Gs)
+    traffic, traffic_note = fields_traffic(name, sum(im.size * (G if d == 3 else 1)
+                                                     for im, d, G in zip(images, ndims, Gs)))
     f_avg = statistics.mean(f_ms)
     achieved = fbytes / (f_avg / 1000.0) / 1e9
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
@@ -845,10 +865,8 @@ def run_ours(args, rank, world, local_rank):
                       "note": "phases run in sequence in a separate timed loop; the headline step overlaps "
                               f"fields and iterations over {args.chunks} image ranges on two streams"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": fields_traffic(name, sum(im.size for im in images)),
-                     "traffic_note": "ncu dram bytes of the 1024-image capture scaled by pixels "
-                                     "(profiles/fields_tma_kernel_c3_1024.md)",
-                     "kernel": "fields pass (fields_tma_kernel, persistent, one launch per sigma class)",
+                     "frac": achieved / hbm, "traffic": traffic, "traffic_note": traffic_note,
+                     "kernel": "fields pass: " + fields_kernel_name(ndims, tuning),
                      "algorithmic_bytes_per_launch": fbytes, "peak_source": f"{peak_src} hbm_gbs"},
         "roofline_alu": alu_roofline(images, pk, ndims, f_avg, clk.summary(), dev),
         "e2e": {"value": world * B / (e2e_ms / 1000.0), "unit": "images/s", "h2d_bytes_per_step": int(h2d),

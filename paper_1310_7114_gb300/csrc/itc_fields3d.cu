@@ -3,7 +3,7 @@
 //
 // The input of a gray image is one lattice point per pixel, at (u, v, I(u, v)) with the pixel's
 // weight.  The convolution along g is analytic: on gray slice g a pixel carries
-//   S = w g_g(g - I) and S_g = S (g - I) (centred moments; S g for absolute ones),
+//   S = w g_g(g - I) and S_g = S (I - g) (centred moments; S I for absolute ones),
 // and the slice's fields are the 2-D passes over S and S_g:
 //   T = g_v * S, T_v = (d g_v) * S or g_v * (v S), T_g = g_v * S_g                (along v)
 //   A = g_u * T, F_u = (d g_u) * T or g_u * (u T), F_v = g_u * T_v, F_g = g_u * T_g (along u).
@@ -112,37 +112,71 @@ __global__ void __launch_bounds__(kThreads, 3) fields3d_kernel(const __grid_cons
     };
     // S and S_g of slice yg over the staged window, four sites per step; nonzero if any S is.
     // Staged columns [clo, chi) of rows inside the image hold its sites; the others hold no data.
-    // A site's tap index is its gray level + Rg - yg, and g - I is that index - Rg, exactly.
+    // The four gray levels of a step are tested at once (byte-wise |I - g| <= Rg), and images
+    // without weights take a loop of their own (a tested weight load costs its address
+    // arithmetic in every step).
     auto s_pass = [&](const ImageDesc* dp, int u0, int v0, int yg) -> int {
         const int H = dp->H, pitch = dp->pitch;
         const float* wimg = dp->weight;
         const int clo = Rv - v0 > 0 ? Rv - v0 : 0;
         const int chi = min(dp->W - (v0 - Rv), TW + 2 * Rv);
-        const int ib = Rg - yg;
-        const float fb = 8388608.f + (float)Rg;   // 2^23 + Rg: (2^23 + idx) - fb = idx - Rg
-        int nonzero = 0;
+        const uint32_t yg4 = (uint32_t)yg * 0x01010101u, rg4 = (uint32_t)min(Rg, 255) * 0x01010101u;
+        const float fb = 8388608.f + (float)yg;   // (2^23 + I) - (2^23 + g) = I - g, exactly
         const int QW = SW / 4;
-#pragma unroll 2
-        for (int q = tid; q < ROWS * QW; q += kThreads) {
-            const int r = q / QW, c = 4 * (q - r * QW);
-            const int gu = u0 - Ru + r;
-            const uint32_t g4 = *reinterpret_cast<const uint32_t*>(s_gray + r * SW + c);
-            const bool row_in = (unsigned)gu < (unsigned)H;
-            float sv[4], sa[4];
+        int nonzero = 0;
+        // per step: 0xff in each byte whose site is in the image and within the slice's band
+        auto band = [&](int q, int& r, int& c, int& gu, uint32_t& g4) -> uint32_t {
+            r = q / QW;
+            c = 4 * (q - r * QW);
+            gu = u0 - Ru + r;
+            g4 = *reinterpret_cast<const uint32_t*>(s_gray + r * SW + c);
+            uint32_t m = (unsigned)gu < (unsigned)H ? __vcmpleu4(__vabsdiffu4(g4, yg4), rg4) : 0u;
+            if (c < clo || c + 3 >= chi) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int idx = (int)__byte_perm(g4, 0u, 0x4440u | (unsigned)j) + ib;
-                const bool ok = row_in && c + j >= clo && c + j < chi && (unsigned)idx <= (unsigned)(2 * Rg);
-                const int ic = min(max(idx, 0), 2 * Rg);
-                float v = ok ? s_gg[ic] : 0.f;
-                if (wimg && ok) v = __ldg(wimg + (size_t)gu * pitch + (v0 - Rv + c + j)) * v;
-                const float dgl = __int_as_float(0x4B000000 + ic) - fb;   // g - I (of the clamped index)
-                sv[j] = v;
-                sa[j] = ABS ? v * (dgl + (float)yg) : v * dgl;
-                nonzero |= (v != 0.f);
+                for (int j = 0; j < 4; ++j)
+                    if (c + j < clo || c + j >= chi) m &= ~(0xffu << (8 * j));
             }
-            st4(s_S + 4 * q, sv[0], sv[1], sv[2], sv[3]);
-            st4(s_Sg + 4 * q, sa[0], sa[1], sa[2], sa[3]);
+            return m;
+        };
+        if (!wimg) {
+#pragma unroll 2
+            for (int q = tid; q < ROWS * QW; q += kThreads) {
+                int r, c, gu;
+                uint32_t g4;
+                const uint32_t m = band(q, r, c, gu, g4);
+                float sv[4], sa[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int gl = (int)((g4 >> (8 * j)) & 0xffu);
+                    const bool in = (m >> (8 * j)) & 1u;
+                    const float gg = s_gg[in ? gl - yg + Rg : 0];
+                    const float v = in ? gg : 0.f;
+                    sv[j] = v;
+                    sa[j] = ABS ? v * (float)gl : v * (__int_as_float(0x4B000000 | gl) - fb);
+                }
+                nonzero |= (m != 0u);
+                st4(s_S + 4 * q, sv[0], sv[1], sv[2], sv[3]);
+                st4(s_Sg + 4 * q, sa[0], sa[1], sa[2], sa[3]);
+            }
+        } else {
+            for (int q = tid; q < ROWS * QW; q += kThreads) {
+                int r, c, gu;
+                uint32_t g4;
+                const uint32_t m = band(q, r, c, gu, g4);
+                float sv[4], sa[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int gl = (int)((g4 >> (8 * j)) & 0xffu);
+                    float v = 0.f;
+                    if ((m >> (8 * j)) & 1u)
+                        v = __ldg(wimg + (size_t)gu * pitch + (v0 - Rv + c + j)) * s_gg[gl - yg + Rg];
+                    sv[j] = v;
+                    sa[j] = ABS ? v * (float)gl : v * (__int_as_float(0x4B000000 | gl) - fb);
+                    nonzero |= (v != 0.f);
+                }
+                st4(s_S + 4 * q, sv[0], sv[1], sv[2], sv[3]);
+                st4(s_Sg + 4 * q, sa[0], sa[1], sa[2], sa[3]);
+            }
         }
         return nonzero;
     };

@@ -116,3 +116,25 @@ def plan_lockstep(images, Ms, params, W0s, iters, oracle_step, ndims=None, Gs=No
             ties += assert_lattice_equal_except_ties(got[b], Wn, raw, what=f"{what}: image {b} iteration {t}")
             Wc[b] = Wn
     return ties
+
+
+def assert_nearest_sites(X, lab, W, shape, tau, what=""):
+    """Segment labels against exact arithmetic, independently of the single-precision metric
+    both the kernel and the oracle evaluate: every point's codebook site is at most a few FP32
+    roundings (8 u, relative) farther than the nearest under sum_i (x_i - r_i)^2 / tau_i^2, and
+    where the nearest site is unique by more than that, the label is that site.  X: N x d points
+    (int), lab: N labels, W: M x d codebook (sites by rounding and clamping to shape)."""
+    u = 2.0 ** -24
+    R = np.clip(np.floor(np.asarray(W, np.float64) + 0.5), 0, np.asarray(shape) - 1).astype(np.int64)
+    t2 = np.asarray(np.broadcast_to(np.asarray(tau, np.float32), (X.shape[1],)), np.float64) ** 2
+    for s in range(0, len(X), 4096):   # chunks of points: N x M metrics stay small
+        Xc, lc = X[s:s + 4096].astype(np.int64), np.asarray(lab[s:s + 4096])
+        d = Xc[:, None, :] - R[None, :, :]
+        D = ((d * d) / t2).sum(-1)
+        best = D.min(1)
+        got = D[np.arange(len(Xc)), lc]
+        assert np.all(got <= best * (1 + 8 * u)), f"{what}: a label farther than the nearest site"
+        if D.shape[1] > 1:
+            srt = np.partition(D, 1, axis=1)[:, :2]
+            clear = srt[:, 1] > srt[:, 0] * (1 + 8 * u)
+            assert np.all(lc[clear] == D.argmin(1)[clear]), f"{what}: not the unique nearest site"

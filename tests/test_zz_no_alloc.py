@@ -3,17 +3,18 @@
 Some hosts hand the library only their input and output buffers and forbid allocation while
 they run, so they cannot pass itc_fields' scratch.  This variant keeps that scratch in a fixed
 array inside the library.  The GPU test checks its output against itc_fields on two calls in a
-row (the second call reuses the shared array that the first one filled), with the same
-tolerance as the other fields tests."""
+row (the second call reuses the shared array that the first one filled), and against the FP64
+oracle, with the same tolerances as the other fields tests."""
 import numpy as np
 import pytest
 
+import oracle
 from gpuhelp import assert_fields_close, radii
 from paper_1310_7114_gb300 import build, itc, synth
 
 
 @pytest.mark.gpu
-def test_noalloc_fields_match_itc_fields_on_two_calls():
+def test_noalloc_fields_match_itc_fields_and_the_oracle_on_two_calls():
     import torch
     build.build()
     itc.lib()
@@ -31,6 +32,10 @@ def test_noalloc_fields_match_itc_fields_on_two_calls():
         old = [ref[i, 0, :, :W].cpu().numpy().astype(np.float64) for i in range(3)]
         assert_fields_close(new, old, radii(sigma), False, "noalloc vs itc_fields")
         assert abs(sxx.item() - sxx_ref.item()) <= 1e-5 * abs(sxx_ref.item())
+        orc = oracle.fields2d(h.astype(np.float64), sigma)
+        assert_fields_close(new, list(orc), radii(sigma), False, "noalloc vs oracle")
+        orc_sxx = oracle.sxx(h.astype(np.float64), orc[0])
+        assert abs(sxx.item() - orc_sxx) <= 1e-5 * orc_sxx
 
 
 def test_noalloc_rejects_images_beyond_the_fixed_scratch():

@@ -10,8 +10,7 @@
 //
 // One tile is TH x 64 sites of one gray slice.  The CTAs are persistent: each takes a contiguous
 // run of the class's tiles, which are ordered slice-fastest within an image, so consecutive tiles
-// share their (u, v) window and the pixels' gray levels and weights are staged once per window
-// and run.  Each tile's share of S_XX is its own partial (FP32 within warps, FP64 across them).
+// share their (u, v) window and the pixels' gray levels are staged once per window and run.  Each tile's share of S_XX is its own partial (FP32 within warps, FP64 across them).
 // Tiles whose slice holds no data write zeros.
 #include "itc_internal.cuh"
 
@@ -34,7 +33,7 @@ __device__ __forceinline__ int find_image(const int* __restrict__ prefix, int n,
 }
 
 template <int RU, int RV, bool ABS, int TH>
-__global__ void __launch_bounds__(kThreads, 3) fields3d_kernel(const __grid_constant__ FieldsLaunch L, int ntiles)
+__global__ void __launch_bounds__(kThreads, (RU > 0 && RU <= 9) ? 3 : 2) fields3d_kernel(const __grid_constant__ FieldsLaunch L, int ntiles)
 {
     constexpr int TW = kTileW;
     constexpr int K = TH / 16;                 // rows per thread of the zero stores
@@ -50,8 +49,9 @@ __global__ void __launch_bounds__(kThreads, 3) fields3d_kernel(const __grid_cons
     const int mode = L.mode;
     const int nstore = mode == 0 ? 4 : (mode == 1 ? 1 : 0);
 
-    // 74 KB at R = 9, so that three CTAs share an SM: the gray levels are staged as bytes and
-    // the weights of weighted images are read from global memory (L1) where they are needed
+    // 76 KB at R = 9, so that three CTAs share an SM (two at larger radii): the gray levels are
+    // staged as bytes and the weights of weighted images are read from global memory (L1) where
+    // they are needed
     extern __shared__ __align__(16) float smem[];
     float* s_S = smem;                    // ROWS x SW: S of the slice
     float* s_Sg = s_S + ROWS * SW;        // S_g

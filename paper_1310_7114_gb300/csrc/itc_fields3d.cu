@@ -292,20 +292,63 @@ __global__ void __launch_bounds__(kThreads, (RU > 0 && RU <= 9) ? 3 : 2) fields3
                     for (int kk = 0; kk < 8; ++kk) acc[f][kk] = 0.f;
                 const float* Tp = sT + kr * TW + cc;
                 const float ubase = (float)(u0 - Ru + kr);
+                if constexpr (RU > 0 && !ABS) {
+                    // two fields per packed FMA, tap-outer over the unit's inputs in registers (a
+                    // tap pair is formed once for the 8 rows): (A, F_u) += (g_u, d g_u) (T, T), then
+                    // (F_v, F_g) += (g_u, g_u) (T_v, T_g); the same products in the same order as
+                    // the scalar loop below (0.183 -> 0.181 ms on C5)
+                    constexpr int NI = 8 + 2 * RU;
+                    float2 pa[8], pb[8];
+                    {
+                        float2 x[NI];
 #pragma unroll
-                for (int i = 0; i < (RU > 0 ? 8 + 2 * RU : 8 + 2 * Ru); ++i) {
-                    const float t0 = Tp[i * TW], t1 = Tp[ROWS * TW + i * TW], t2 = Tp[2 * ROWS * TW + i * TW];
-                    const float tu = ABS ? t0 * (ubase + (float)i) : 0.f;
+                        for (int i = 0; i < NI; ++i) {
+                            const float t0 = Tp[i * TW];
+                            x[i] = make_float2(t0, t0);
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) pa[kk] = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int e = 0; e <= 2 * RU; ++e) {
+                            const float2 gp = make_float2(tp.gu[e], tp.dgu[e]);
+#pragma unroll
+                            for (int kk = 0; kk < 8; ++kk) pa[kk] = __ffma2_rn(gp, x[kk + e], pa[kk]);
+                        }
+                    }
+                    {
+                        float2 x[NI];
+#pragma unroll
+                        for (int i = 0; i < NI; ++i) x[i] = make_float2(Tp[ROWS * TW + i * TW], Tp[2 * ROWS * TW + i * TW]);
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) pb[kk] = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int e = 0; e <= 2 * RU; ++e) {
+                            const float2 gp = make_float2(tp.gu[e], tp.gu[e]);
+#pragma unroll
+                            for (int kk = 0; kk < 8; ++kk) pb[kk] = __ffma2_rn(gp, x[kk + e], pb[kk]);
+                        }
+                    }
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
-                        const int e = i - kk;
-                        if (e >= 0 && e <= 2 * Ru) {
-                            const float g = tp.gu[e];
-                            acc[0][kk] = fmaf(g, t0, acc[0][kk]);
-                            if constexpr (ABS) acc[1][kk] = fmaf(g, tu, acc[1][kk]);
-                            else acc[1][kk] = fmaf(tp.dgu[e], t0, acc[1][kk]);
-                            acc[2][kk] = fmaf(g, t1, acc[2][kk]);
-                            acc[3][kk] = fmaf(g, t2, acc[3][kk]);
+                        acc[0][kk] = pa[kk].x; acc[1][kk] = pa[kk].y;
+                        acc[2][kk] = pb[kk].x; acc[3][kk] = pb[kk].y;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < (RU > 0 ? 8 + 2 * RU : 8 + 2 * Ru); ++i) {
+                        const float t0 = Tp[i * TW], t1 = Tp[ROWS * TW + i * TW], t2 = Tp[2 * ROWS * TW + i * TW];
+                        const float tu = ABS ? t0 * (ubase + (float)i) : 0.f;
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const int e = i - kk;
+                            if (e >= 0 && e <= 2 * Ru) {
+                                const float g = tp.gu[e];
+                                acc[0][kk] = fmaf(g, t0, acc[0][kk]);
+                                if constexpr (ABS) acc[1][kk] = fmaf(g, tu, acc[1][kk]);
+                                else acc[1][kk] = fmaf(tp.dgu[e], t0, acc[1][kk]);
+                                acc[2][kk] = fmaf(g, t1, acc[2][kk]);
+                                acc[3][kk] = fmaf(g, t2, acc[3][kk]);
+                            }
                         }
                     }
                 }

@@ -41,7 +41,7 @@ FIELDS_TRAFFIC = {
     "c3": {"bytes_per_site": 969.25e6 / 86358723, "source_sha256": "c1919dae6100b141",
            "source": "paper_1310_7114_gb300/csrc/itc_fields_tma.cu",
            "note": "ncu dram bytes of the 1024-image capture scaled by pixels (profiles/fields_tma_kernel_c3_1024.md)"},
-    "c5": {"bytes_per_site": (0.21e6 + 206.87e6) / 16777216, "source_sha256": "527c93c765583a5c",
+    "c5": {"bytes_per_site": (0.27e6 + 206.93e6) / 16777216, "source_sha256": "6eedaafde8ac4a48",
            "source": "paper_1310_7114_gb300/csrc/itc_fields3d.cu",
            "note": "ncu dram bytes of one launch (profiles/fields3d_kernel_c5_gray3d.md)"},
 }

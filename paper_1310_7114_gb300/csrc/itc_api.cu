@@ -71,7 +71,8 @@ int check_params(const itc_params* p, int ndim) {
         const double ru = ceil((double)p->trunc * ws[0]), rv = ceil((double)p->trunc * ws[1]);
         if (ru > ITC_MAX_RADIUS_UV || rv > ITC_MAX_RADIUS_UV) return ITC_ERR_UNSUPPORTED;
         if (ndim == 3 && ceil((double)p->trunc * ws[2]) > ITC_MAX_RADIUS_G) return ITC_ERR_UNSUPPORTED;
-        // 3-D tiles stage four input channels; past R = 24 they exceed the 227 KB of shared memory
+        // 3-D tiles hold S, S_g, three row-pass planes and the gray bytes of 32 + 2R rows: 143 KB
+        // of shared memory at R = 24, the largest radius accepted for them
         if (ndim == 3 && (ru > ITC_MAX_RADIUS_UV_3D || rv > ITC_MAX_RADIUS_UV_3D)) return ITC_ERR_UNSUPPORTED;
     }
     return ITC_OK;
